@@ -1,0 +1,342 @@
+"""Benchmark of the GSW hologram engine (one JSON line on stdout).
+
+Workload (default): rand100_512 -- a 512 x 512 SLM, 100 traps with x, y ~ U[-40, 40] um and
+z ~ U[-10, 10] um (seed 0), 30 GSW iterations with fast sincos, 8-bit phase output.
+One step = upload of the starting phases (device to device) + hot_gsw(30) + the 8-bit
+encoding of the result, i.e. one complete hologram.
+
+Metric: GSW pixel-trap updates per second (one update = one (pixel, trap) pair through one
+full iteration, forward field and back-projection), summed over all GPUs; holograms/s is
+reported beside it.  --gpus N > 1 runs N independent replicas (one per rank; the path has
+no exchange step), timed between barriers, max over ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (bounded sample).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "GSW pixel-trap updates/s (512x512 px, M=100, 30 iterations)"
+UNIT = "updates/s"
+SFU_LANES_PER_SM = 16          # sin.approx / cos.approx results per clock per SM (sm_103a)
+SFU_OPS_PER_UPDATE = 4         # one sin + one cos in the forward field, one each in back-projection
+L2_FLUSH_BYTES = 256 << 20     # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--workload", default="rand100_512")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-iters", type=int, default=0,
+                    help="GSW iterations of the CPU-baseline sample (0: the workload's own count)")
+    return ap.parse_args()
+
+
+def workload_config(w, extra=None):
+    cfg = {"workload": f"{w.name}: {w.W}x{w.H} px, M={w.M} traps, {w.iters} GSW iterations, "
+                       f"{w.precision} sincos" + (", 8-bit output" if w.quantize else ""),
+           "W": w.W, "H": w.H, "M": w.M, "iters": w.iters, "precision": w.precision,
+           "output": "u8" if w.quantize else "f32", "seed": 0}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU)
+
+def cpu_baseline(w, iters: int):
+    """The FP64 oracle as it stands, on this host's cores, over `iters` full GSW iterations of
+    the workload (a bounded sample of its `w.iters`)."""
+    import oracle
+    cores = oracle.set_threads()
+    t0 = time.perf_counter()
+    oracle.gsw(w.geom, w.xyz, iters, w.phi0, w.w0)
+    dt = time.perf_counter() - t0
+    return {"value": w.N * w.M * iters / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{iters} of {w.iters} GSW iterations of {w.name} (FP64, all {w.N} pixels, "
+                      f"all {w.M} traps, plus one final forward), {dt:.2f} s"}
+
+
+def run_reference(args):
+    from paper_0907_4027_gb300 import workloads as wl
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = wl.NAMED[args.workload]()
+    iters = 2
+    for _ in range(args.warmup):
+        cpu_baseline(w, iters)
+    times, cores = [], None
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        r = cpu_baseline(w, iters)
+        times.append(w.N * w.M * iters / r["value"])
+        cores = r["cores"]
+    total = time.perf_counter() - t_all
+    value = w.N * w.M * iters * args.steps / sum(times)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": workload_config(w, {"reference_step": f"{iters} GSW iterations (bounded sample)"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{iters} of {w.iters} GSW iterations of {w.name} per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- engine (GPU)
+
+def kernel_source_hash() -> str:
+    src = os.path.join(ROOT, "paper_0907_4027_gb300", "csrc", "gsw_kernels.cuh")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the fused step kernel from the committed ncu summary, if the
+    summary was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"gsw_step_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not h or not b or h.group(1) != kernel_source_hash():
+        return None
+    return float(b.group(1))
+
+
+def run_engine(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_0907_4027_gb300 import _build
+    _build.build()
+    from paper_0907_4027_gb300 import hot, workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = wl.NAMED[args.workload]()
+    stream = torch.cuda.current_stream()
+    h = hot.Hologram(w.W, w.H, w.pitch, w.wavelength, w.focal, stream.cuda_stream, w.precision)
+    h.set_traps(w.xyz, w.w0)
+    phi0 = torch.tensor(w.phi0, dtype=torch.float32, device="cuda")
+    out = torch.empty(w.N, dtype=torch.uint8 if w.quantize else torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    fmt = "u8" if w.quantize else "f32"
+
+    def step():
+        h.set_phase(phi0)
+        h.gsw(w.iters, metrics=False)
+        h.phase(fmt, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: per-step events, L2 flushed between steps (outside the events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = h.launches
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = h.launches - launches0
+    if world > 1:
+        dist.barrier()
+    # per-kernel device times: the same steps again, kernels launched one by one between
+    # CUDA events on the launching stream (the timed region above replays CUDA graphs)
+    h.profile(True)
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        step()
+    prof = h.profile_read()
+    h.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = torch.tensor([sum(step_ms)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(total_ms, op=dist.ReduceOp.MAX)
+    total_ms = float(total_ms.item())
+    updates_per_step = w.N * w.M * w.iters
+    value = world * updates_per_step * args.steps / (total_ms * 1e-3)
+
+    # roofline of the dominant kernel (fused back-projection + forward, one iteration/launch)
+    step_kernel_ms, step_kernel_n = prof["step"]
+    avg_launch_s = step_kernel_ms * 1e-3 / max(step_kernel_n, 1)
+    achieved = w.N * w.M / avg_launch_s
+    dev = torch.cuda.get_device_properties(local)
+    sm_max_mhz = 2070.0
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        sm_max_mhz = float(json.load(open(peaks_path)).get("sm_max_mhz", sm_max_mhz))
+    peak = dev.multi_processor_count * SFU_LANES_PER_SM * sm_max_mhz * 1e6 / SFU_OPS_PER_UPDATE
+    traffic = profiled_traffic(args.workload)
+    kernel_share = {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4)
+                    for k, v in prof.items()}
+
+    # end to end through the public API with host buffers
+    xyz = w.xyz.copy()
+    phi_host = torch.tensor(w.phi0, dtype=torch.float32).pin_memory()
+    g_host = torch.empty(w.N, dtype=torch.uint8 if w.quantize else torch.float32).pin_memory()
+    phi_np, g_np = phi_host.numpy(), g_host.numpy()
+
+    def e2e_step():
+        h.set_traps(xyz, w.w0)
+        h.set_phase(phi_np)
+        e, u = h.gsw(w.iters, metrics=True)
+        h.phase(fmt, out=g_np)
+        return e, u
+
+    from paper_0907_4027_gb300.hot import hot_phase_out, HOT_FMT_U8, HOT_FMT_F32  # noqa: F401
+    for _ in range(2):
+        e2e_step()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        eu = e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+    e2e_value = world * updates_per_step * args.steps / float(e2e_s.item())
+    h2d = w.N * 4 + w.M * 3 * 8 + w.M * 8
+    d2h = w.N * (1 if w.quantize else 4) + 16
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(w, {
+                "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                "l2": "flushed between steps (256 MB write outside the step events)",
+                "timing": "CUDA events per step on the launching stream, summed; hot_gsw replays "
+                          "one CUDA graph per call; roofline kernel times from a second pass of "
+                          "the same steps with per-launch events"}),
+            "holograms_per_s": world * args.steps / (total_ms * 1e-3),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "updates/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "gsw_tile_kernel<fast, back, fwd> (one GSW iteration per launch)",
+                         "peak_basis": f"{dev.multi_processor_count} SMs x {SFU_LANES_PER_SM} SFU "
+                                       f"lanes/clk x {sm_max_mhz:.0f} MHz / {SFU_OPS_PER_UPDATE} "
+                                       "SFU ops per update",
+                         "avg_launch_us": avg_launch_s * 1e6, "launches": step_kernel_n},
+            "kernel_time_share": kernel_share,
+            "kernel_time_ms": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "api": "hot_set_traps + hot_set_phase (pinned host) + hot_gsw + hot_phase_out (host)",
+                    "final_e": eu[0], "final_u": eu[1]},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_iters or w.iters)
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_engine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,149 @@
+/*
+ * hot.h -- C ABI of the GB300 engine for weighted Gerchberg-Saxton (GSW) holograms by
+ * direct superposition (S. Bianchi, R. Di Leonardo, "Real-time optical micro-manipulation
+ * using optimized holograms generated on the GPU").
+ *
+ * The engine computes, for an SLM of W x H pixels (pitch p) and M traps (x_m, y_m, z_m)
+ * behind optics of wavelength lambda and effective focal length f:
+ *   Eq. 2   Delta_j^m = z_m pi/(lambda f^2) (x_j^2 + y_j^2) + 2 pi/(lambda f) (x_j x_m + y_j y_m)
+ *   Eq. 1   V_m = (1/N) sum_j exp(i (phi_j - Delta_j^m))                  (forward field)
+ *   Sec. 3  w_m <- w_m <|V|> / |V_m|,  <|V|> = mean over m of |V_m|     (weight update)
+ *   Sec. 4  phi_j = arg sum_m w_m (V_m/|V_m|) exp(i Delta_j^m)            (back-projection)
+ *   Eq. 4   e = sum_m |V_m|^2,  u = 1 - (max I - min I)/(max I + min I)  (quality)
+ *   Sec. 5  8-bit SLM grey levels g_j = rint(phi_j 256/(2 pi)) mod 256
+ * Pixel j = iy*W + ix has coordinates x_j = (ix - floor(W/2)) p, y_j = (iy - floor(H/2)) p.
+ * Device arithmetic is FP32, except the trap-table set-up (Eq. 2 reduced modulo 2 pi in FP64,
+ * once per hot_set_traps) and the reduction of the per-tile field partials (float-float,
+ * about 48 significant bits).  Every reduction runs in a fixed order: results are
+ * bit-reproducible for a given device, size and precision mode.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: HOT_OK (0) or a negative hot_status; no call aborts or exits.
+ *     hot_last_error() returns a text for the last failure of the calling thread.
+ *   - Invalid sizes or pointers give HOT_EINVAL before any device work is queued.
+ *   - Work is queued on the context's CUDA stream (given at creation; NULL is the legacy
+ *     default stream).  Calls that return data to host memory synchronise that stream.
+ *   - Host pointers are read or written before the call returns; device pointers
+ *     (on_device = 1) must be valid on the context's device and are used in stream order.
+ *   - The library owns every device buffer of a context; hot_destroy frees them.
+ *   - A context is not thread-safe: use one context per thread.
+ */
+#ifndef HOT_H
+#define HOT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hot_ctx hot_ctx;
+
+typedef enum {
+  HOT_OK = 0,
+  HOT_EINVAL = -1,   /* invalid argument (size, pointer, mode) */
+  HOT_ENOMEM = -2,   /* device or host allocation failed */
+  HOT_ECUDA = -3,    /* a CUDA call failed; see hot_last_error() */
+  HOT_ETIMEOUT = -4, /* a bounded device-side wait expired */
+  HOT_ESTATE = -5    /* call out of order (e.g. hot_gsw before hot_set_traps) */
+} hot_status;
+
+typedef enum {
+  HOT_PREC_ACCURATE = 0, /* sincospif on the exactly reduced phase (FP32, ~1 ulp) */
+  HOT_PREC_FAST = 1      /* sin.approx / cos.approx (SFU) on the reduced phase */
+} hot_precision;
+
+typedef enum {
+  HOT_FMT_F32 = 0, /* float32 radians in (-pi, pi] */
+  HOT_FMT_U8 = 1   /* uint8 grey level, rint(phi 256/(2 pi)) mod 256 (Sec. 5) */
+} hot_format;
+
+/* Largest trap count a context accepts. */
+#define HOT_MAX_TRAPS 4096
+
+/* Creates a context for a W x H SLM (Sec. 3: pixel pitch, wavelength, effective focal
+ * length, all in metres) on the current CUDA device, queueing work on cuda_stream
+ * (a cudaStream_t, or NULL).  W, H >= 1, W*H < 2^31; pitch, wavelength, focal > 0 and
+ * finite.  The initial phase is 0 everywhere and the precision is HOT_PREC_ACCURATE.
+ * *out receives the context (set to NULL on failure). */
+int hot_create(hot_ctx **out, int width, int height, double pitch_m, double wavelength_m,
+               double focal_m, void *cuda_stream);
+
+/* Sets the M traps (Sec. 4 "trap structure"): xyz_m is a host array of M*3 doubles
+ * (x_m, y_m, z_m) in metres, row per trap; w0 (host, M doubles > 0, or NULL for all 1) are
+ * the initial GSW weights.  1 <= M <= HOT_MAX_TRAPS, coordinates finite.  Builds the
+ * per-trap phase tables on the device (Eq. 2 reduced modulo 2 pi in FP64). */
+int hot_set_traps(hot_ctx *c, int M, const double *xyz_m, const double *w0);
+
+/* Replaces the GSW weights (host, M doubles > 0).  HOT_ESTATE before hot_set_traps. */
+int hot_set_weights(hot_ctx *c, const double *w);
+
+/* Sets the pixel phases phi_j (N = W*H float32 radians, row-major, any range):
+ * host memory (on_device = 0) or device memory (on_device = 1). */
+int hot_set_phase(hot_ctx *c, const float *phi, int on_device);
+
+/* Selects HOT_PREC_ACCURATE or HOT_PREC_FAST for the following calls. */
+int hot_set_precision(hot_ctx *c, int precision);
+
+/* Runs `iters` GSW iterations (Sec. 3, Fig. 2) from the current phases and weights:
+ * for k = 1..iters: V = F(phi) (Eq. 1); w_m <- w_m <|V|>/|V_m|; phi = arg of the
+ * back-projection with coefficients w_m V_m/|V_m|.  Then V = F(phi) of the final phase and
+ * its efficiency e and uniformity u (Eq. 4).  iters = 0 only evaluates F, e and u.
+ * Repeated calls continue from the state left by the previous one, so two calls with
+ * K1 and K2 iterations give the same phases, weights and fields as one call with K1 + K2.
+ * eff_out / unif_out (host, nullable): if either is non-NULL the call synchronises and
+ * writes them; otherwise it returns once the work is queued.  Readings where the paper
+ * is silent: if |V_m| < 1e-30 the unit field is taken as 1 and w_m is kept; arg(0) = 0.
+ * HOT_ESTATE before hot_set_traps; HOT_EINVAL if iters < 0. */
+int hot_gsw(hot_ctx *c, int iters, double *eff_out, double *unif_out);
+
+/* Writes the current phases (N pixels, row-major) to dst in format fmt (hot_format):
+ * float32 radians in (-pi, pi] or uint8 grey levels (Sec. 5: 256 levels linear in
+ * 0..2 pi, level 0 = phase 0, round to nearest).  dst is host (on_device = 0, the call
+ * synchronises) or device memory (on_device = 1, queued). */
+int hot_phase_out(hot_ctx *c, void *dst, int fmt, int on_device);
+
+/* Copies to host the trap fields V (2*M doubles, interleaved Re, Im) of the last forward
+ * evaluation (after hot_gsw: the fields of the final phase) and the current weights w
+ * (M doubles).  Either pointer may be NULL.  Synchronises.  HOT_ESTATE if no forward
+ * evaluation has run since the traps or phases were set. */
+int hot_get_fields(hot_ctx *c, double *V, double *w);
+
+/* Selects how hot_gsw issues its kernels: enable = 1 (default) replays a CUDA graph of the
+ * whole iters-iteration sequence, captured on first use for each (iters, precision) and
+ * dropped when the trap count changes; enable = 0 launches the kernels one by one.  The
+ * results are identical.  While profiling (hot_profile) kernels are always launched one by
+ * one. */
+int hot_use_graphs(hot_ctx *c, int enable);
+
+/* Waits for all work queued by the context. */
+int hot_sync(hot_ctx *c);
+
+/* Number of kernels the context has launched since creation (instrumentation). */
+long long hot_kernel_launches(const hot_ctx *c);
+
+/* Kernel classes reported by hot_profile_read. */
+typedef enum {
+  HOT_KERNEL_STEP = 0,    /* fused back-projection + forward field (one GSW iteration) */
+  HOT_KERNEL_FORWARD = 1, /* forward field only (Eq. 1 of the starting phases) */
+  HOT_KERNEL_FINISH = 2,  /* FP64 field reduction, weight update, Eq. 4 metrics */
+  HOT_KERNEL_OTHER = 3,   /* trap tables, 8-bit encoding */
+  HOT_KERNEL_KINDS = 4
+} hot_kernel_kind;
+
+/* Instrumentation: while enabled (enable = 1), CUDA events are recorded on the context's
+ * stream around every kernel the context launches.  hot_profile_read synchronises the
+ * stream and writes, per hot_kernel_kind, the summed device time in milliseconds (ms[4])
+ * and the number of launches (launches[4]) recorded since the last read, then clears the
+ * records.  Either array may be NULL.  Disabling drops unread records. */
+int hot_profile(hot_ctx *c, int enable);
+int hot_profile_read(hot_ctx *c, double *ms, long long *launches);
+
+/* Frees the context and its device buffers (NULL-safe). */
+void hot_destroy(hot_ctx *c);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char *hot_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOT_H */

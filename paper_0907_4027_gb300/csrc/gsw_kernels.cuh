@@ -1,0 +1,520 @@
+// gsw_kernels.cuh -- sm_103a kernels of the GSW hologram engine.
+//
+// Hot path (Sec. 3-4 of Bianchi & Di Leonardo): per iteration one fused kernel does the
+// back-projection of iteration k (phi_j = arg sum_m c_m e^{i Delta_j^m}) and the forward
+// field of iteration k+1 (per-tile partial sums of e^{i phi_j} e^{-i Delta_j^m}, Eq. 1);
+// a finish kernel (one block per trap) then reduces the partials of every trap in fixed
+// order in float-float arithmetic, and its last block updates the weights and forms the
+// next coefficients c_m = w_m V_m/|V_m|.  No FP64 runs per iteration.
+//
+// Per pair the kernels take exactly one complex exponential and accumulate it without a
+// complex multiply: the back-projection folds the phase of its coefficient into the argument,
+// S_j += w_m e^{i (Delta_j^m + arg V_m)}, and the forward field evaluates Eq. 1 as written,
+// V_m += e^{i (phi_j - Delta_j^m)}.
+//
+// Phase generation: Eq. 2 splits into a column part and a row part,
+//   Delta_j^m / 2pi = [a_m ix' + c_m ix'^2] + [b_m iy' + c_m iy'^2]
+// with a_m = x_m p/(lambda f), b_m = y_m p/(lambda f), c_m = z_m p^2/(2 lambda f^2),
+// ix' = ix - floor(W/2), iy' = iy - floor(H/2).  Each bracket is reduced modulo one turn
+// in FP64 once per (trap, column) and (trap, row) when the traps are set, and stored as
+// FP32.  Per (pixel, trap) pair the kernels add the two reduced parts (one FADD) and take
+// one complex exponential: sin.approx/cos.approx on the SFU (fast) or sincospif
+// (accurate).  Delta itself is never stored.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hot {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kTileW = 32;      // pixels per sub-tile row: one per lane
+constexpr int kRowsMax = 16;    // rows per sub-tile (each lane keeps one field per row)
+constexpr int kChunk = 128;     // traps whose tables are staged in shared memory at once
+constexpr float kTwoPi = 6.283185307179586f;
+
+// Work decomposition: the image is cut into 32-pixel-wide column strips; each strip's rows
+// are dealt out as contiguous runs to a fixed number of resident blocks (one wave), so that
+// every block gets the same number of row segments within one.  A block walks its run as
+// sub-tiles of at most kRowsMax rows.  Sub-tile t writes partial[m][t].
+struct SubTile {
+  int x0, y0, rows, pad;
+};
+
+struct StepArgs {
+  int W, H, M;
+  int n_sub;              // number of sub-tiles (columns of `partial`)
+  const SubTile *sub;     // [n_sub]
+  const int *first;       // [gridDim.x + 1]: block b processes sub-tiles first[b] .. first[b+1]-1
+  const float *X;         // [M][W] column phase parts (turns if accurate, radians if fast)
+  const float *Y;         // [M][H] row phase parts (same unit)
+  const float2 *coef;     // [M] back-projection coefficients (w_m, arg V_m in table units)
+  float *phi;             // [H*W] pixel phases, radians
+  float2 *partial;        // [M][n_sub] sub-tile sums of e^{i phi_j} e^{-i Delta_j^m}
+};
+
+__device__ __forceinline__ float sin_approx(float x) {
+  float y;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// cos and sin of an angle given in table units: radians (fast) or turns (accurate).
+template <bool FAST>
+__device__ __forceinline__ void cis(float x, float &co, float &si) {
+  if (FAST) {
+    si = sin_approx(x);  // |x| <= 3 pi here
+    co = cos_approx(x);
+  } else {
+    sincospif(2.0f * x, &si, &co);  // |x| <= 3/2 turns
+  }
+}
+
+// A pixel phase (radians) in table units: radians (fast) or turns (accurate).
+template <bool FAST>
+__device__ __forceinline__ float phase_units(float ph) {
+  return FAST ? ph : ph * 0.15915494309189535f;
+}
+
+// Shared memory of a block: the staged tables of one trap chunk (X for the sub-tile's 32
+// columns, Y for its rows, and the chunk's coefficients), the per-warp partial superpositions
+// of half a sub-tile's rows, and the pixel phases of the sub-tile.
+constexpr int kHalfRows = kRowsMax / 2;
+constexpr int kXsFloats = kChunk * kTileW;
+constexpr int kYsFloats = kChunk * kRowsMax;
+constexpr int kSmemBytes = (kXsFloats + kYsFloats) * 4 + kChunk * 8 + kWarps * kHalfRows * kTileW * 8 +
+                           kRowsMax * kTileW * 4;
+
+__host__ __device__ constexpr int step_smem_bytes(int, bool) { return kSmemBytes; }
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 4 : 0;  // 0 source bytes: the destination is zero-filled
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization
+// may start while the previous kernel of the stream is still running; grid_dependency_wait()
+// blocks until that kernel has finished and its writes are visible (a no-op otherwise), and
+// allow_dependents() lets the next kernel start its own prologue early.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+// Stages, with asynchronous copies (all in flight at once), the X (32 columns from x0) and Y
+// (rows y0 .. y0+rows-1) tables of traps [m0, m0+n), plus their coefficients when BACK.
+// The caller synchronises the block afterwards.
+template <bool BACK>
+__device__ __forceinline__ void stage_tables(const StepArgs &a, int m0, int n, const SubTile &st,
+                                             float *Xs, float *Ys, float2 *Cs, bool xy = true) {
+  for (int i = threadIdx.x; xy && i < n * kTileW; i += kThreads) {
+    const int k = i / kTileW, col = st.x0 + (i % kTileW);
+    const bool ok = col < a.W;
+    cp_async4(Xs + i, a.X + (ok ? (size_t)(m0 + k) * a.W + col : 0), ok);
+  }
+  for (int i = threadIdx.x; xy && i < n * kRowsMax; i += kThreads) {
+    const int k = i / kRowsMax, r = i % kRowsMax;
+    const bool ok = r < st.rows;
+    cp_async4(Ys + i, a.Y + (ok ? (size_t)(m0 + k) * a.H + st.y0 + r : 0), ok);
+  }
+  if (BACK)
+    for (int i = threadIdx.x; i < n; i += kThreads) cp_async8(Cs + i, a.coef + m0 + i);
+  cp_async_wait_all();
+}
+
+constexpr int kGroup = 8;  // traps reduced together over the lanes of a warp
+
+// Sums acc[0..7] over the 32 lanes of a warp with 18 shuffles instead of 8 x 5: at each of
+// the first three steps a lane keeps half of its traps and sends the other half to its
+// partner, so that after offsets 16, 8, 4 lane l holds trap (l >> 2) & 7 summed over 8 lanes;
+// two butterfly steps finish the sum.  Returns the total of trap (lane >> 2) & 7 (exact
+// same value in every run; lanes with (lane & 3) == 0 are the ones that store it).
+__device__ __forceinline__ float2 warp_reduce8(float2 (&acc)[kGroup], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const float2 send = b4 ? acc[i] : acc[i + 4], keep = b4 ? acc[i + 4] : acc[i];
+    acc[i].x = keep.x + __shfl_xor_sync(0xffffffffu, send.x, 16);
+    acc[i].y = keep.y + __shfl_xor_sync(0xffffffffu, send.y, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    const float2 send = b3 ? acc[i] : acc[i + 2], keep = b3 ? acc[i + 2] : acc[i];
+    acc[i].x = keep.x + __shfl_xor_sync(0xffffffffu, send.x, 8);
+    acc[i].y = keep.y + __shfl_xor_sync(0xffffffffu, send.y, 8);
+  }
+  {
+    const float2 send = b2 ? acc[0] : acc[1], keep = b2 ? acc[1] : acc[0];
+    acc[0].x = keep.x + __shfl_xor_sync(0xffffffffu, send.x, 4);
+    acc[0].y = keep.y + __shfl_xor_sync(0xffffffffu, send.y, 4);
+  }
+  float2 v = acc[0];
+  v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
+  v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
+  v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
+  v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
+  return v;
+}
+
+// Back-projection of traps [lo, hi) of the staged chunk onto the R rows of this lane:
+// S_r += w_m e^{i (X_m + Y_m(r) + arg V_m)}.  R is a compile-time row count.
+template <bool FAST, int R>
+__device__ __forceinline__ void back_traps(const float *Xs, const float *Ys, const float2 *Cs, int lo, int hi,
+                                           int lane, float2 (&S)[kRowsMax]) {
+  for (int k = lo; k < hi; k++) {
+    const float2 c = Cs[k];                      // (w_m, arg V_m)
+    const float xm = Xs[k * kTileW + lane] + c.y;
+    const float4 *yq = reinterpret_cast<const float4 *>(Ys + k * kRowsMax);
+#pragma unroll
+    for (int q = 0; q < (R + 3) / 4; q++) {
+      const float4 y4 = yq[q];
+      const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const int r = 4 * q + j;
+        if (r < R) {
+          float co, si;
+          cis<FAST>(xm + yy[j], co, si);
+          S[r].x = fmaf(c.x, co, S[r].x);
+          S[r].y = fmaf(c.x, si, S[r].y);
+        }
+      }
+    }
+  }
+}
+
+// Forward field (Eq. 1) of traps [lo, hi) of the staged chunk over the R rows of this lane's
+// column: sum_r e^{i (phi_r - X_m - Y_m(r))}, summed over the warp 8 traps at a time; writes
+// partial[(m0 + k) * stride + t].  ph holds the lane's pixel phases in table units; msk is 1
+// for a lane inside the image and 0 for a lane past its right edge.
+template <bool FAST, int R>
+__device__ __forceinline__ void forward_traps(const float *Xs, const float *Ys, int lo, int hi, int lane,
+                                              const float (&ph)[kRowsMax], float msk, float2 *partial,
+                                              size_t stride, int t, int m0) {
+  for (int g = lo; g < hi; g += kGroup) {
+    float2 acc[kGroup];
+#pragma unroll
+    for (int i = 0; i < kGroup; i++) {
+      acc[i] = make_float2(0.f, 0.f);
+      const int k = g + i;
+      if (k < hi) {
+        const float xm = Xs[k * kTileW + lane];
+        const float4 *yq = reinterpret_cast<const float4 *>(Ys + k * kRowsMax);
+#pragma unroll
+        for (int q = 0; q < (R + 3) / 4; q++) {
+          const float4 y4 = yq[q];
+          const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            const int r = 4 * q + j;
+            if (r < R) {
+              float co, si;
+              cis<FAST>((ph[r] - yy[j]) - xm, co, si);
+              acc[i].x = fmaf(msk, co, acc[i].x);
+              acc[i].y = fmaf(msk, si, acc[i].y);
+            }
+          }
+        }
+      }
+    }
+    const float2 v = warp_reduce8(acc, lane);
+    const int k = g + ((lane >> 2) & 7);
+    if ((lane & 3) == 0 && k < hi) partial[(size_t)(m0 + k) * stride + t] = v;
+  }
+}
+
+// Calls BODY with the compile-time constant R equal to the runtime value rows (1..kRowsMax).
+#define HOT_WITH_ROWS(rows, BODY)              \
+  switch (rows) {                              \
+    case 1: { constexpr int R = 1; BODY; } break;   \
+    case 2: { constexpr int R = 2; BODY; } break;   \
+    case 3: { constexpr int R = 3; BODY; } break;   \
+    case 4: { constexpr int R = 4; BODY; } break;   \
+    case 5: { constexpr int R = 5; BODY; } break;   \
+    case 6: { constexpr int R = 6; BODY; } break;   \
+    case 7: { constexpr int R = 7; BODY; } break;   \
+    case 8: { constexpr int R = 8; BODY; } break;   \
+    case 9: { constexpr int R = 9; BODY; } break;   \
+    case 10: { constexpr int R = 10; BODY; } break; \
+    case 11: { constexpr int R = 11; BODY; } break; \
+    case 12: { constexpr int R = 12; BODY; } break; \
+    case 13: { constexpr int R = 13; BODY; } break; \
+    case 14: { constexpr int R = 14; BODY; } break; \
+    case 15: { constexpr int R = 15; BODY; } break; \
+    default: { constexpr int R = 16; BODY; } break; \
+  }
+static_assert(kRowsMax == 16, "HOT_WITH_ROWS covers 1..16 rows");
+
+// Persistent blocks, one wave; the 8 warps of a block split the traps of each chunk.
+// BACK: back-projection with a.coef -> a.phi.  FWD: forward partials of the sub-tile phases.
+template <bool FAST, bool BACK, bool FWD>
+__global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *Xs = reinterpret_cast<float *>(smem_raw);
+  float *Ys = Xs + kXsFloats;
+  float2 *Cs = reinterpret_cast<float2 *>(Ys + kYsFloats);
+  float2 *Sp = Cs + kChunk;                                           // [kWarps][kHalfRows][kTileW]
+  float *Ps = reinterpret_cast<float *>(Sp + kWarps * kHalfRows * kTileW);  // [kRowsMax][kTileW] phases
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mc = a.M < kChunk ? a.M : kChunk;
+  const int nchunks = (a.M + mc - 1) / mc;
+  const int t_begin = a.first[blockIdx.x], t_end = a.first[blockIdx.x + 1];
+
+  // Prologue, overlapping the previous kernel: the trap tables are constant during hot_gsw,
+  // so the first chunk of the back-projection is staged before waiting for the coefficients.
+  allow_dependents();
+  bool prestaged = false;
+  if (BACK && t_begin < t_end) {
+    const SubTile st0 = a.sub[t_begin];
+    stage_tables<false>(a, 0, mc, st0, Xs, Ys, Cs);
+    prestaged = true;
+  }
+  grid_dependency_wait();
+
+  for (int t = t_begin; t < t_end; t++) {
+    const SubTile st = a.sub[t];
+    const int ix = st.x0 + lane;
+    const bool col_ok = ix < a.W;
+
+    if (BACK) {
+      float2 S[kRowsMax];
+#pragma unroll
+      for (int r = 0; r < kRowsMax; r++) S[r] = make_float2(0.f, 0.f);
+      for (int ch = 0; ch < nchunks; ch++) {
+        const int m0 = ch * mc, n = min(mc, a.M - m0);
+        __syncthreads();  // earlier readers of the tables are done
+        stage_tables<true>(a, m0, n, st, Xs, Ys, Cs, !prestaged);
+        prestaged = false;
+        __syncthreads();
+        const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
+        HOT_WITH_ROWS(st.rows, (back_traps<FAST, R>(Xs, Ys, Cs, lo, hi, lane, S)));
+      }
+      // Sum the 8 warps' superpositions, half of the rows at a time, in warp order.
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        if (h * kHalfRows >= st.rows) break;
+        __syncthreads();  // Sp and the phase rows are free
+#pragma unroll
+        for (int i = 0; i < kHalfRows; i++)
+          if (h * kHalfRows + i < st.rows) Sp[(warp * kHalfRows + i) * kTileW + lane] = S[h * kHalfRows + i];
+        __syncthreads();
+        if (warp < kHalfRows && h * kHalfRows + warp < st.rows) {
+          const int r = h * kHalfRows + warp;
+          float2 s = Sp[warp * kTileW + lane];
+#pragma unroll
+          for (int w = 1; w < kWarps; w++) {
+            const float2 q = Sp[(w * kHalfRows + warp) * kTileW + lane];
+            s.x += q.x;
+            s.y += q.y;
+          }
+          const float ph = atan2f(s.y, s.x);
+          if (col_ok) a.phi[(size_t)(st.y0 + r) * a.W + ix] = ph;
+          if (FWD) Ps[r * kTileW + lane] = phase_units<FAST>(ph);
+        }
+      }
+    } else if (FWD) {
+      __syncthreads();  // earlier readers of the phases and of the tables are done
+      for (int r = warp; r < st.rows; r += kWarps)
+        Ps[r * kTileW + lane] = col_ok ? phase_units<FAST>(a.phi[(size_t)(st.y0 + r) * a.W + ix]) : 0.0f;
+    }
+
+    if (FWD) {
+      __syncthreads();  // the phases are complete
+      float ph[kRowsMax];
+#pragma unroll
+      for (int r = 0; r < kRowsMax; r++) ph[r] = r < st.rows ? Ps[r * kTileW + lane] : 0.0f;
+      for (int ch = 0; ch < nchunks; ch++) {
+        const int m0 = ch * mc, n = min(mc, a.M - m0);
+        if (!BACK || nchunks > 1) {  // with one chunk the back-projection's tables are still staged
+          if (ch) __syncthreads();
+          stage_tables<false>(a, m0, n, st, Xs, Ys, Cs);
+          __syncthreads();
+        }
+        const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
+        HOT_WITH_ROWS(st.rows, (forward_traps<FAST, R>(Xs, Ys, lo, hi, lane, ph, col_ok ? 1.f : 0.f, a.partial,
+                                                       a.n_sub, t, m0)));
+      }
+    }
+  }
+}
+
+struct FinishArgs {
+  int M, n_tiles, update;
+  float inv_n;
+  float angle_units;      // 1 (radians) or 1/(2 pi) (turns): units of the tables
+  const float2 *partial;  // [M][n_tiles]
+  float4 *V;              // [M] out: V_m (Eq. 1) as float-float (hi.re, hi.im, lo.re, lo.im)
+  float *w;               // [M] in/out: GSW weights
+  float2 *coef;           // [M] out: (w_m, arg V_m) -- the coefficient w_m V_m/|V_m| in polar form
+  float *metrics;         // [2] out: e, u (Eq. 4)
+  float *amp;             // [M] scratch: |V_m|
+  float *arg;             // [M] scratch: arg V_m in table units (0 if |V_m| < 1e-30)
+  unsigned int *ticket;   // one counter, 0 between launches
+};
+
+constexpr int kFinishThreads = 256;
+
+// Float-float ("double-single") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
+// TwoSum (Knuth) and FastTwoSum (Dekker) give the exact rounding error of one addition.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (b.hi - bb);
+  const float e = err + (a.lo + b.lo);
+  const float hi = s + e;
+  return {hi, e - (hi - s)};
+}
+__device__ __forceinline__ ff ff_shfl_down(ff a, int o) {
+  return {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+}
+
+// Fixed-order float-float sum over the block; the result is valid in thread 0.
+__device__ __forceinline__ ff block_sum_ff(ff v, ff *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = ff_add(v, ff_shfl_down(v, o));
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  ff s = {0.f, 0.f};
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) s = ff_add(s, red[i]);
+  return s;
+}
+
+// Grid of M blocks.  Block m: V_m = (1/N) sum over tiles of the partials in float-float,
+// fixed order; |V_m| and V_m/|V_m|.  The last block to finish (ticket) forms <|V|>, updates
+// the weights (Sec. 3), the next coefficients c_m = w_m V_m/|V_m| and e, u (Eq. 4), reading
+// every trap in index order.
+__global__ void __launch_bounds__(kFinishThreads) gsw_finish_kernel(FinishArgs a) {
+  __shared__ ff red[kFinishThreads / 32];
+  __shared__ float rmx[kFinishThreads / 32], rmn[kFinishThreads / 32];
+  __shared__ float bcast;
+  __shared__ bool last;
+  const int m = blockIdx.x;
+  grid_dependency_wait();  // the partials of the step kernel
+  allow_dependents();
+  {
+    ff sr = {0.f, 0.f}, si = {0.f, 0.f};
+    const float2 *p = a.partial + (size_t)m * a.n_tiles;
+    for (int t = threadIdx.x; t < a.n_tiles; t += kFinishThreads) {
+      const float2 v = p[t];
+      sr = ff_add(sr, {v.x, 0.f});
+      si = ff_add(si, {v.y, 0.f});
+    }
+    sr = block_sum_ff(sr, red);
+    si = block_sum_ff(si, red);
+    if (threadIdx.x == 0) {
+      const float4 v = make_float4(sr.hi * a.inv_n, si.hi * a.inv_n, sr.lo * a.inv_n, si.lo * a.inv_n);
+      const float vr = v.x + v.z, vi = v.y + v.w;
+      const float am = sqrtf(vr * vr + vi * vi);
+      a.V[m] = v;
+      a.amp[m] = am;
+      a.arg[m] = am >= 1e-30f ? atan2f(vi, vr) * a.angle_units : 0.f;
+      __threadfence();
+      last = atomicAdd(a.ticket, 1u) == (unsigned)(a.M - 1);
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  ff sa = {0.f, 0.f}, si = {0.f, 0.f};
+  float mx = -1.f, mn = 3.0e38f;
+  for (int k = threadIdx.x; k < a.M; k += kFinishThreads) {
+    const float am = __ldcg(a.amp + k);
+    const float I = am * am;
+    sa = ff_add(sa, {am, 0.f});
+    si = ff_add(si, {I, 0.f});
+    mx = fmaxf(mx, I);
+    mn = fminf(mn, I);
+  }
+  sa = block_sum_ff(sa, red);
+  si = block_sum_ff(si, red);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rmx[threadIdx.x >> 5] = mx;
+    rmn[threadIdx.x >> 5] = mn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float X = -1.f, N = 3.0e38f;
+    for (int i = 0; i < kFinishThreads / 32; i++) {
+      X = fmaxf(X, rmx[i]);
+      N = fminf(N, rmn[i]);
+    }
+    bcast = (sa.hi + sa.lo) / (float)a.M;
+    a.metrics[0] = si.hi + si.lo;
+    a.metrics[1] = (X + N > 0.f) ? 1.f - (X - N) / (X + N) : 0.f;
+    *a.ticket = 0u;
+  }
+  __syncthreads();
+  const float mean = bcast;
+  for (int k = threadIdx.x; k < a.M; k += kFinishThreads) {
+    const float am = __ldcg(a.amp + k);
+    float wk = a.w[k];
+    if (a.update && am >= 1e-30f) {
+      wk = wk * mean / am;
+      a.w[k] = wk;
+    }
+    a.coef[k] = make_float2(wk, __ldcg(a.arg + k));
+  }
+}
+
+// Per (trap, column) and (trap, row) phase parts of Eq. 2 reduced modulo one turn in FP64.
+// abc: [M][3] = a_m, b_m, c_m in turns (see the file header).  Writes turns and radians.
+__global__ void build_tables_kernel(int W, int H, int M, const double *abc, float *Xt, float *Yt,
+                                    float *Xr, float *Yr) {
+  const long long total = (long long)M * (W + H);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(idx / (W + H)), i = (int)(idx % (W + H));
+    const double am = abc[3 * m], bm = abc[3 * m + 1], cm = abc[3 * m + 2];
+    double t;
+    if (i < W) {
+      const double q = (double)(i - W / 2);
+      t = fma(cm * q, q, am * q);
+    } else {
+      const double q = (double)((i - W) - H / 2);
+      t = fma(cm * q, q, bm * q);
+    }
+    t -= rint(t);  // [-1/2, 1/2] turns
+    const float tf = (float)t, rf = (float)(t * 6.283185307179586476925286766559);
+    if (i < W) {
+      Xt[(size_t)m * W + i] = tf;
+      Xr[(size_t)m * W + i] = rf;
+    } else {
+      Yt[(size_t)m * H + (i - W)] = tf;
+      Yr[(size_t)m * H + (i - W)] = rf;
+    }
+  }
+}
+
+// Sec. 5 encoding of the phases: uint8 g = rint(phi 256 / 2pi) mod 256 (FP32 decision).
+__global__ void quantize_kernel(const float *phi, unsigned char *g, long long n) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    const float q = rintf(phi[j] * (256.0f / kTwoPi));
+    g[j] = (unsigned char)(((int)q) & 255);
+  }
+}
+
+}  // namespace hot

@@ -1,0 +1,624 @@
+// hot.cu -- host runtime and C ABI (include/hot.h) of the GSW hologram engine.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/hot.h"
+#include "gsw_kernels.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define HOT_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(e_ == cudaErrorMemoryAllocation ? HOT_ENOMEM : HOT_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                   \
+  } while (0)
+
+template <typename T>
+int dalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return HOT_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? HOT_ENOMEM : HOT_ECUDA, "cudaMalloc(%zu B): %s",
+                count * sizeof(T), cudaGetErrorString(e));
+  }
+  return HOT_OK;
+}
+
+template <typename T>
+void dfree(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+}  // namespace
+
+struct hot_ctx {
+  int W = 0, H = 0;
+  double pitch = 0, lam = 0, focal = 0;
+  cudaStream_t st = nullptr;
+  int dev = 0;
+  int precision = HOT_PREC_ACCURATE;
+  // work schedule of the step kernels (see hot::SubTile)
+  int grid = 0, n_sub = 0;
+  hot::SubTile *sub = nullptr;  // [n_sub]
+  int *first = nullptr;         // [grid + 1]
+  int sched_smem_M = -1;        // M the schedule's occupancy was computed for
+  // state
+  float *phi = nullptr;  // [N]
+  int M = 0;
+  double *abc = nullptr;                                       // [M][3]
+  float *Xt = nullptr, *Yt = nullptr, *Xr = nullptr, *Yr = nullptr;  // tables
+  float *w = nullptr;                                          // [M]
+  float2 *coef = nullptr;                                      // [M]
+  float4 *V = nullptr;                                         // [M] float-float fields
+  float2 *partial = nullptr;                                   // [M][n_sub]
+  float *amp = nullptr;                                        // [M] scratch
+  float *arg = nullptr;                                        // [M] scratch
+  float *metrics = nullptr;                                    // [2]
+  unsigned int *ticket = nullptr;                              // finish-kernel counter
+  unsigned char *u8 = nullptr;                                 // [N] staging for host output
+  bool have_fields = false;
+  long long launches = 0;
+  // instrumentation
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  bool profiling = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> spare;
+  // CUDA graphs of whole hot_gsw(iters) launch sequences, keyed by (iters, precision)
+  struct Graph {
+    int iters, precision;
+    long long kernels;
+    cudaGraphExec_t exec;
+  };
+  bool use_graphs = true;
+  cudaStream_t cap = nullptr;  // capture stream (capture is not allowed on the legacy stream)
+  std::vector<Graph> graphs;
+};
+
+namespace {
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
+
+void drop_graphs(hot_ctx *c) {
+  for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
+void free_traps(hot_ctx *c) {
+  drop_graphs(c);
+  dfree(c->abc);
+  dfree(c->Xt);
+  dfree(c->Yt);
+  dfree(c->Xr);
+  dfree(c->Yr);
+  dfree(c->w);
+  dfree(c->coef);
+  dfree(c->V);
+  dfree(c->partial);
+  dfree(c->amp);
+  dfree(c->arg);
+  c->M = 0;
+  c->have_fields = false;
+}
+
+int check_launch(hot_ctx *c, const char *what) {
+  c->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(HOT_ECUDA, "launch of %s: %s", what, cudaGetErrorString(e));
+  return HOT_OK;
+}
+
+cudaEvent_t take_event(hot_ctx *c) {
+  if (!c->spare.empty()) {
+    cudaEvent_t e = c->spare.back();
+    c->spare.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void clear_records(hot_ctx *c) {
+  for (auto &r : c->recs) {
+    c->spare.push_back(r.a);
+    c->spare.push_back(r.b);
+  }
+  c->recs.clear();
+}
+
+// Brackets one kernel launch with events when profiling is on.
+struct Probe {
+  hot_ctx *c;
+  int kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Probe(hot_ctx *ctx, int k) : c(ctx), kind(k) {
+    if (!c->profiling) return;
+    a = take_event(c);
+    b = take_event(c);
+    if (a && b) cudaEventRecord(a, c->st);
+  }
+  ~Probe() {
+    if (!a || !b) return;
+    cudaEventRecord(b, c->st);
+    c->recs.push_back({kind, a, b});
+  }
+};
+
+// Launches kernel<<<grid, block, smem, c->st>>>(args...); with pdl, as a programmatic
+// dependent of the previous kernel in the stream (its prologue may overlap that kernel).
+template <typename... KArgs, typename... Args>
+void launch(hot_ctx *c, void (*kernel)(KArgs...), int grid, int block, int smem, bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c->st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <bool FAST, bool BACK, bool FWD>
+int launch_tile(hot_ctx *c, bool pdl) {
+  hot::StepArgs a;
+  a.W = c->W;
+  a.H = c->H;
+  a.M = c->M;
+  a.n_sub = c->n_sub;
+  a.sub = c->sub;
+  a.first = c->first;
+  a.X = FAST ? c->Xr : c->Xt;
+  a.Y = FAST ? c->Yr : c->Yt;
+  a.coef = c->coef;
+  a.phi = c->phi;
+  a.partial = c->partial;
+  const int smem = hot::step_smem_bytes(c->M, BACK);
+  Probe p(c, BACK && FWD ? HOT_KERNEL_STEP : FWD ? HOT_KERNEL_FORWARD : HOT_KERNEL_OTHER);
+  launch(c, hot::gsw_step_kernel<FAST, BACK, FWD>, c->grid, hot::kThreads, smem, pdl, a);
+  return check_launch(c, "gsw_step_kernel");
+}
+
+// Raises the dynamic shared-memory limit of every step-kernel variant to what M needs.
+int set_step_smem(int M) {
+  const int back = hot::step_smem_bytes(M, true), fwd = hot::step_smem_bytes(M, false);
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd));
+  return HOT_OK;
+}
+
+// One wave of persistent blocks (SMs x resident blocks of the fused kernel); the W/32 x H row
+// segments are dealt out in equal contiguous runs, cut into sub-tiles of <= kRowsMax rows.
+int build_schedule(hot_ctx *c) {
+  int rc = set_step_smem(c->M);
+  if (rc != HOT_OK) return rc;
+  int sms = 0, per_sm = 0;
+  HOT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+  HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_step_kernel<true, true, true>,
+                                                         hot::kThreads, hot::step_smem_bytes(c->M, true)));
+  if (per_sm < 1) per_sm = 1;
+  const int strips = (c->W + hot::kTileW - 1) / hot::kTileW;
+  const long long U = (long long)strips * c->H;
+  const int G = (int)std::min<long long>((long long)sms * per_sm, U);
+  std::vector<hot::SubTile> sub;
+  std::vector<int> first(G + 1);
+  for (int b = 0; b < G; b++) {
+    first[b] = (int)sub.size();
+    long long s = U * b / G;
+    const long long s1 = U * (b + 1) / G;
+    while (s < s1) {
+      const int strip = (int)(s / c->H), row = (int)(s % c->H);
+      const long long run_end = std::min<long long>(s1, (long long)(strip + 1) * c->H);
+      const int L = (int)(run_end - s);
+      const int nsub = (L + hot::kRowsMax - 1) / hot::kRowsMax;
+      for (int i = 0; i < nsub; i++) {
+        const int r0 = row + (int)((long long)L * i / nsub), r1 = row + (int)((long long)L * (i + 1) / nsub);
+        sub.push_back({strip * hot::kTileW, r0, r1 - r0, 0});
+      }
+      s = run_end;
+    }
+  }
+  first[G] = (int)sub.size();
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  dfree(c->sub);
+  dfree(c->first);
+  c->grid = 0;
+  c->n_sub = 0;
+  rc = dalloc(&c->sub, sub.size());
+  if (rc == HOT_OK) rc = dalloc(&c->first, first.size());
+  if (rc != HOT_OK) return rc;
+  HOT_CUDA(cudaMemcpy(c->sub, sub.data(), sizeof(hot::SubTile) * sub.size(), cudaMemcpyHostToDevice));
+  HOT_CUDA(cudaMemcpy(c->first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice));
+  c->grid = G;
+  c->n_sub = (int)sub.size();
+  return HOT_OK;
+}
+
+int launch_step(hot_ctx *c, bool back, bool fwd, bool pdl) {
+  const bool fast = c->precision == HOT_PREC_FAST;
+  if (back && fwd) return fast ? launch_tile<true, true, true>(c, pdl) : launch_tile<false, true, true>(c, pdl);
+  if (back) return fast ? launch_tile<true, true, false>(c, pdl) : launch_tile<false, true, false>(c, pdl);
+  return fast ? launch_tile<true, false, true>(c, pdl) : launch_tile<false, false, true>(c, pdl);
+}
+
+int launch_finish(hot_ctx *c, bool update) {
+  hot::FinishArgs a;
+  a.M = c->M;
+  a.n_tiles = c->n_sub;
+  a.update = update ? 1 : 0;
+  a.inv_n = (float)(1.0 / ((double)c->W * (double)c->H));
+  a.partial = c->partial;
+  a.V = c->V;
+  a.w = c->w;
+  a.coef = c->coef;
+  a.metrics = c->metrics;
+  a.amp = c->amp;
+  a.arg = c->arg;
+  a.angle_units = c->precision == HOT_PREC_FAST ? 1.0f : 0.15915494309189535f;
+  a.ticket = c->ticket;
+  Probe p(c, HOT_KERNEL_FINISH);
+  launch(c, hot::gsw_finish_kernel, c->M, hot::kFinishThreads, 0, !c->profiling, a);
+  return check_launch(c, "gsw_finish_kernel");
+}
+
+// The launch sequence of hot_gsw(iters) on c->st.
+// Inside the sequence every kernel is a programmatic dependent of the one before it (except
+// when profiling, where events separate the launches); the first one waits normally for
+// whatever preceded hot_gsw in the stream (trap tables, phases).
+int enqueue_gsw(hot_ctx *c, int iters) {
+  const bool pdl = !c->profiling;
+  int rc = launch_step(c, false, true, false);  // V = F(phi)
+  if (rc == HOT_OK) rc = launch_finish(c, iters > 0);
+  for (int k = 1; k <= iters && rc == HOT_OK; k++) {
+    rc = launch_step(c, true, true, pdl);         // phi^k = B(c^k); partials of F(phi^k)
+    if (rc == HOT_OK) rc = launch_finish(c, k < iters);
+  }
+  return rc;
+}
+
+// Replays (capturing on first use) the graph of enqueue_gsw(iters).
+int launch_gsw_graph(hot_ctx *c, int iters) {
+  for (auto &g : c->graphs)
+    if (g.iters == iters && g.precision == c->precision) {
+      HOT_CUDA(cudaGraphLaunch(g.exec, c->st));
+      c->launches += g.kernels;
+      return HOT_OK;
+    }
+  if (!c->cap) HOT_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  if (c->graphs.size() >= 8) {
+    cudaGraphExecDestroy(c->graphs.front().exec);
+    c->graphs.erase(c->graphs.begin());
+  }
+  cudaStream_t user = c->st;
+  const long long before = c->launches;
+  HOT_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  c->st = c->cap;
+  int rc = enqueue_gsw(c, iters);
+  c->st = user;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &graph);
+  const long long kernels = c->launches - before;
+  c->launches = before;
+  if (rc != HOT_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(HOT_ECUDA, "hot_gsw: graph capture: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(HOT_ECUDA, "hot_gsw: graph instantiation: %s", cudaGetErrorString(e));
+  c->graphs.push_back({iters, c->precision, kernels, exec});
+  HOT_CUDA(cudaGraphLaunch(exec, c->st));
+  c->launches += kernels;
+  return HOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hot_last_error(void) { return g_err; }
+
+int hot_create(hot_ctx **out, int width, int height, double pitch_m, double wavelength_m,
+               double focal_m, void *cuda_stream) {
+  g_err[0] = 0;
+  if (!out) return fail(HOT_EINVAL, "hot_create: out is NULL");
+  *out = nullptr;
+  if (width < 1 || height < 1 || (long long)width * height >= (1LL << 31))
+    return fail(HOT_EINVAL, "hot_create: invalid size %d x %d", width, height);
+  if (!finite_pos(pitch_m) || !finite_pos(wavelength_m) || !finite_pos(focal_m))
+    return fail(HOT_EINVAL, "hot_create: pitch, wavelength and focal length must be finite and > 0");
+  hot_ctx *c = new (std::nothrow) hot_ctx;
+  if (!c) return fail(HOT_ENOMEM, "hot_create: out of host memory");
+  c->W = width;
+  c->H = height;
+  c->pitch = pitch_m;
+  c->lam = wavelength_m;
+  c->focal = focal_m;
+  c->st = static_cast<cudaStream_t>(cuda_stream);
+  int rc = HOT_OK;
+  cudaError_t e = cudaGetDevice(&c->dev);
+  if (e != cudaSuccess) rc = fail(HOT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  const size_t N = (size_t)width * height;
+  if (rc == HOT_OK) rc = dalloc(&c->phi, N);
+  if (rc == HOT_OK) rc = dalloc(&c->metrics, 2);
+  if (rc == HOT_OK) rc = dalloc(&c->ticket, 1);
+  if (rc == HOT_OK) {
+    e = cudaMemsetAsync(c->phi, 0, N * sizeof(float), c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ticket, 0, sizeof(unsigned int), c->st);
+    if (e != cudaSuccess) rc = fail(HOT_ECUDA, "hot_create: %s", cudaGetErrorString(e));
+  }
+  if (rc != HOT_OK) {
+    hot_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return HOT_OK;
+}
+
+void hot_destroy(hot_ctx *c) {
+  if (!c) return;
+  if (c->phi || c->M) cudaStreamSynchronize(c->st);
+  drop_graphs(c);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  clear_records(c);
+  for (cudaEvent_t e : c->spare) cudaEventDestroy(e);
+  c->spare.clear();
+  free_traps(c);
+  dfree(c->phi);
+  dfree(c->sub);
+  dfree(c->first);
+  dfree(c->metrics);
+  dfree(c->ticket);
+  dfree(c->u8);
+  delete c;
+}
+
+int hot_set_traps(hot_ctx *c, int M, const double *xyz_m, const double *w0) {
+  if (!c) return fail(HOT_EINVAL, "hot_set_traps: NULL context");
+  if (M < 1 || M > HOT_MAX_TRAPS) return fail(HOT_EINVAL, "hot_set_traps: M = %d not in [1, %d]", M, HOT_MAX_TRAPS);
+  if (!xyz_m) return fail(HOT_EINVAL, "hot_set_traps: xyz is NULL");
+  for (int i = 0; i < 3 * M; i++)
+    if (!std::isfinite(xyz_m[i])) return fail(HOT_EINVAL, "hot_set_traps: coordinate %d not finite", i);
+  if (w0)
+    for (int m = 0; m < M; m++)
+      if (!finite_pos(w0[m])) return fail(HOT_EINVAL, "hot_set_traps: weight %d not finite and > 0", m);
+  // Eq. 2 in turns per pixel index: a = x p/(lambda f), b = y p/(lambda f), c = z p^2/(2 lambda f^2)
+  double *abc = static_cast<double *>(malloc(sizeof(double) * 3 * M));
+  float *wh = static_cast<float *>(malloc(sizeof(float) * M));
+  if (!abc || !wh) {
+    free(abc);
+    free(wh);
+    return fail(HOT_ENOMEM, "hot_set_traps: out of host memory");
+  }
+  const double lin = c->pitch / (c->lam * c->focal);
+  const double quad = c->pitch * c->pitch / (2.0 * c->lam * c->focal * c->focal);
+  for (int m = 0; m < M; m++) {
+    abc[3 * m] = xyz_m[3 * m] * lin;
+    abc[3 * m + 1] = xyz_m[3 * m + 1] * lin;
+    abc[3 * m + 2] = xyz_m[3 * m + 2] * quad;
+    wh[m] = w0 ? (float)w0[m] : 1.0f;
+  }
+  int rc = HOT_OK;
+  if (M != c->M) {
+    cudaStreamSynchronize(c->st);
+    free_traps(c);
+    c->M = M;
+    rc = build_schedule(c);
+    c->M = 0;
+    if (rc != HOT_OK) {
+      free(abc);
+      free(wh);
+      return rc;
+    }
+    const size_t nt = (size_t)c->n_sub;
+    rc = dalloc(&c->abc, 3 * (size_t)M);
+    if (rc == HOT_OK) rc = dalloc(&c->Xt, (size_t)M * c->W);
+    if (rc == HOT_OK) rc = dalloc(&c->Xr, (size_t)M * c->W);
+    if (rc == HOT_OK) rc = dalloc(&c->Yt, (size_t)M * c->H);
+    if (rc == HOT_OK) rc = dalloc(&c->Yr, (size_t)M * c->H);
+    if (rc == HOT_OK) rc = dalloc(&c->w, M);
+    if (rc == HOT_OK) rc = dalloc(&c->coef, M);
+    if (rc == HOT_OK) rc = dalloc(&c->V, M);
+    if (rc == HOT_OK) rc = dalloc(&c->partial, (size_t)M * nt);
+    if (rc == HOT_OK) rc = dalloc(&c->amp, M);
+    if (rc == HOT_OK) rc = dalloc(&c->arg, M);
+    if (rc != HOT_OK) {
+      free_traps(c);
+      free(abc);
+      free(wh);
+      return rc;
+    }
+    c->M = M;
+  }
+  cudaError_t e = cudaMemcpyAsync(c->abc, abc, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->w, wh, sizeof(float) * M, cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);  // host buffers are released below
+  free(abc);
+  free(wh);
+  if (e != cudaSuccess) return fail(HOT_ECUDA, "hot_set_traps: %s", cudaGetErrorString(e));
+  const long long total = (long long)M * (c->W + c->H);
+  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  Probe p(c, HOT_KERNEL_OTHER);
+  hot::build_tables_kernel<<<blocks, 256, 0, c->st>>>(c->W, c->H, M, c->abc, c->Xt, c->Yt, c->Xr, c->Yr);
+  c->have_fields = false;
+  return check_launch(c, "build_tables_kernel");
+}
+
+int hot_set_weights(hot_ctx *c, const double *w) {
+  if (!c || !w) return fail(HOT_EINVAL, "hot_set_weights: NULL argument");
+  if (!c->M) return fail(HOT_ESTATE, "hot_set_weights: no traps set");
+  std::vector<float> wf(c->M);
+  for (int m = 0; m < c->M; m++) {
+    if (!finite_pos(w[m])) return fail(HOT_EINVAL, "hot_set_weights: weight %d not finite and > 0", m);
+    wf[m] = (float)w[m];
+  }
+  HOT_CUDA(cudaMemcpyAsync(c->w, wf.data(), sizeof(float) * c->M, cudaMemcpyHostToDevice, c->st));
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  return HOT_OK;
+}
+
+int hot_set_phase(hot_ctx *c, const float *phi, int on_device) {
+  if (!c || !phi) return fail(HOT_EINVAL, "hot_set_phase: NULL argument");
+  const size_t bytes = sizeof(float) * (size_t)c->W * c->H;
+  if (on_device) {
+    HOT_CUDA(cudaMemcpyAsync(c->phi, phi, bytes, cudaMemcpyDeviceToDevice, c->st));
+  } else {
+    HOT_CUDA(cudaMemcpyAsync(c->phi, phi, bytes, cudaMemcpyHostToDevice, c->st));
+    HOT_CUDA(cudaStreamSynchronize(c->st));
+  }
+  c->have_fields = false;
+  return HOT_OK;
+}
+
+int hot_set_precision(hot_ctx *c, int precision) {
+  if (!c) return fail(HOT_EINVAL, "hot_set_precision: NULL context");
+  if (precision != HOT_PREC_ACCURATE && precision != HOT_PREC_FAST)
+    return fail(HOT_EINVAL, "hot_set_precision: unknown mode %d", precision);
+  c->precision = precision;
+  return HOT_OK;
+}
+
+int hot_gsw(hot_ctx *c, int iters, double *eff_out, double *unif_out) {
+  if (!c) return fail(HOT_EINVAL, "hot_gsw: NULL context");
+  if (iters < 0) return fail(HOT_EINVAL, "hot_gsw: iters = %d < 0", iters);
+  if (!c->M) return fail(HOT_ESTATE, "hot_gsw: no traps set");
+  const int rc = (c->use_graphs && !c->profiling) ? launch_gsw_graph(c, iters) : enqueue_gsw(c, iters);
+  if (rc != HOT_OK) return rc;
+  c->have_fields = true;
+  if (eff_out || unif_out) {
+    float m[2];
+    HOT_CUDA(cudaMemcpyAsync(m, c->metrics, sizeof m, cudaMemcpyDeviceToHost, c->st));
+    HOT_CUDA(cudaStreamSynchronize(c->st));
+    if (eff_out) *eff_out = m[0];
+    if (unif_out) *unif_out = m[1];
+  }
+  return HOT_OK;
+}
+
+int hot_phase_out(hot_ctx *c, void *dst, int fmt, int on_device) {
+  if (!c || !dst) return fail(HOT_EINVAL, "hot_phase_out: NULL argument");
+  if (fmt != HOT_FMT_F32 && fmt != HOT_FMT_U8) return fail(HOT_EINVAL, "hot_phase_out: unknown format %d", fmt);
+  const size_t N = (size_t)c->W * c->H;
+  if (fmt == HOT_FMT_F32) {
+    HOT_CUDA(cudaMemcpyAsync(dst, c->phi, N * sizeof(float),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+  } else {
+    unsigned char *g = static_cast<unsigned char *>(dst);
+    if (!on_device) {
+      if (!c->u8) {
+        int rc = dalloc(&c->u8, N);
+        if (rc != HOT_OK) return rc;
+      }
+      g = c->u8;
+    }
+    const int blocks = (int)(((long long)N + 255) / 256 < 8192 ? ((long long)N + 255) / 256 : 8192);
+    int rc;
+    {
+      Probe p(c, HOT_KERNEL_OTHER);
+      hot::quantize_kernel<<<blocks, 256, 0, c->st>>>(c->phi, g, (long long)N);
+      rc = check_launch(c, "quantize_kernel");
+    }
+    if (rc != HOT_OK) return rc;
+    if (!on_device) HOT_CUDA(cudaMemcpyAsync(dst, c->u8, N, cudaMemcpyDeviceToHost, c->st));
+  }
+  if (!on_device) HOT_CUDA(cudaStreamSynchronize(c->st));
+  return HOT_OK;
+}
+
+int hot_get_fields(hot_ctx *c, double *V, double *w) {
+  if (!c) return fail(HOT_EINVAL, "hot_get_fields: NULL context");
+  if (!c->M) return fail(HOT_ESTATE, "hot_get_fields: no traps set");
+  if (V && !c->have_fields) return fail(HOT_ESTATE, "hot_get_fields: no forward evaluation since the last change");
+  std::vector<float4> vf(V ? c->M : 0);
+  std::vector<float> wf(w ? c->M : 0);
+  if (V) HOT_CUDA(cudaMemcpyAsync(vf.data(), c->V, sizeof(float4) * c->M, cudaMemcpyDeviceToHost, c->st));
+  if (w) HOT_CUDA(cudaMemcpyAsync(wf.data(), c->w, sizeof(float) * c->M, cudaMemcpyDeviceToHost, c->st));
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  for (int m = 0; V && m < c->M; m++) {  // float-float -> double
+    V[2 * m] = (double)vf[m].x + (double)vf[m].z;
+    V[2 * m + 1] = (double)vf[m].y + (double)vf[m].w;
+  }
+  for (int m = 0; w && m < c->M; m++) w[m] = wf[m];
+  return HOT_OK;
+}
+
+int hot_sync(hot_ctx *c) {
+  if (!c) return fail(HOT_EINVAL, "hot_sync: NULL context");
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  return HOT_OK;
+}
+
+long long hot_kernel_launches(const hot_ctx *c) { return c ? c->launches : 0; }
+
+int hot_use_graphs(hot_ctx *c, int enable) {
+  if (!c) return fail(HOT_EINVAL, "hot_use_graphs: NULL context");
+  c->use_graphs = enable != 0;
+  return HOT_OK;
+}
+
+int hot_profile(hot_ctx *c, int enable) {
+  if (!c) return fail(HOT_EINVAL, "hot_profile: NULL context");
+  if (!enable && c->profiling) {
+    HOT_CUDA(cudaStreamSynchronize(c->st));
+    clear_records(c);
+  }
+  c->profiling = enable != 0;
+  return HOT_OK;
+}
+
+int hot_profile_read(hot_ctx *c, double *ms, long long *launches) {
+  if (!c) return fail(HOT_EINVAL, "hot_profile_read: NULL context");
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  double t[HOT_KERNEL_KINDS] = {0, 0, 0, 0};
+  long long n[HOT_KERNEL_KINDS] = {0, 0, 0, 0};
+  for (auto &r : c->recs) {
+    float x = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&x, r.a, r.b);
+    if (e != cudaSuccess) {
+      clear_records(c);
+      return fail(HOT_ECUDA, "hot_profile_read: %s", cudaGetErrorString(e));
+    }
+    t[r.kind] += x;
+    n[r.kind] += 1;
+  }
+  clear_records(c);
+  for (int k = 0; k < HOT_KERNEL_KINDS; k++) {
+    if (ms) ms[k] = t[k];
+    if (launches) launches[k] = n[k];
+  }
+  return HOT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+"""ctypes binding of the C ABI in include/hot.h (argument marshalling only).
+
+Every computation runs in libhot.so's CUDA kernels.  Importing this module loads the
+library and raises ImportError if it has not been built (``__graft_entry__.build()`` or
+``python -m paper_0907_4027_gb300._build``): there is no CPU fallback.
+
+Module-level functions carry the C names (``hot_create`` ... ``hot_last_error``) and take
+numpy arrays for host memory or CUDA tensors (anything with ``data_ptr()``) for device
+memory.  ``Hologram`` is a small convenience class over them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhot.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is missing: build it with __graft_entry__.build() "
+                      "(the engine has no CPU fallback)")
+lib = ctypes.CDLL(_LIB_PATH)
+
+HOT_OK, HOT_EINVAL, HOT_ENOMEM, HOT_ECUDA, HOT_ETIMEOUT, HOT_ESTATE = 0, -1, -2, -3, -4, -5
+HOT_PREC_ACCURATE, HOT_PREC_FAST = 0, 1
+HOT_FMT_F32, HOT_FMT_U8 = 0, 1
+HOT_MAX_TRAPS = 4096
+_STATUS = {0: "HOT_OK", -1: "HOT_EINVAL", -2: "HOT_ENOMEM", -3: "HOT_ECUDA", -4: "HOT_ETIMEOUT",
+           -5: "HOT_ESTATE"}
+
+_c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+# Every symbol declared in include/hot.h with its C signature.
+SIGNATURES = {
+    "hot_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _c_int, _c_double, _c_double, _c_double, _vp]),
+    "hot_set_traps": (_c_int, [_vp, _c_int, _vp, _vp]),
+    "hot_set_weights": (_c_int, [_vp, _vp]),
+    "hot_set_phase": (_c_int, [_vp, _vp, _c_int]),
+    "hot_set_precision": (_c_int, [_vp, _c_int]),
+    "hot_gsw": (_c_int, [_vp, _c_int, _dp, _dp]),
+    "hot_phase_out": (_c_int, [_vp, _vp, _c_int, _c_int]),
+    "hot_get_fields": (_c_int, [_vp, _vp, _vp]),
+    "hot_sync": (_c_int, [_vp]),
+    "hot_kernel_launches": (ctypes.c_longlong, [_vp]),
+    "hot_use_graphs": (_c_int, [_vp, _c_int]),
+    "hot_profile": (_c_int, [_vp, _c_int]),
+    "hot_profile_read": (_c_int, [_vp, _vp, _vp]),
+    "hot_destroy": (None, [_vp]),
+    "hot_last_error": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in SIGNATURES.items():
+    _fn = getattr(lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class HotError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib.hot_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
+
+
+def _ok(rc: int, where: str) -> int:
+    if rc != HOT_OK:
+        raise HotError(rc, where)
+    return rc
+
+
+def _host_ptr(a: np.ndarray, dtype) -> tuple:
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(_vp)
+
+
+def _is_device(x) -> bool:
+    return hasattr(x, "data_ptr") and getattr(x, "is_cuda", False)
+
+
+# ---- C-named wrappers -------------------------------------------------------------
+
+def hot_last_error() -> str:
+    return lib.hot_last_error().decode(errors="replace")
+
+
+def hot_create(width: int, height: int, pitch_m: float, wavelength_m: float, focal_m: float,
+               cuda_stream: int | None = None) -> int:
+    h = _vp()
+    _ok(lib.hot_create(ctypes.byref(h), int(width), int(height), float(pitch_m), float(wavelength_m),
+                       float(focal_m), _vp(cuda_stream or 0)), "hot_create")
+    return h.value
+
+
+def hot_set_traps(ctx: int, xyz_m, w0=None) -> None:
+    xyz, p = _host_ptr(np.asarray(xyz_m).reshape(-1, 3), np.float64)
+    wp = None
+    if w0 is not None:
+        w0, wp = _host_ptr(np.asarray(w0).reshape(-1), np.float64)
+        assert w0.size == len(xyz)
+    _ok(lib.hot_set_traps(_vp(ctx), len(xyz), p, wp), "hot_set_traps")
+
+
+def hot_set_weights(ctx: int, w) -> None:
+    w, p = _host_ptr(np.asarray(w).reshape(-1), np.float64)
+    _ok(lib.hot_set_weights(_vp(ctx), p), "hot_set_weights")
+
+
+def hot_set_phase(ctx: int, phi) -> None:
+    """phi: host array (N,) or a CUDA float32 tensor of N elements."""
+    if _is_device(phi):
+        _ok(lib.hot_set_phase(_vp(ctx), _vp(phi.data_ptr()), 1), "hot_set_phase")
+    else:
+        a, p = _host_ptr(np.asarray(phi).reshape(-1), np.float32)
+        _ok(lib.hot_set_phase(_vp(ctx), p, 0), "hot_set_phase")
+
+
+def hot_set_precision(ctx: int, precision) -> None:
+    if isinstance(precision, str):
+        precision = {"accurate": HOT_PREC_ACCURATE, "fast": HOT_PREC_FAST}[precision]
+    _ok(lib.hot_set_precision(_vp(ctx), int(precision)), "hot_set_precision")
+
+
+def hot_gsw(ctx: int, iters: int, metrics: bool = True):
+    """Runs iters GSW iterations; returns (e, u) if metrics else None (queued only)."""
+    if metrics:
+        e, u = ctypes.c_double(), ctypes.c_double()
+        _ok(lib.hot_gsw(_vp(ctx), int(iters), ctypes.byref(e), ctypes.byref(u)), "hot_gsw")
+        return e.value, u.value
+    _ok(lib.hot_gsw(_vp(ctx), int(iters), None, None), "hot_gsw")
+    return None
+
+
+def hot_phase_out(ctx: int, dst, fmt: int, n: int | None = None):
+    """dst: CUDA tensor (filled in stream order) or None -> returns a new host array of n."""
+    if _is_device(dst):
+        _ok(lib.hot_phase_out(_vp(ctx), _vp(dst.data_ptr()), int(fmt), 1), "hot_phase_out")
+        return dst
+    if dst is None:
+        dst = np.empty(int(n), dtype=np.float32 if fmt == HOT_FMT_F32 else np.uint8)
+    _ok(lib.hot_phase_out(_vp(ctx), dst.ctypes.data_as(_vp), int(fmt), 0), "hot_phase_out")
+    return dst
+
+
+def hot_get_fields(ctx: int, M: int):
+    V = np.empty(2 * M)
+    w = np.empty(M)
+    _ok(lib.hot_get_fields(_vp(ctx), V.ctypes.data_as(_vp), w.ctypes.data_as(_vp)), "hot_get_fields")
+    return V[0::2] + 1j * V[1::2], w
+
+
+def hot_sync(ctx: int) -> None:
+    _ok(lib.hot_sync(_vp(ctx)), "hot_sync")
+
+
+def hot_kernel_launches(ctx: int) -> int:
+    return int(lib.hot_kernel_launches(_vp(ctx)))
+
+
+HOT_KERNEL_STEP, HOT_KERNEL_FORWARD, HOT_KERNEL_FINISH, HOT_KERNEL_OTHER = 0, 1, 2, 3
+KERNEL_KINDS = ("step", "forward", "finish", "other")
+
+
+def hot_use_graphs(ctx: int, enable: bool) -> None:
+    _ok(lib.hot_use_graphs(_vp(ctx), int(bool(enable))), "hot_use_graphs")
+
+
+def hot_profile(ctx: int, enable: bool) -> None:
+    _ok(lib.hot_profile(_vp(ctx), int(bool(enable))), "hot_profile")
+
+
+def hot_profile_read(ctx: int) -> dict:
+    """{kind: (total_ms, launches)} since the last read (synchronises)."""
+    ms = np.zeros(4)
+    n = np.zeros(4, dtype=np.int64)
+    _ok(lib.hot_profile_read(_vp(ctx), ms.ctypes.data_as(_vp), n.ctypes.data_as(_vp)), "hot_profile_read")
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def hot_destroy(ctx: int) -> None:
+    lib.hot_destroy(_vp(ctx))
+
+
+# ---- convenience class -------------------------------------------------------------
+
+class Hologram:
+    """One GSW context: a W x H SLM with the given optics (metres)."""
+
+    def __init__(self, W: int, H: int, pitch: float, wavelength: float, focal: float,
+                 stream: int | None = None, precision: str = "accurate"):
+        self.W, self.H, self.M = int(W), int(H), 0
+        self.ctx = hot_create(W, H, pitch, wavelength, focal, stream)
+        hot_set_precision(self.ctx, precision)
+
+    @classmethod
+    def from_workload(cls, wl, stream: int | None = None):
+        h = cls(wl.W, wl.H, wl.pitch, wl.wavelength, wl.focal, stream, wl.precision)
+        h.set_traps(wl.xyz, wl.w0)
+        h.set_phase(wl.phi0)
+        return h
+
+    @property
+    def N(self) -> int:
+        return self.W * self.H
+
+    def set_traps(self, xyz, w0=None):
+        hot_set_traps(self.ctx, xyz, w0)
+        self.M = int(np.asarray(xyz).size // 3)
+
+    def set_weights(self, w):
+        hot_set_weights(self.ctx, w)
+
+    def set_phase(self, phi):
+        hot_set_phase(self.ctx, phi)
+
+    def set_precision(self, precision):
+        hot_set_precision(self.ctx, precision)
+
+    def gsw(self, iters: int, metrics: bool = True):
+        return hot_gsw(self.ctx, iters, metrics)
+
+    def phase(self, fmt: str = "f32", out=None):
+        f = HOT_FMT_F32 if fmt == "f32" else HOT_FMT_U8
+        return hot_phase_out(self.ctx, out, f, self.N)
+
+    def fields(self):
+        return hot_get_fields(self.ctx, self.M)
+
+    def sync(self):
+        hot_sync(self.ctx)
+
+    def use_graphs(self, enable: bool = True):
+        hot_use_graphs(self.ctx, enable)
+
+    def profile(self, enable: bool = True):
+        hot_profile(self.ctx, enable)
+
+    def profile_read(self) -> dict:
+        return hot_profile_read(self.ctx)
+
+    @property
+    def launches(self) -> int:
+        return hot_kernel_launches(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            hot_destroy(self.ctx)
+            self.ctx = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
