@@ -143,6 +143,37 @@ void hot_destroy(hot_ctx *c);
 /* Text of the last error on the calling thread ("" if none). */
 const char *hot_last_error(void);
 
+/* ---- allocation-free evaluation of the trap fields ---------------------------------------
+ * The paper has no counterpart of this entry point; it exists for callers that must not
+ * allocate device memory: a real-time hologram loop whose memory is planned once up front,
+ * code whose device memory is owned by an external pool or allocator, or hosts that forbid
+ * cudaMalloc/cudaFree after start-up.  Every other entry point allocates in its context.
+ *
+ * hot_field_noalloc computes V_m = (1/N) sum_j exp(i (phi_j - Delta_j^m)) (the same forward
+ * field that hot_gsw(c, 0, ...) evaluates for a context) and, if eu is not NULL, e and u of
+ * Eq. 4.  It calls no cudaMalloc, cudaFree or other allocating routine: its working memory
+ * (trap tables, work schedule, per-tile partial sums, reduction counters) lives in one
+ * file-scope __device__ array of HOT_NOALLOC_SCRATCH_BYTES that every GPU which loads the
+ * library holds until the process exits.
+ *   width, height, pitch_m, wavelength_m, focal_m: as for hot_create.
+ *   M, xyz_m: trap count and DEVICE array of M*3 doubles (x_m, y_m, z_m) in metres.
+ *   phi: DEVICE array of width*height float32 phases (radians), row-major.
+ *   precision: HOT_PREC_ACCURATE or HOT_PREC_FAST.
+ *   V: DEVICE output, 2*M doubles interleaved (Re, Im).  eu: DEVICE output of 2 doubles
+ *   (e, u) or NULL.  cuda_stream: a cudaStream_t or NULL.
+ * Work is queued on cuda_stream; the host reads nothing back.  Sizes whose working memory
+ * exceeds the scratch array (roughly 8 M (W + H) + 8 M (W/32 * H / 16 + 2 * SMs) bytes) are
+ * rejected with HOT_EINVAL and a message naming the need and the limit.
+ * The first call on each device looks up the device address of the scratch array on that
+ * device (cudaGetSymbolAddress): make that first call before any stream capture.  Every
+ * call reuses the same array and leaves its contents behind: calls that overlap on the GPU
+ * (on different streams, or from different host threads without ordering) race with each
+ * other and give wrong results; serialise them. */
+#define HOT_NOALLOC_SCRATCH_BYTES (16u << 20)
+int hot_field_noalloc(int width, int height, double pitch_m, double wavelength_m, double focal_m, int M,
+                      const double *xyz_m, const float *phi, int precision, double *V, double *eu,
+                      void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

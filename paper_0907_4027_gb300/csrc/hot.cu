@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -622,3 +623,206 @@ int hot_profile_read(hot_ctx *c, double *ms, long long *launches) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free trap-field evaluation (hot_field_noalloc): all working memory is carved out
+// of one file-scope device array, whose device address is looked up once per device.
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[HOT_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_base[kNoallocMaxDevices];  // device address per device, or NULL
+
+// Device address of the scratch array on the current device (looked up on first use).
+int noalloc_scratch(int dev, unsigned char **out) {
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(HOT_EINVAL, "hot_field_noalloc: device %d beyond %d", dev, kNoallocMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_base[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(HOT_ECUDA, "hot_field_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_noalloc_base[dev] = static_cast<unsigned char *>(p);
+  }
+  *out = g_noalloc_base[dev];
+  return HOT_OK;
+}
+
+// Number of sub-tiles block b of G receives: its run of the U = strips x H row segments,
+// cut at strip ends and into pieces of at most kRowsMax rows (the rule of build_schedule).
+__host__ __device__ int noalloc_block_subtiles(long long U, int G, int H, int b, hot::SubTile *out) {
+  long long s = U * b / G;
+  const long long s1 = U * (b + 1) / G;
+  int n = 0;
+  while (s < s1) {
+    const int strip = (int)(s / H), row = (int)(s % H);
+    const long long run_end = (s1 < (long long)(strip + 1) * H) ? s1 : (long long)(strip + 1) * H;
+    const int L = (int)(run_end - s);
+    const int nsub = (L + hot::kRowsMax - 1) / hot::kRowsMax;
+    for (int i = 0; out && i < nsub; i++) {
+      const int r0 = row + (int)((long long)L * i / nsub), r1 = row + (int)((long long)L * (i + 1) / nsub);
+      out[n + i] = {strip * hot::kTileW, r0, r1 - r0, 0};
+    }
+    n += nsub;
+    s = run_end;
+  }
+  return n;
+}
+
+// Writes the schedule (sub-tiles and per-block first index) for G blocks.
+__global__ void noalloc_schedule_kernel(long long U, int G, int H, hot::SubTile *sub, int *first) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > G) return;
+  int f = 0;
+  for (int q = 0; q < b; q++) f += noalloc_block_subtiles(U, G, H, q, nullptr);
+  first[b] = f;
+  if (b < G) noalloc_block_subtiles(U, G, H, b, sub + f);
+}
+
+// a_m, b_m, c_m of Eq. 2 in turns per pixel index, from device trap coordinates.
+__global__ void noalloc_abc_kernel(int M, const double *xyz, double lin, double quad, double *abc) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < M) {
+    abc[3 * m] = xyz[3 * m] * lin;
+    abc[3 * m + 1] = xyz[3 * m + 1] * lin;
+    abc[3 * m + 2] = xyz[3 * m + 2] * quad;
+  }
+}
+
+// Float-float fields and metrics of the finish kernel -> the caller's double outputs.
+__global__ void noalloc_out_kernel(int M, const float4 *Vf, const float *metrics, double *V, double *eu) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < M) {
+    const float4 v = Vf[m];
+    V[2 * m] = (double)v.x + (double)v.z;
+    V[2 * m + 1] = (double)v.y + (double)v.w;
+  }
+  if (eu && m == 0) {
+    eu[0] = metrics[0];
+    eu[1] = metrics[1];
+  }
+}
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int hot_field_noalloc(int width, int height, double pitch_m, double wavelength_m, double focal_m,
+                                 int M, const double *xyz_m, const float *phi, int precision, double *V,
+                                 double *eu, void *cuda_stream) {
+  if (width < 1 || height < 1 || (long long)width * height >= (1LL << 31))
+    return fail(HOT_EINVAL, "hot_field_noalloc: invalid size %d x %d", width, height);
+  if (!finite_pos(pitch_m) || !finite_pos(wavelength_m) || !finite_pos(focal_m))
+    return fail(HOT_EINVAL, "hot_field_noalloc: pitch, wavelength and focal length must be finite and > 0");
+  if (M < 1 || M > HOT_MAX_TRAPS) return fail(HOT_EINVAL, "hot_field_noalloc: M = %d not in [1, %d]", M, HOT_MAX_TRAPS);
+  if (!xyz_m || !phi || !V) return fail(HOT_EINVAL, "hot_field_noalloc: NULL input or output");
+  if (precision != HOT_PREC_ACCURATE && precision != HOT_PREC_FAST)
+    return fail(HOT_EINVAL, "hot_field_noalloc: unknown precision %d", precision);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const bool fast = precision == HOT_PREC_FAST;
+  int dev = 0;
+  HOT_CUDA(cudaGetDevice(&dev));
+
+  // Work schedule: identical to a context's (one wave of step-kernel blocks).
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                hot::step_smem_bytes(M, false)));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                hot::step_smem_bytes(M, false)));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                hot::step_smem_bytes(M, true)));
+  int sms = 0, per_sm = 0;
+  HOT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_step_kernel<true, true, true>,
+                                                         hot::kThreads, hot::step_smem_bytes(M, true)));
+  if (per_sm < 1) per_sm = 1;
+  const int strips = (width + hot::kTileW - 1) / hot::kTileW;
+  const long long U = (long long)strips * height;
+  const int G = (int)std::min<long long>((long long)sms * per_sm, U);
+  int n_sub = 0;
+  for (int b = 0; b < G; b++) n_sub += noalloc_block_subtiles(U, G, height, b, nullptr);
+
+  // Carve the scratch array.
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off += align256(bytes); return o; };
+  const size_t o_abc = take(sizeof(double) * 3 * M);
+  const size_t o_xt = take(sizeof(float) * (size_t)M * width), o_xr = take(sizeof(float) * (size_t)M * width);
+  const size_t o_yt = take(sizeof(float) * (size_t)M * height), o_yr = take(sizeof(float) * (size_t)M * height);
+  const size_t o_sub = take(sizeof(hot::SubTile) * n_sub), o_first = take(sizeof(int) * (G + 1));
+  const size_t o_part = take(sizeof(float2) * (size_t)M * n_sub);
+  const size_t o_V = take(sizeof(float4) * M), o_w = take(sizeof(float) * M), o_coef = take(sizeof(float2) * M);
+  const size_t o_amp = take(sizeof(float) * M), o_arg = take(sizeof(float) * M);
+  const size_t o_met = take(sizeof(float) * 2), o_ticket = take(sizeof(unsigned int));
+  if (off > HOT_NOALLOC_SCRATCH_BYTES)
+    return fail(HOT_EINVAL, "hot_field_noalloc: %d x %d pixels and %d traps need %zu bytes of scratch, the limit is %u",
+                width, height, M, off, (unsigned)HOT_NOALLOC_SCRATCH_BYTES);
+  unsigned char *base = nullptr;
+  int rc = noalloc_scratch(dev, &base);
+  if (rc != HOT_OK) return rc;
+  double *abc = reinterpret_cast<double *>(base + o_abc);
+  float *Xt = reinterpret_cast<float *>(base + o_xt), *Xr = reinterpret_cast<float *>(base + o_xr);
+  float *Yt = reinterpret_cast<float *>(base + o_yt), *Yr = reinterpret_cast<float *>(base + o_yr);
+  hot::SubTile *d_sub = reinterpret_cast<hot::SubTile *>(base + o_sub);
+  int *d_first = reinterpret_cast<int *>(base + o_first);
+  float2 *partial = reinterpret_cast<float2 *>(base + o_part);
+  float4 *Vf = reinterpret_cast<float4 *>(base + o_V);
+  float *w = reinterpret_cast<float *>(base + o_w);
+  float2 *coef = reinterpret_cast<float2 *>(base + o_coef);
+  float *amp = reinterpret_cast<float *>(base + o_amp), *arg = reinterpret_cast<float *>(base + o_arg);
+  float *metrics = reinterpret_cast<float *>(base + o_met);
+  unsigned int *ticket = reinterpret_cast<unsigned int *>(base + o_ticket);
+
+  // The schedule is written on the device; weights and the reduction counter start at zero
+  // (the array keeps whatever the previous call left).
+  noalloc_schedule_kernel<<<(G + 1 + 255) / 256, 256, 0, st>>>(U, G, height, d_sub, d_first);
+  HOT_CUDA(cudaGetLastError());
+  HOT_CUDA(cudaMemsetAsync(w, 0, sizeof(float) * M, st));
+  HOT_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st));
+
+  const double lin = pitch_m / (wavelength_m * focal_m);
+  const double quad = pitch_m * pitch_m / (2.0 * wavelength_m * focal_m * focal_m);
+  noalloc_abc_kernel<<<(M + 255) / 256, 256, 0, st>>>(M, xyz_m, lin, quad, abc);
+  HOT_CUDA(cudaGetLastError());
+  const long long total = (long long)M * (width + height);
+  const int tb = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  hot::build_tables_kernel<<<tb, 256, 0, st>>>(width, height, M, abc, Xt, Yt, Xr, Yr);
+  HOT_CUDA(cudaGetLastError());
+
+  hot::StepArgs a;
+  a.W = width;
+  a.H = height;
+  a.M = M;
+  a.n_sub = n_sub;
+  a.sub = d_sub;
+  a.first = d_first;
+  a.X = fast ? Xr : Xt;
+  a.Y = fast ? Yr : Yt;
+  a.coef = coef;
+  a.phi = const_cast<float *>(phi);  // the forward-only kernel reads the phases and writes none
+  a.partial = partial;
+  const int smem = hot::step_smem_bytes(M, false);
+  if (fast) hot::gsw_step_kernel<true, false, true><<<G, hot::kThreads, smem, st>>>(a);
+  else hot::gsw_step_kernel<false, false, true><<<G, hot::kThreads, smem, st>>>(a);
+  HOT_CUDA(cudaGetLastError());
+
+  hot::FinishArgs f;
+  f.M = M;
+  f.n_tiles = n_sub;
+  f.update = 0;
+  f.inv_n = (float)(1.0 / ((double)width * (double)height));
+  f.angle_units = fast ? 1.0f : 0.15915494309189535f;
+  f.partial = partial;
+  f.V = Vf;
+  f.w = w;
+  f.coef = coef;
+  f.metrics = metrics;
+  f.amp = amp;
+  f.arg = arg;
+  f.ticket = ticket;
+  hot::gsw_finish_kernel<<<M, hot::kFinishThreads, 0, st>>>(f);
+  HOT_CUDA(cudaGetLastError());
+  noalloc_out_kernel<<<(M + 255) / 256, 256, 0, st>>>(M, Vf, metrics, V, eu);
+  HOT_CUDA(cudaGetLastError());
+  return HOT_OK;
+}

@@ -48,6 +48,8 @@ SIGNATURES = {
     "hot_profile_read": (_c_int, [_vp, _vp, _vp]),
     "hot_destroy": (None, [_vp]),
     "hot_last_error": (ctypes.c_char_p, []),
+    "hot_field_noalloc": (_c_int, [_c_int, _c_int, _c_double, _c_double, _c_double, _c_int, _vp, _vp, _c_int,
+                                   _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in SIGNATURES.items():
     _fn = getattr(lib, _name)
@@ -178,6 +180,23 @@ def hot_profile_read(ctx: int) -> dict:
 
 def hot_destroy(ctx: int) -> None:
     lib.hot_destroy(_vp(ctx))
+
+
+HOT_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def hot_field_noalloc(width: int, height: int, pitch_m: float, wavelength_m: float, focal_m: float,
+                      xyz_dev, phi_dev, precision, V_dev, eu_dev=None, cuda_stream: int | None = None) -> None:
+    """Allocation-free trap fields: all arguments but the sizes are CUDA tensors (device
+    memory); xyz_dev (M, 3) float64, phi_dev (N,) float32, V_dev (2M,) float64 output,
+    eu_dev (2,) float64 output or None.  Queued on cuda_stream."""
+    if isinstance(precision, str):
+        precision = {"accurate": HOT_PREC_ACCURATE, "fast": HOT_PREC_FAST}[precision]
+    M = int(xyz_dev.numel() // 3)
+    _ok(lib.hot_field_noalloc(int(width), int(height), float(pitch_m), float(wavelength_m), float(focal_m), M,
+                              _vp(xyz_dev.data_ptr()), _vp(phi_dev.data_ptr()), int(precision),
+                              _vp(V_dev.data_ptr()), _vp(eu_dev.data_ptr() if eu_dev is not None else 0),
+                              _vp(cuda_stream or 0)), "hot_field_noalloc")
 
 
 # ---- convenience class -------------------------------------------------------------
