@@ -13,9 +13,9 @@
  *   Sec. 5  8-bit SLM grey levels g_j = rint(phi_j 256/(2 pi)) mod 256
  * Pixel j = iy*W + ix has coordinates x_j = (ix - floor(W/2)) p, y_j = (iy - floor(H/2)) p.
  * Device arithmetic is FP32, except the trap-table set-up (Eq. 2 reduced modulo 2 pi in FP64,
- * once per hot_set_traps) and the reduction of the per-tile field partials (float-float,
- * about 48 significant bits).  Every reduction runs in a fixed order: results are
- * bit-reproducible for a given device, size and precision mode.
+ * once per hot_set_traps) and the sum of the per-sub-tile field sums over the image, which is
+ * exact integer arithmetic in 64-bit fixed point.  Every other reduction runs in a fixed
+ * order: results are bit-reproducible for a given device, size and precision mode.
  *
  * Conventions shared by every entry point:
  *   - Return value: HOT_OK (0) or a negative hot_status; no call aborts or exits.
@@ -152,7 +152,7 @@ const char *hot_last_error(void);
  * hot_field_noalloc computes V_m = (1/N) sum_j exp(i (phi_j - Delta_j^m)) (the same forward
  * field that hot_gsw(c, 0, ...) evaluates for a context) and, if eu is not NULL, e and u of
  * Eq. 4.  It calls no cudaMalloc, cudaFree or other allocating routine: its working memory
- * (trap tables, work schedule, per-tile partial sums, reduction counters) lives in one
+ * (trap tables, work schedule, field accumulators, reduction counter) lives in one
  * file-scope __device__ array of HOT_NOALLOC_SCRATCH_BYTES that every GPU which loads the
  * library holds until the process exits.
  *   width, height, pitch_m, wavelength_m, focal_m: as for hot_create.
@@ -162,7 +162,7 @@ const char *hot_last_error(void);
  *   V: DEVICE output, 2*M doubles interleaved (Re, Im).  eu: DEVICE output of 2 doubles
  *   (e, u) or NULL.  cuda_stream: a cudaStream_t or NULL.
  * Work is queued on cuda_stream; the host reads nothing back.  Sizes whose working memory
- * exceeds the scratch array (roughly 8 M (W + H) + 8 M (W/32 * H / 16 + 2 * SMs) bytes) are
+ * exceeds the scratch array (about 8 M (W + H) + 60 M + 16 (W/32) (H/16) bytes) are
  * rejected with HOT_EINVAL and a message naming the need and the limit.
  * The first call on each device looks up the device address of the scratch array on that
  * device (cudaGetSymbolAddress): make that first call before any stream capture.  Every

@@ -1,11 +1,14 @@
 // gsw_kernels.cuh -- sm_103a kernels of the GSW hologram engine.
 //
-// Hot path (Sec. 3-4 of Bianchi & Di Leonardo): per iteration one fused kernel does the
-// back-projection of iteration k (phi_j = arg sum_m c_m e^{i Delta_j^m}) and the forward
-// field of iteration k+1 (per-tile partial sums of e^{i phi_j} e^{-i Delta_j^m}, Eq. 1);
-// a finish kernel (one block per trap) then reduces the partials of every trap in fixed
-// order in float-float arithmetic, and its last block updates the weights and forms the
-// next coefficients c_m = w_m V_m/|V_m|.  No FP64 runs per iteration.
+// Hot path (Sec. 3-4 of Bianchi & Di Leonardo): per iteration one kernel does the weight
+// update of iteration k (Sec. 3), the back-projection phi_j = arg sum_m c_m e^{i Delta_j^m}
+// and the forward field of iteration k+1 (Eq. 1).  Every sub-tile adds its per-trap sums of
+// e^{i (phi_j - Delta_j^m)} into 64-bit fixed-point accumulators with integer atomics, which
+// are exact and therefore independent of the order in which blocks arrive.  The next launch
+// reads the completed sums: every block forms V_m, <|V|>, the new weights and the
+// coefficients c_m = w_m V_m/|V_m| itself, in the same fixed order, so no block waits for
+// another and no reduction tail sits between iterations.  Accumulators rotate over three
+// buffers (read, written, cleared) and weights over two.  No FP64 runs per iteration.
 //
 // Per pair the kernels take exactly one complex exponential and accumulate it without a
 // complex multiply: the back-projection folds the phase of its coefficient into the argument,
@@ -29,28 +32,36 @@ namespace hot {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr int kTileW = 32;      // pixels per sub-tile row: one per lane
-constexpr int kRowsMax = 16;    // rows per sub-tile (each lane keeps one field per row)
+constexpr int kRowsMax = 14;    // rows per sub-tile (each lane keeps one field per row)
+constexpr int kYStride = (kRowsMax + 3) & ~3;  // floats per trap in the staged row table (16-byte rows)
 constexpr int kChunk = 128;     // traps whose tables are staged in shared memory at once
 constexpr float kTwoPi = 6.283185307179586f;
 
 // Work decomposition: the image is cut into 32-pixel-wide column strips; each strip's rows
 // are dealt out as contiguous runs to a fixed number of resident blocks (one wave), so that
 // every block gets the same number of row segments within one.  A block walks its run as
-// sub-tiles of at most kRowsMax rows.  Sub-tile t writes partial[m][t].
+// sub-tiles of at most kRowsMax rows.
 struct SubTile {
   int x0, y0, rows, pad;
 };
 
 struct StepArgs {
   int W, H, M;
-  int n_sub;              // number of sub-tiles (columns of `partial`)
-  const SubTile *sub;     // [n_sub]
+  const SubTile *sub;     // work schedule: sub-tiles
   const int *first;       // [gridDim.x + 1]: block b processes sub-tiles first[b] .. first[b+1]-1
   const float *X;         // [M][W] column phase parts (turns if accurate, radians if fast)
   const float *Y;         // [M][H] row phase parts (same unit)
-  const float2 *coef;     // [M] back-projection coefficients (w_m, arg V_m in table units)
   float *phi;             // [H*W] pixel phases, radians
-  float2 *partial;        // [M][n_sub] sub-tile sums of e^{i phi_j} e^{-i Delta_j^m}
+  // BACK: weight update and coefficients from the previous launch's forward field
+  const unsigned long long *acc_in;  // [2][M] fixed-point sums of the previous forward: Re, Im
+  const float *w_in;                 // [M] weights before this iteration's update
+  float *w_out;                      // [M] updated weights (trap m written by block m % gridDim.x)
+  // FWD: forward field of this launch's phases
+  unsigned long long *acc_out;       // [2][M] zero on entry (cleared by the launch before last)
+  unsigned long long *acc_clear;     // [2][M] cleared here for the next launch
+  float fx_scale;           // 2^fx_shift: fixed-point scale of the sums
+  float inv_fx_n;           // 1 / (N 2^fx_shift)
+  float angle_units;        // 1 (radians) or 1/(2 pi) (turns): units of the tables
 };
 
 __device__ __forceinline__ float sin_approx(float x) {
@@ -86,7 +97,7 @@ __device__ __forceinline__ float phase_units(float ph) {
 // of half a sub-tile's rows, and the pixel phases of the sub-tile.
 constexpr int kHalfRows = kRowsMax / 2;
 constexpr int kXsFloats = kChunk * kTileW;
-constexpr int kYsFloats = kChunk * kRowsMax;
+constexpr int kYsFloats = kChunk * kYStride;
 constexpr int kSmemBytes = (kXsFloats + kYsFloats) * 4 + kChunk * 8 + kWarps * kHalfRows * kTileW * 8 +
                            kRowsMax * kTileW * 4;
 
@@ -96,10 +107,6 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   const int n = valid ? 4 : 0;  // 0 source bytes: the destination is zero-filled
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
@@ -112,24 +119,41 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
+// The field V_m of the previous forward, from its fixed-point sums.
+__device__ __forceinline__ float2 field_from_sums(const StepArgs &a, int m) {
+  const long long sr = (long long)__ldcg(a.acc_in + m), si = (long long)__ldcg(a.acc_in + a.M + m);
+  return make_float2((float)sr * a.inv_fx_n, (float)si * a.inv_fx_n);
+}
+
+// Sec. 3 weight update and back-projection coefficient of trap m in polar form
+// (w_m, arg V_m): w_m <- w_m <|V|>/|V_m|; if |V_m| < 1e-30 the unit field is 1 and w_m stays.
+__device__ __forceinline__ float2 coefficient(const StepArgs &a, int m, float mean) {
+  const float2 v = field_from_sums(a, m);
+  const float am = sqrtf(v.x * v.x + v.y * v.y);
+  float w = a.w_in[m];
+  if (am >= 1e-30f) w = w * mean / am;
+  return make_float2(w, am >= 1e-30f ? atan2f(v.y, v.x) * a.angle_units : 0.f);
+}
+
 // Stages, with asynchronous copies (all in flight at once), the X (32 columns from x0) and Y
 // (rows y0 .. y0+rows-1) tables of traps [m0, m0+n), plus their coefficients when BACK.
 // The caller synchronises the block afterwards.
 template <bool BACK>
 __device__ __forceinline__ void stage_tables(const StepArgs &a, int m0, int n, const SubTile &st,
-                                             float *Xs, float *Ys, float2 *Cs, bool xy = true) {
+                                             float *Xs, float *Ys, float2 *Cs, bool xy = true,
+                                             float mean = 0.f) {
   for (int i = threadIdx.x; xy && i < n * kTileW; i += kThreads) {
     const int k = i / kTileW, col = st.x0 + (i % kTileW);
     const bool ok = col < a.W;
     cp_async4(Xs + i, a.X + (ok ? (size_t)(m0 + k) * a.W + col : 0), ok);
   }
-  for (int i = threadIdx.x; xy && i < n * kRowsMax; i += kThreads) {
-    const int k = i / kRowsMax, r = i % kRowsMax;
+  for (int i = threadIdx.x; xy && i < n * kYStride; i += kThreads) {
+    const int k = i / kYStride, r = i % kYStride;
     const bool ok = r < st.rows;
     cp_async4(Ys + i, a.Y + (ok ? (size_t)(m0 + k) * a.H + st.y0 + r : 0), ok);
   }
   if (BACK)
-    for (int i = threadIdx.x; i < n; i += kThreads) cp_async8(Cs + i, a.coef + m0 + i);
+    for (int i = threadIdx.x; i < n; i += kThreads) Cs[i] = coefficient(a, m0 + i, mean);
   cp_async_wait_all();
 }
 
@@ -175,7 +199,7 @@ __device__ __forceinline__ void back_traps(const float *Xs, const float *Ys, con
   for (int k = lo; k < hi; k++) {
     const float2 c = Cs[k];                      // (w_m, arg V_m)
     const float xm = Xs[k * kTileW + lane] + c.y;
-    const float4 *yq = reinterpret_cast<const float4 *>(Ys + k * kRowsMax);
+    const float4 *yq = reinterpret_cast<const float4 *>(Ys + k * kYStride);
 #pragma unroll
     for (int q = 0; q < (R + 3) / 4; q++) {
       const float4 y4 = yq[q];
@@ -195,13 +219,13 @@ __device__ __forceinline__ void back_traps(const float *Xs, const float *Ys, con
 }
 
 // Forward field (Eq. 1) of traps [lo, hi) of the staged chunk over the R rows of this lane's
-// column: sum_r e^{i (phi_r - X_m - Y_m(r))}, summed over the warp 8 traps at a time; writes
-// partial[(m0 + k) * stride + t].  ph holds the lane's pixel phases in table units; msk is 1
-// for a lane inside the image and 0 for a lane past its right edge.
+// column: sum_r e^{i (phi_r - X_m - Y_m(r))}, summed over the warp 8 traps at a time and
+// added, in fixed point, to acc_out[m0 + k] (Re) and acc_out[M + m0 + k] (Im).  ph holds the lane's
+// pixel phases in table units; msk is 1 for a lane inside the image, 0 past its right edge.
 template <bool FAST, int R>
 __device__ __forceinline__ void forward_traps(const float *Xs, const float *Ys, int lo, int hi, int lane,
-                                              const float (&ph)[kRowsMax], float msk, float2 *partial,
-                                              size_t stride, int t, int m0) {
+                                              const float (&ph)[kRowsMax], float msk, const StepArgs &a,
+                                              int m0) {
   for (int g = lo; g < hi; g += kGroup) {
     float2 acc[kGroup];
 #pragma unroll
@@ -210,7 +234,7 @@ __device__ __forceinline__ void forward_traps(const float *Xs, const float *Ys, 
       const int k = g + i;
       if (k < hi) {
         const float xm = Xs[k * kTileW + lane];
-        const float4 *yq = reinterpret_cast<const float4 *>(Ys + k * kRowsMax);
+        const float4 *yq = reinterpret_cast<const float4 *>(Ys + k * kYStride);
 #pragma unroll
         for (int q = 0; q < (R + 3) / 4; q++) {
           const float4 y4 = yq[q];
@@ -230,7 +254,104 @@ __device__ __forceinline__ void forward_traps(const float *Xs, const float *Ys, 
     }
     const float2 v = warp_reduce8(acc, lane);
     const int k = g + ((lane >> 2) & 7);
-    if ((lane & 3) == 0 && k < hi) partial[(size_t)(m0 + k) * stride + t] = v;
+    if ((lane & 3) == 0 && k < hi) {
+      // |v| <= 32 * kRowsMax, so v * 2^fx_shift is an exact integer far below 2^63
+      atomicAdd(a.acc_out + m0 + k, (unsigned long long)__float2ll_rn(v.x * a.fx_scale));
+      atomicAdd(a.acc_out + a.M + m0 + k, (unsigned long long)__float2ll_rn(v.y * a.fx_scale));
+    }
+  }
+}
+
+// Float-float ("double-single") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
+// TwoSum (Knuth) and FastTwoSum (Dekker) give the exact rounding error of one addition.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (b.hi - bb);
+  const float e = err + (a.lo + b.lo);
+  const float hi = s + e;
+  return {hi, e - (hi - s)};
+}
+
+// <|V|> of the previous forward (mean of |V_m| over the traps, Sec. 3), computed by every
+// block in the same fixed order (thread-strided float-float sums, warp shuffles, warps in
+// order), so that all blocks obtain the same value bit for bit.
+__device__ __forceinline__ float mean_field_amplitude(const StepArgs &a) {
+  __shared__ ff part[kWarps];
+  ff s = {0.f, 0.f};
+  for (int m = threadIdx.x; m < a.M; m += kThreads) {
+    const float2 v = field_from_sums(a, m);
+    s = ff_add(s, {sqrtf(v.x * v.x + v.y * v.y), 0.f});
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1)
+    s = ff_add(s, {__shfl_down_sync(0xffffffffu, s.hi, o), __shfl_down_sync(0xffffffffu, s.lo, o)});
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  ff q = part[0];
+#pragma unroll
+  for (int i = 1; i < kWarps; i++) q = ff_add(q, part[i]);
+  return (q.hi + q.lo) / (float)a.M;
+}
+
+struct FinalizeArgs {
+  int M;
+  const unsigned long long *acc;  // [2][M] sums of the last forward field
+  unsigned long long *acc_all;    // [3][2][M] all accumulators: cleared for the next call
+  const float *w_src;             // [M] weights after the last update
+  float *w_dst;                   // [M] where the weights live between calls (may equal w_src)
+  long long *Vsum;                // [2][M] out: the sums (V_m = Vsum / (N 2^fx_shift))
+  float *metrics;                 // [2] out: e, u (Eq. 4)
+  float inv_fx_n;
+};
+
+constexpr int kFinalizeThreads = 1024;
+
+// One block, once per hot_gsw call: efficiency e = sum |V_m|^2 and uniformity
+// u = 1 - (max I - min I)/(max I + min I) (Eq. 4) of the final forward field (fixed order),
+// the field sums for the caller, the weights back into their home buffer, and every
+// accumulator cleared.
+__global__ void __launch_bounds__(kFinalizeThreads) gsw_finalize_kernel(FinalizeArgs a) {
+  struct Part {
+    ff si;
+    float mx, mn;
+  };
+  __shared__ Part part[kFinalizeThreads / 32];
+  grid_dependency_wait();
+  Part p = {{0.f, 0.f}, -1.f, 3.0e38f};
+  for (int m = threadIdx.x; m < a.M; m += kFinalizeThreads) {
+    const long long sr = (long long)__ldcg(a.acc + m), si = (long long)__ldcg(a.acc + a.M + m);
+    a.Vsum[m] = sr;
+    a.Vsum[a.M + m] = si;
+    const float vr = (float)sr * a.inv_fx_n, vi = (float)si * a.inv_fx_n;
+    const float I = vr * vr + vi * vi;
+    p.si = ff_add(p.si, {I, 0.f});
+    p.mx = fmaxf(p.mx, I);
+    p.mn = fminf(p.mn, I);
+    if (a.w_dst != a.w_src) a.w_dst[m] = a.w_src[m];
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    p.si = ff_add(p.si, {__shfl_down_sync(0xffffffffu, p.si.hi, o), __shfl_down_sync(0xffffffffu, p.si.lo, o)});
+    p.mx = fmaxf(p.mx, __shfl_down_sync(0xffffffffu, p.mx, o));
+    p.mn = fminf(p.mn, __shfl_down_sync(0xffffffffu, p.mn, o));
+  }
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = p;
+  __syncthreads();  // every read of the accumulators is done before they are cleared
+  for (int i = threadIdx.x; i < 6 * a.M; i += kFinalizeThreads) a.acc_all[i] = 0ull;
+  if (threadIdx.x == 0) {
+    Part q = part[0];
+    for (int i = 1; i < kFinalizeThreads / 32; i++) {
+      q.si = ff_add(q.si, part[i].si);
+      q.mx = fmaxf(q.mx, part[i].mx);
+      q.mn = fminf(q.mn, part[i].mn);
+    }
+    a.metrics[0] = q.si.hi + q.si.lo;
+    a.metrics[1] = (q.mx + q.mn > 0.f) ? 1.f - (q.mx - q.mn) / (q.mx + q.mn) : 0.f;
   }
 }
 
@@ -250,14 +371,12 @@ __device__ __forceinline__ void forward_traps(const float *Xs, const float *Ys, 
     case 11: { constexpr int R = 11; BODY; } break; \
     case 12: { constexpr int R = 12; BODY; } break; \
     case 13: { constexpr int R = 13; BODY; } break; \
-    case 14: { constexpr int R = 14; BODY; } break; \
-    case 15: { constexpr int R = 15; BODY; } break; \
-    default: { constexpr int R = 16; BODY; } break; \
+    default: { constexpr int R = 14; BODY; } break; \
   }
-static_assert(kRowsMax == 16, "HOT_WITH_ROWS covers 1..16 rows");
+static_assert(kRowsMax == 14, "HOT_WITH_ROWS covers 1..14 rows");
 
 // Persistent blocks, one wave; the 8 warps of a block split the traps of each chunk.
-// BACK: back-projection with a.coef -> a.phi.  FWD: forward partials of the sub-tile phases.
+// BACK: weight update and back-projection -> a.phi.  FWD: forward field of the sub-tile phases.
 template <bool FAST, bool BACK, bool FWD>
 __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -273,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
   const int t_begin = a.first[blockIdx.x], t_end = a.first[blockIdx.x + 1];
 
   // Prologue, overlapping the previous kernel: the trap tables are constant during hot_gsw,
-  // so the first chunk of the back-projection is staged before waiting for the coefficients.
+  // so the first chunk of the back-projection is staged before waiting for its field sums.
   allow_dependents();
   bool prestaged = false;
   if (BACK && t_begin < t_end) {
@@ -282,6 +401,14 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
     prestaged = true;
   }
   grid_dependency_wait();
+  if (FWD)  // the buffer the next launch accumulates into
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
+  float mean = 0.f;
+  if (BACK) {
+    mean = mean_field_amplitude(a);
+    for (int m = blockIdx.x + gridDim.x * threadIdx.x; m < a.M; m += gridDim.x * kThreads)
+      a.w_out[m] = coefficient(a, m, mean).x;
+  }
 
   for (int t = t_begin; t < t_end; t++) {
     const SubTile st = a.sub[t];
@@ -295,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
       for (int ch = 0; ch < nchunks; ch++) {
         const int m0 = ch * mc, n = min(mc, a.M - m0);
         __syncthreads();  // earlier readers of the tables are done
-        stage_tables<true>(a, m0, n, st, Xs, Ys, Cs, !prestaged);
+        stage_tables<true>(a, m0, n, st, Xs, Ys, Cs, !prestaged, mean);
         prestaged = false;
         __syncthreads();
         const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
@@ -343,139 +470,9 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
           __syncthreads();
         }
         const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
-        HOT_WITH_ROWS(st.rows, (forward_traps<FAST, R>(Xs, Ys, lo, hi, lane, ph, col_ok ? 1.f : 0.f, a.partial,
-                                                       a.n_sub, t, m0)));
+        HOT_WITH_ROWS(st.rows, (forward_traps<FAST, R>(Xs, Ys, lo, hi, lane, ph, col_ok ? 1.f : 0.f, a, m0)));
       }
     }
-  }
-}
-
-struct FinishArgs {
-  int M, n_tiles, update;
-  float inv_n;
-  float angle_units;      // 1 (radians) or 1/(2 pi) (turns): units of the tables
-  const float2 *partial;  // [M][n_tiles]
-  float4 *V;              // [M] out: V_m (Eq. 1) as float-float (hi.re, hi.im, lo.re, lo.im)
-  float *w;               // [M] in/out: GSW weights
-  float2 *coef;           // [M] out: (w_m, arg V_m) -- the coefficient w_m V_m/|V_m| in polar form
-  float *metrics;         // [2] out: e, u (Eq. 4)
-  float *amp;             // [M] scratch: |V_m|
-  float *arg;             // [M] scratch: arg V_m in table units (0 if |V_m| < 1e-30)
-  unsigned int *ticket;   // one counter, 0 between launches
-};
-
-constexpr int kFinishThreads = 256;
-
-// Float-float ("double-single") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
-// TwoSum (Knuth) and FastTwoSum (Dekker) give the exact rounding error of one addition.
-struct ff {
-  float hi, lo;
-};
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  const float err = (a.hi - (s - bb)) + (b.hi - bb);
-  const float e = err + (a.lo + b.lo);
-  const float hi = s + e;
-  return {hi, e - (hi - s)};
-}
-__device__ __forceinline__ ff ff_shfl_down(ff a, int o) {
-  return {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
-}
-
-// Fixed-order float-float sum over the block; the result is valid in thread 0.
-__device__ __forceinline__ ff block_sum_ff(ff v, ff *red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v = ff_add(v, ff_shfl_down(v, o));
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  ff s = {0.f, 0.f};
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); i++) s = ff_add(s, red[i]);
-  return s;
-}
-
-// Grid of M blocks.  Block m: V_m = (1/N) sum over tiles of the partials in float-float,
-// fixed order; |V_m| and V_m/|V_m|.  The last block to finish (ticket) forms <|V|>, updates
-// the weights (Sec. 3), the next coefficients c_m = w_m V_m/|V_m| and e, u (Eq. 4), reading
-// every trap in index order.
-__global__ void __launch_bounds__(kFinishThreads) gsw_finish_kernel(FinishArgs a) {
-  __shared__ ff red[kFinishThreads / 32];
-  __shared__ float rmx[kFinishThreads / 32], rmn[kFinishThreads / 32];
-  __shared__ float bcast;
-  __shared__ bool last;
-  const int m = blockIdx.x;
-  grid_dependency_wait();  // the partials of the step kernel
-  allow_dependents();
-  {
-    ff sr = {0.f, 0.f}, si = {0.f, 0.f};
-    const float2 *p = a.partial + (size_t)m * a.n_tiles;
-    for (int t = threadIdx.x; t < a.n_tiles; t += kFinishThreads) {
-      const float2 v = p[t];
-      sr = ff_add(sr, {v.x, 0.f});
-      si = ff_add(si, {v.y, 0.f});
-    }
-    sr = block_sum_ff(sr, red);
-    si = block_sum_ff(si, red);
-    if (threadIdx.x == 0) {
-      const float4 v = make_float4(sr.hi * a.inv_n, si.hi * a.inv_n, sr.lo * a.inv_n, si.lo * a.inv_n);
-      const float vr = v.x + v.z, vi = v.y + v.w;
-      const float am = sqrtf(vr * vr + vi * vi);
-      a.V[m] = v;
-      a.amp[m] = am;
-      a.arg[m] = am >= 1e-30f ? atan2f(vi, vr) * a.angle_units : 0.f;
-      __threadfence();
-      last = atomicAdd(a.ticket, 1u) == (unsigned)(a.M - 1);
-    }
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  ff sa = {0.f, 0.f}, si = {0.f, 0.f};
-  float mx = -1.f, mn = 3.0e38f;
-  for (int k = threadIdx.x; k < a.M; k += kFinishThreads) {
-    const float am = __ldcg(a.amp + k);
-    const float I = am * am;
-    sa = ff_add(sa, {am, 0.f});
-    si = ff_add(si, {I, 0.f});
-    mx = fmaxf(mx, I);
-    mn = fminf(mn, I);
-  }
-  sa = block_sum_ff(sa, red);
-  si = block_sum_ff(si, red);
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
-    mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    rmx[threadIdx.x >> 5] = mx;
-    rmn[threadIdx.x >> 5] = mn;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float X = -1.f, N = 3.0e38f;
-    for (int i = 0; i < kFinishThreads / 32; i++) {
-      X = fmaxf(X, rmx[i]);
-      N = fminf(N, rmn[i]);
-    }
-    bcast = (sa.hi + sa.lo) / (float)a.M;
-    a.metrics[0] = si.hi + si.lo;
-    a.metrics[1] = (X + N > 0.f) ? 1.f - (X - N) / (X + N) : 0.f;
-    *a.ticket = 0u;
-  }
-  __syncthreads();
-  const float mean = bcast;
-  for (int k = threadIdx.x; k < a.M; k += kFinishThreads) {
-    const float am = __ldcg(a.amp + k);
-    float wk = a.w[k];
-    if (a.update && am >= 1e-30f) {
-      wk = wk * mean / am;
-      a.w[k] = wk;
-    }
-    a.coef[k] = make_float2(wk, __ldcg(a.arg + k));
   }
 }
 

@@ -69,14 +69,11 @@ struct hot_ctx {
   int M = 0;
   double *abc = nullptr;                                       // [M][3]
   float *Xt = nullptr, *Yt = nullptr, *Xr = nullptr, *Yr = nullptr;  // tables
-  float *w = nullptr;                                          // [M]
-  float2 *coef = nullptr;                                      // [M]
-  float4 *V = nullptr;                                         // [M] float-float fields
-  float2 *partial = nullptr;                                   // [M][n_sub]
-  float *amp = nullptr;                                        // [M] scratch
-  float *arg = nullptr;                                        // [M] scratch
+  float *w = nullptr;                                          // [2][M] weights (home: w[0])
+  unsigned long long *acc = nullptr;                           // [3][2][M] fixed-point field sums
+  long long *Vsum = nullptr;                                   // [2][M] sums of the last forward
   float *metrics = nullptr;                                    // [2]
-  unsigned int *ticket = nullptr;                              // finish-kernel counter
+  int fx_shift = 0;                                            // fixed-point scale 2^fx_shift
   unsigned char *u8 = nullptr;                                 // [N] staging for host output
   bool have_fields = false;
   long long launches = 0;
@@ -116,11 +113,8 @@ void free_traps(hot_ctx *c) {
   dfree(c->Xr);
   dfree(c->Yr);
   dfree(c->w);
-  dfree(c->coef);
-  dfree(c->V);
-  dfree(c->partial);
-  dfree(c->amp);
-  dfree(c->arg);
+  dfree(c->acc);
+  dfree(c->Vsum);
   c->M = 0;
   c->have_fields = false;
 }
@@ -186,20 +180,28 @@ void launch(hot_ctx *c, void (*kernel)(KArgs...), int grid, int block, int smem,
   cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// Launch k of a hot_gsw sequence (k = 0: forward field of the starting phases; k >= 1:
+// iteration k).  Accumulators rotate over three buffers, weights over two.
 template <bool FAST, bool BACK, bool FWD>
-int launch_tile(hot_ctx *c, bool pdl) {
+int launch_tile(hot_ctx *c, bool pdl, int k) {
   hot::StepArgs a;
   a.W = c->W;
   a.H = c->H;
   a.M = c->M;
-  a.n_sub = c->n_sub;
   a.sub = c->sub;
   a.first = c->first;
   a.X = FAST ? c->Xr : c->Xt;
   a.Y = FAST ? c->Yr : c->Yt;
-  a.coef = c->coef;
   a.phi = c->phi;
-  a.partial = c->partial;
+  const size_t M2 = 2 * (size_t)c->M;
+  a.acc_in = c->acc + M2 * ((k + 2) % 3);
+  a.acc_out = c->acc + M2 * (k % 3);
+  a.acc_clear = c->acc + M2 * ((k + 1) % 3);
+  a.w_in = c->w + (size_t)c->M * ((k + 1) & 1);
+  a.w_out = c->w + (size_t)c->M * (k & 1);
+  a.fx_scale = ldexpf(1.0f, c->fx_shift);
+  a.inv_fx_n = (float)(1.0 / ((double)c->W * (double)c->H * ldexp(1.0, c->fx_shift)));
+  a.angle_units = FAST ? 1.0f : 0.15915494309189535f;
   const int smem = hot::step_smem_bytes(c->M, BACK);
   Probe p(c, BACK && FWD ? HOT_KERNEL_STEP : FWD ? HOT_KERNEL_FORWARD : HOT_KERNEL_OTHER);
   launch(c, hot::gsw_step_kernel<FAST, BACK, FWD>, c->grid, hot::kThreads, smem, pdl, a);
@@ -265,31 +267,30 @@ int build_schedule(hot_ctx *c) {
   return HOT_OK;
 }
 
-int launch_step(hot_ctx *c, bool back, bool fwd, bool pdl) {
+// One step-kernel launch (launch k of the sequence): weight update + back-projection and/or
+// forward field.
+int launch_step(hot_ctx *c, bool back, bool fwd, bool pdl, int k) {
   const bool fast = c->precision == HOT_PREC_FAST;
-  if (back && fwd) return fast ? launch_tile<true, true, true>(c, pdl) : launch_tile<false, true, true>(c, pdl);
-  if (back) return fast ? launch_tile<true, true, false>(c, pdl) : launch_tile<false, true, false>(c, pdl);
-  return fast ? launch_tile<true, false, true>(c, pdl) : launch_tile<false, false, true>(c, pdl);
+  if (back && fwd) return fast ? launch_tile<true, true, true>(c, pdl, k) : launch_tile<false, true, true>(c, pdl, k);
+  if (back) return fast ? launch_tile<true, true, false>(c, pdl, k) : launch_tile<false, true, false>(c, pdl, k);
+  return fast ? launch_tile<true, false, true>(c, pdl, k) : launch_tile<false, false, true>(c, pdl, k);
 }
 
-int launch_finish(hot_ctx *c, bool update) {
-  hot::FinishArgs a;
-  a.M = c->M;
-  a.n_tiles = c->n_sub;
-  a.update = update ? 1 : 0;
-  a.inv_n = (float)(1.0 / ((double)c->W * (double)c->H));
-  a.partial = c->partial;
-  a.V = c->V;
-  a.w = c->w;
-  a.coef = c->coef;
-  a.metrics = c->metrics;
-  a.amp = c->amp;
-  a.arg = c->arg;
-  a.angle_units = c->precision == HOT_PREC_FAST ? 1.0f : 0.15915494309189535f;
-  a.ticket = c->ticket;
+// After the last launch (k = iters): Eq. 4 metrics, field sums, weights home, accumulators cleared.
+int launch_finalize(hot_ctx *c, bool pdl, int iters) {
+  hot::FinalizeArgs f;
+  const size_t M2 = 2 * (size_t)c->M;
+  f.M = c->M;
+  f.acc = c->acc + M2 * (iters % 3);
+  f.acc_all = c->acc;
+  f.w_src = c->w + (size_t)c->M * (iters & 1);
+  f.w_dst = c->w;
+  f.Vsum = c->Vsum;
+  f.metrics = c->metrics;
+  f.inv_fx_n = (float)(1.0 / ((double)c->W * (double)c->H * ldexp(1.0, c->fx_shift)));
   Probe p(c, HOT_KERNEL_FINISH);
-  launch(c, hot::gsw_finish_kernel, c->M, hot::kFinishThreads, 0, !c->profiling, a);
-  return check_launch(c, "gsw_finish_kernel");
+  launch(c, hot::gsw_finalize_kernel, 1, hot::kFinalizeThreads, 0, pdl, f);
+  return check_launch(c, "gsw_finalize_kernel");
 }
 
 // The launch sequence of hot_gsw(iters) on c->st.
@@ -298,12 +299,10 @@ int launch_finish(hot_ctx *c, bool update) {
 // whatever preceded hot_gsw in the stream (trap tables, phases).
 int enqueue_gsw(hot_ctx *c, int iters) {
   const bool pdl = !c->profiling;
-  int rc = launch_step(c, false, true, false);  // V = F(phi)
-  if (rc == HOT_OK) rc = launch_finish(c, iters > 0);
-  for (int k = 1; k <= iters && rc == HOT_OK; k++) {
-    rc = launch_step(c, true, true, pdl);         // phi^k = B(c^k); partials of F(phi^k)
-    if (rc == HOT_OK) rc = launch_finish(c, k < iters);
-  }
+  int rc = launch_step(c, false, true, false, 0);       // V^1 = F(phi^0)
+  for (int k = 1; k <= iters && rc == HOT_OK; k++)
+    rc = launch_step(c, true, true, pdl, k);            // w^k, c^k from V^k; phi^k; V^{k+1} = F(phi^k)
+  if (rc == HOT_OK) rc = launch_finalize(c, pdl, iters);  // e, u of V^{iters+1}
   return rc;
 }
 
@@ -368,16 +367,19 @@ int hot_create(hot_ctx **out, int width, int height, double pitch_m, double wave
   c->lam = wavelength_m;
   c->focal = focal_m;
   c->st = static_cast<cudaStream_t>(cuda_stream);
+  {  // fixed-point scale of the field sums: |sum| <= N, kept below 2^61
+    int bits = 0;
+    while ((1LL << bits) < (long long)width * height) bits++;
+    c->fx_shift = 61 - bits;
+  }
   int rc = HOT_OK;
   cudaError_t e = cudaGetDevice(&c->dev);
   if (e != cudaSuccess) rc = fail(HOT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   const size_t N = (size_t)width * height;
   if (rc == HOT_OK) rc = dalloc(&c->phi, N);
   if (rc == HOT_OK) rc = dalloc(&c->metrics, 2);
-  if (rc == HOT_OK) rc = dalloc(&c->ticket, 1);
   if (rc == HOT_OK) {
     e = cudaMemsetAsync(c->phi, 0, N * sizeof(float), c->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->ticket, 0, sizeof(unsigned int), c->st);
     if (e != cudaSuccess) rc = fail(HOT_ECUDA, "hot_create: %s", cudaGetErrorString(e));
   }
   if (rc != HOT_OK) {
@@ -401,7 +403,6 @@ void hot_destroy(hot_ctx *c) {
   dfree(c->sub);
   dfree(c->first);
   dfree(c->metrics);
-  dfree(c->ticket);
   dfree(c->u8);
   delete c;
 }
@@ -443,18 +444,16 @@ int hot_set_traps(hot_ctx *c, int M, const double *xyz_m, const double *w0) {
       free(wh);
       return rc;
     }
-    const size_t nt = (size_t)c->n_sub;
     rc = dalloc(&c->abc, 3 * (size_t)M);
     if (rc == HOT_OK) rc = dalloc(&c->Xt, (size_t)M * c->W);
     if (rc == HOT_OK) rc = dalloc(&c->Xr, (size_t)M * c->W);
     if (rc == HOT_OK) rc = dalloc(&c->Yt, (size_t)M * c->H);
     if (rc == HOT_OK) rc = dalloc(&c->Yr, (size_t)M * c->H);
-    if (rc == HOT_OK) rc = dalloc(&c->w, M);
-    if (rc == HOT_OK) rc = dalloc(&c->coef, M);
-    if (rc == HOT_OK) rc = dalloc(&c->V, M);
-    if (rc == HOT_OK) rc = dalloc(&c->partial, (size_t)M * nt);
-    if (rc == HOT_OK) rc = dalloc(&c->amp, M);
-    if (rc == HOT_OK) rc = dalloc(&c->arg, M);
+    if (rc == HOT_OK) rc = dalloc(&c->w, 2 * (size_t)M);
+    if (rc == HOT_OK) rc = dalloc(&c->acc, 6 * (size_t)M);
+    if (rc == HOT_OK) rc = dalloc(&c->Vsum, 2 * (size_t)M);
+    if (rc == HOT_OK && cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * 6 * M, c->st) != cudaSuccess)
+      rc = fail(HOT_ECUDA, "hot_set_traps: clearing the field accumulators failed");
     if (rc != HOT_OK) {
       free_traps(c);
       free(abc);
@@ -562,14 +561,15 @@ int hot_get_fields(hot_ctx *c, double *V, double *w) {
   if (!c) return fail(HOT_EINVAL, "hot_get_fields: NULL context");
   if (!c->M) return fail(HOT_ESTATE, "hot_get_fields: no traps set");
   if (V && !c->have_fields) return fail(HOT_ESTATE, "hot_get_fields: no forward evaluation since the last change");
-  std::vector<float4> vf(V ? c->M : 0);
+  std::vector<long long> vs(V ? 2 * c->M : 0);
   std::vector<float> wf(w ? c->M : 0);
-  if (V) HOT_CUDA(cudaMemcpyAsync(vf.data(), c->V, sizeof(float4) * c->M, cudaMemcpyDeviceToHost, c->st));
+  if (V) HOT_CUDA(cudaMemcpyAsync(vs.data(), c->Vsum, sizeof(long long) * 2 * c->M, cudaMemcpyDeviceToHost, c->st));
   if (w) HOT_CUDA(cudaMemcpyAsync(wf.data(), c->w, sizeof(float) * c->M, cudaMemcpyDeviceToHost, c->st));
   HOT_CUDA(cudaStreamSynchronize(c->st));
-  for (int m = 0; V && m < c->M; m++) {  // float-float -> double
-    V[2 * m] = (double)vf[m].x + (double)vf[m].z;
-    V[2 * m + 1] = (double)vf[m].y + (double)vf[m].w;
+  const double inv = 1.0 / ((double)c->W * (double)c->H * ldexp(1.0, c->fx_shift));
+  for (int m = 0; V && m < c->M; m++) {  // fixed-point sums -> V_m
+    V[2 * m] = (double)vs[m] * inv;
+    V[2 * m + 1] = (double)vs[c->M + m] * inv;
   }
   for (int m = 0; w && m < c->M; m++) w[m] = wf[m];
   return HOT_OK;
@@ -691,13 +691,14 @@ __global__ void noalloc_abc_kernel(int M, const double *xyz, double lin, double 
   }
 }
 
-// Float-float fields and metrics of the finish kernel -> the caller's double outputs.
-__global__ void noalloc_out_kernel(int M, const float4 *Vf, const float *metrics, double *V, double *eu) {
+// Fixed-point field sums and metrics of the step kernel -> the caller's double outputs.
+__global__ void noalloc_out_kernel(int M, const long long *Vsum, float, int width, int height, int fx_shift,
+                                   const float *metrics, double *V, double *eu) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const double inv = 1.0 / ((double)width * (double)height * ldexp(1.0, fx_shift));
   if (m < M) {
-    const float4 v = Vf[m];
-    V[2 * m] = (double)v.x + (double)v.z;
-    V[2 * m + 1] = (double)v.y + (double)v.w;
+    V[2 * m] = (double)Vsum[m] * inv;
+    V[2 * m + 1] = (double)Vsum[M + m] * inv;
   }
   if (eu && m == 0) {
     eu[0] = metrics[0];
@@ -750,10 +751,8 @@ extern "C" int hot_field_noalloc(int width, int height, double pitch_m, double w
   const size_t o_xt = take(sizeof(float) * (size_t)M * width), o_xr = take(sizeof(float) * (size_t)M * width);
   const size_t o_yt = take(sizeof(float) * (size_t)M * height), o_yr = take(sizeof(float) * (size_t)M * height);
   const size_t o_sub = take(sizeof(hot::SubTile) * n_sub), o_first = take(sizeof(int) * (G + 1));
-  const size_t o_part = take(sizeof(float2) * (size_t)M * n_sub);
-  const size_t o_V = take(sizeof(float4) * M), o_w = take(sizeof(float) * M), o_coef = take(sizeof(float2) * M);
-  const size_t o_amp = take(sizeof(float) * M), o_arg = take(sizeof(float) * M);
-  const size_t o_met = take(sizeof(float) * 2), o_ticket = take(sizeof(unsigned int));
+  const size_t o_acc = take(sizeof(unsigned long long) * 6 * M), o_vsum = take(sizeof(long long) * 2 * M);
+  const size_t o_w = take(sizeof(float) * M), o_met = take(sizeof(float) * 2);
   if (off > HOT_NOALLOC_SCRATCH_BYTES)
     return fail(HOT_EINVAL, "hot_field_noalloc: %d x %d pixels and %d traps need %zu bytes of scratch, the limit is %u",
                 width, height, M, off, (unsigned)HOT_NOALLOC_SCRATCH_BYTES);
@@ -765,20 +764,16 @@ extern "C" int hot_field_noalloc(int width, int height, double pitch_m, double w
   float *Yt = reinterpret_cast<float *>(base + o_yt), *Yr = reinterpret_cast<float *>(base + o_yr);
   hot::SubTile *d_sub = reinterpret_cast<hot::SubTile *>(base + o_sub);
   int *d_first = reinterpret_cast<int *>(base + o_first);
-  float2 *partial = reinterpret_cast<float2 *>(base + o_part);
-  float4 *Vf = reinterpret_cast<float4 *>(base + o_V);
+  unsigned long long *acc = reinterpret_cast<unsigned long long *>(base + o_acc);
+  long long *Vsum = reinterpret_cast<long long *>(base + o_vsum);
   float *w = reinterpret_cast<float *>(base + o_w);
-  float2 *coef = reinterpret_cast<float2 *>(base + o_coef);
-  float *amp = reinterpret_cast<float *>(base + o_amp), *arg = reinterpret_cast<float *>(base + o_arg);
   float *metrics = reinterpret_cast<float *>(base + o_met);
-  unsigned int *ticket = reinterpret_cast<unsigned int *>(base + o_ticket);
 
-  // The schedule is written on the device; weights and the reduction counter start at zero
-  // (the array keeps whatever the previous call left).
+  // The schedule is written on the device; the accumulators start at zero (the array keeps
+  // whatever the previous call left).
   noalloc_schedule_kernel<<<(G + 1 + 255) / 256, 256, 0, st>>>(U, G, height, d_sub, d_first);
   HOT_CUDA(cudaGetLastError());
-  HOT_CUDA(cudaMemsetAsync(w, 0, sizeof(float) * M, st));
-  HOT_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st));
+  HOT_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 6 * M, st));
 
   const double lin = pitch_m / (wavelength_m * focal_m);
   const double quad = pitch_m * pitch_m / (2.0 * wavelength_m * focal_m * focal_m);
@@ -789,40 +784,42 @@ extern "C" int hot_field_noalloc(int width, int height, double pitch_m, double w
   hot::build_tables_kernel<<<tb, 256, 0, st>>>(width, height, M, abc, Xt, Yt, Xr, Yr);
   HOT_CUDA(cudaGetLastError());
 
+  int bits = 0;
+  while ((1LL << bits) < (long long)width * height) bits++;
+  const int fx_shift = 61 - bits;
   hot::StepArgs a;
   a.W = width;
   a.H = height;
   a.M = M;
-  a.n_sub = n_sub;
   a.sub = d_sub;
   a.first = d_first;
   a.X = fast ? Xr : Xt;
   a.Y = fast ? Yr : Yt;
-  a.coef = coef;
   a.phi = const_cast<float *>(phi);  // the forward-only kernel reads the phases and writes none
-  a.partial = partial;
+  a.acc_in = acc + 4 * (size_t)M;
+  a.acc_out = acc;
+  a.acc_clear = acc + 2 * (size_t)M;
+  a.w_in = w;
+  a.w_out = w;
+  a.fx_scale = ldexpf(1.0f, fx_shift);
+  a.inv_fx_n = (float)(1.0 / ((double)width * (double)height * ldexp(1.0, fx_shift)));
+  a.angle_units = fast ? 1.0f : 0.15915494309189535f;
   const int smem = hot::step_smem_bytes(M, false);
   if (fast) hot::gsw_step_kernel<true, false, true><<<G, hot::kThreads, smem, st>>>(a);
   else hot::gsw_step_kernel<false, false, true><<<G, hot::kThreads, smem, st>>>(a);
   HOT_CUDA(cudaGetLastError());
-
-  hot::FinishArgs f;
+  hot::FinalizeArgs f;
   f.M = M;
-  f.n_tiles = n_sub;
-  f.update = 0;
-  f.inv_n = (float)(1.0 / ((double)width * (double)height));
-  f.angle_units = fast ? 1.0f : 0.15915494309189535f;
-  f.partial = partial;
-  f.V = Vf;
-  f.w = w;
-  f.coef = coef;
+  f.acc = acc;
+  f.acc_all = acc;
+  f.w_src = w;
+  f.w_dst = w;
+  f.Vsum = Vsum;
   f.metrics = metrics;
-  f.amp = amp;
-  f.arg = arg;
-  f.ticket = ticket;
-  hot::gsw_finish_kernel<<<M, hot::kFinishThreads, 0, st>>>(f);
+  f.inv_fx_n = a.inv_fx_n;
+  hot::gsw_finalize_kernel<<<1, hot::kFinalizeThreads, 0, st>>>(f);
   HOT_CUDA(cudaGetLastError());
-  noalloc_out_kernel<<<(M + 255) / 256, 256, 0, st>>>(M, Vf, metrics, V, eu);
+  noalloc_out_kernel<<<(M + 255) / 256, 256, 0, st>>>(M, Vsum, a.inv_fx_n, width, height, fx_shift, metrics, V, eu);
   HOT_CUDA(cudaGetLastError());
   return HOT_OK;
 }
