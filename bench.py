@@ -40,8 +40,8 @@ L2_FLUSH_BYTES = 256 << 20     # > 129 MB L2
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--workload", default="rand100_512")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -87,6 +87,12 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_first_sample(self, timeout: float = 5.0):
+        """Blocks until nvidia-smi has printed one sample (so the timed region is covered)."""
+        t0 = time.time()
+        while self.proc and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.01)
 
     def __exit__(self, *exc):
         if self.proc:
@@ -226,6 +232,7 @@ def run_engine(args):
     torch.cuda.synchronize()
     launches0 = h.launches
     with ClockSampler(local) as clk:
+        clk.wait_first_sample()
         for i in range(args.steps):
             flush.fill_(float(i))
             ev[i][0].record(stream)
@@ -235,10 +242,31 @@ def run_engine(args):
     launches = h.launches - launches0
     if world > 1:
         dist.barrier()
+    # Dominant kernel: one step-kernel launch per GSW iteration.  Its duration in the real
+    # (graph-replayed, programmatically dependent) pipeline is the marginal time of an
+    # iteration: CUDA events around hot_gsw(K) and hot_gsw(K_small) on the launching stream.
+    k_small = max(1, w.iters // 3)
+    n_roof = min(args.steps, 50)
+    evk = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(n_roof)]
+    for i in range(n_roof):
+        flush.fill_(float(i))
+        h.set_phase(phi0)
+        evk[i][0].record(stream)
+        h.gsw(w.iters, metrics=False)
+        evk[i][1].record(stream)
+        flush.fill_(float(i))
+        h.set_phase(phi0)
+        evk[i][2].record(stream)
+        h.gsw(k_small, metrics=False)
+        evk[i][3].record(stream)
+    torch.cuda.synchronize()
+    per_iter = sorted((e[0].elapsed_time(e[1]) - e[2].elapsed_time(e[3])) / (w.iters - k_small) for e in evk)
+    iter_ms = per_iter[len(per_iter) // 2]
     # per-kernel device times: the same steps again, kernels launched one by one between
     # CUDA events on the launching stream (the timed region above replays CUDA graphs)
+    n_prof = min(args.steps, 20)
     h.profile(True)
-    for i in range(args.steps):
+    for i in range(n_prof):
         flush.fill_(float(i))
         step()
     prof = h.profile_read()
@@ -251,9 +279,10 @@ def run_engine(args):
     updates_per_step = w.N * w.M * w.iters
     value = world * updates_per_step * args.steps / (total_ms * 1e-3)
 
-    # roofline of the dominant kernel (fused back-projection + forward, one iteration/launch)
+    # roofline of the dominant kernel (weight update + back-projection + forward field of one
+    # GSW iteration per launch)
     step_kernel_ms, step_kernel_n = prof["step"]
-    avg_launch_s = step_kernel_ms * 1e-3 / max(step_kernel_n, 1)
+    avg_launch_s = iter_ms * 1e-3
     achieved = w.N * w.M / avg_launch_s
     dev = torch.cuda.get_device_properties(local)
     sm_max_mhz = 2070.0
@@ -261,6 +290,7 @@ def run_engine(args):
     if os.path.exists(peaks_path):
         sm_max_mhz = float(json.load(open(peaks_path)).get("sm_max_mhz", sm_max_mhz))
     peak = dev.multi_processor_count * SFU_LANES_PER_SM * sm_max_mhz * 1e6 / SFU_OPS_PER_UPDATE
+    sfu_measured = hot.hot_sfu_rate(0)[0]
     traffic = profiled_traffic(args.workload)
     kernel_share = {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4)
                     for k, v in prof.items()}
@@ -284,14 +314,15 @@ def run_engine(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    n_e2e = min(args.steps, 200)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(n_e2e):
         eu = e2e_step()
     torch.cuda.synchronize()
     e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
-    e2e_value = world * updates_per_step * args.steps / float(e2e_s.item())
+    e2e_value = world * updates_per_step * n_e2e / float(e2e_s.item())
     h2d = w.N * 4 + w.M * 3 * 8 + w.M * 8
     d2h = w.N * (1 if w.quantize else 4) + 16
 
@@ -309,13 +340,17 @@ def run_engine(args):
             "holograms_per_s": world * args.steps / (total_ms * 1e-3),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "updates/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "gsw_tile_kernel<fast, back, fwd> (one GSW iteration per launch)",
+                         "kernel": "gsw_step_kernel<fast, back, fwd> (one GSW iteration per launch)",
                          "peak_basis": f"{dev.multi_processor_count} SMs x {SFU_LANES_PER_SM} SFU "
                                        f"lanes/clk x {sm_max_mhz:.0f} MHz / {SFU_OPS_PER_UPDATE} "
                                        "SFU ops per update",
-                         "avg_launch_us": avg_launch_s * 1e6, "launches": step_kernel_n},
+                         "sfu_lanes_per_clk_per_sm_measured": round(sfu_measured, 2),
+                         "avg_launch_us": avg_launch_s * 1e6,
+                         "launch_timing": f"marginal iteration time of graph-replayed hot_gsw({w.iters}) "
+                                          f"vs hot_gsw({k_small}), CUDA events, median of {n_roof}",
+                         "avg_launch_us_unpipelined": step_kernel_ms * 1e3 / max(step_kernel_n, 1)},
             "kernel_time_share": kernel_share,
-            "kernel_time_ms": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
+            "kernel_time_ms": {k: round(v[0] / n_prof, 4) for k, v in prof.items()},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "api": "hot_set_traps + hot_set_phase (pinned host) + hot_gsw + hot_phase_out (host)",
                     "final_e": eu[0], "final_u": eu[1]},

@@ -140,6 +140,15 @@ int hot_profile_read(hot_ctx *c, double *ms, long long *launches);
 /* Frees the context and its device buffers (NULL-safe). */
 void hot_destroy(hot_ctx *c);
 
+/* Instrumentation (no counterpart in the paper): measures, on the current device, the
+ * throughput of the special-function unit that bounds hot_gsw in HOT_PREC_FAST mode, in
+ * lane results per clock per SM, with a dependency-free loop of 1024 threads per SM whose
+ * arguments change every iteration (clock64-timed).  op: 0 = sin.approx and cos.approx of
+ * one argument (the pattern of the GSW kernels), 1 = sin.approx alone, 2 = ex2.approx.
+ * *per_clk_per_sm receives the rate and *sms (nullable) the SM count.  Synchronises the
+ * device; takes a few milliseconds. */
+int hot_sfu_rate(int op, double *per_clk_per_sm, int *sms);
+
 /* Text of the last error on the calling thread ("" if none). */
 const char *hot_last_error(void);
 

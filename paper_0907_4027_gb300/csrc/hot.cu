@@ -625,6 +625,77 @@ int hot_profile_read(hot_ctx *c, double *ms, long long *launches) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------------
+// SFU throughput probe (hot_sfu_rate).
+namespace {
+
+template <int OP>
+__global__ void __launch_bounds__(1024) sfu_rate_kernel(float *out, long long *cycles, int iters, float step) {
+  float acc[8], x[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    x[i] = 0.37f * i + 1e-3f * (threadIdx.x & 63) - 3.0f;
+    acc[i] = 0.f;
+  }
+  __syncthreads();
+  const long long t0 = clock64();
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      x[i] += step;  // a new argument every iteration
+      if (OP == 0) {
+        acc[i] = fmaf(hot::sin_approx(x[i]), hot::cos_approx(x[i]), acc[i]);
+      } else if (OP == 1) {
+        acc[i] += hot::sin_approx(x[i]);
+      } else {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x[i] * 0.001f));
+        acc[i] += y;
+      }
+    }
+  }
+  __syncthreads();
+  const long long t1 = clock64();
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; i++) s += acc[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
+}  // namespace
+
+extern "C" int hot_sfu_rate(int op, double *per_clk_per_sm, int *sms) {
+  if (!per_clk_per_sm || op < 0 || op > 2) return fail(HOT_EINVAL, "hot_sfu_rate: invalid argument");
+  int dev = 0, n = 0;
+  HOT_CUDA(cudaGetDevice(&dev));
+  HOT_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  const int threads = 1024, iters = 2048;
+  float *out = nullptr;
+  long long *cyc = nullptr;
+  int rc = dalloc(&out, (size_t)n * threads);
+  if (rc == HOT_OK) rc = dalloc(&cyc, (size_t)n);
+  std::vector<long long> h(n);
+  for (int rep = 0; rc == HOT_OK && rep < 2; rep++) {  // the first run warms up
+    if (op == 0) sfu_rate_kernel<0><<<n, threads>>>(out, cyc, iters, 1e-4f);
+    else if (op == 1) sfu_rate_kernel<1><<<n, threads>>>(out, cyc, iters, 1e-4f);
+    else sfu_rate_kernel<2><<<n, threads>>>(out, cyc, iters, 1e-4f);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, sizeof(long long) * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = fail(HOT_ECUDA, "hot_sfu_rate: %s", cudaGetErrorString(e));
+  }
+  dfree(out);
+  dfree(cyc);
+  if (rc != HOT_OK) return rc;
+  double mean = 0.0;
+  for (long long v : h) mean += (double)v;
+  mean /= n;
+  const double results = (op == 0 ? 2.0 : 1.0) * threads * (double)iters * 8;  // per block (= per SM)
+  *per_clk_per_sm = results / mean;
+  if (sms) *sms = n;
+  return HOT_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Allocation-free trap-field evaluation (hot_field_noalloc): all working memory is carved out
 // of one file-scope device array, whose device address is looked up once per device.
 namespace {

@@ -48,6 +48,7 @@ SIGNATURES = {
     "hot_profile_read": (_c_int, [_vp, _vp, _vp]),
     "hot_destroy": (None, [_vp]),
     "hot_last_error": (ctypes.c_char_p, []),
+    "hot_sfu_rate": (_c_int, [_c_int, _dp, ctypes.POINTER(_c_int)]),
     "hot_field_noalloc": (_c_int, [_c_int, _c_int, _c_double, _c_double, _c_double, _c_int, _vp, _vp, _c_int,
                                    _vp, _vp, _vp]),
 }
@@ -180,6 +181,14 @@ def hot_profile_read(ctx: int) -> dict:
 
 def hot_destroy(ctx: int) -> None:
     lib.hot_destroy(_vp(ctx))
+
+
+def hot_sfu_rate(op: int = 0):
+    """(SFU lane results per clock per SM, SM count) for op 0 = sin+cos of one argument,
+    1 = sin alone, 2 = ex2 (measured on the current device)."""
+    r, n = ctypes.c_double(), _c_int()
+    _ok(lib.hot_sfu_rate(int(op), ctypes.byref(r), ctypes.byref(n)), "hot_sfu_rate")
+    return r.value, n.value
 
 
 HOT_NOALLOC_SCRATCH_BYTES = 16 << 20
