@@ -114,6 +114,21 @@ int hot_get_fields(hot_ctx *c, double *V, double *w);
  * one. */
 int hot_use_graphs(hot_ctx *c, int enable);
 
+/* Trap fields of arbitrary phases (Eq. 1) for the context's traps, without touching its GSW
+ * state (phases, weights): V_m = (1/N) sum_j exp(i (phi_j - Delta_j^m)).
+ * phi: DEVICE float32 [N] row-major; V: DEVICE float32 [2*M] output, interleaved (Re, Im).
+ * Queued on the context's stream.  hot_get_fields afterwards returns these fields.
+ * HOT_ESTATE before hot_set_traps. */
+int hot_field(hot_ctx *c, const float *phi, float *V);
+
+/* Adjoint of Eq. 1, i.e. the gradient of a real loss L(V) with respect to the phases:
+ *   dL/dphi_j = (1/N) Im[ exp(-i phi_j) sum_m G_m exp(i Delta_j^m) ],  G_m = 2 dL/d conj(V_m)
+ * (the PyTorch convention for the gradient of a complex tensor).  It is the back-projection
+ * superposition of Sec. 4 with coefficients G_m.  phi: DEVICE float32 [N]; G: DEVICE float32
+ * [2*M] interleaved; grad: DEVICE float32 [N] output.  Queued on the context's stream; the
+ * GSW state is not touched.  HOT_ESTATE before hot_set_traps. */
+int hot_field_adjoint(hot_ctx *c, const float *phi, const float *G, float *grad);
+
 /* Waits for all work queued by the context. */
 int hot_sync(hot_ctx *c);
 

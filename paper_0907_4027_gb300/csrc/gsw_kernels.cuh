@@ -59,6 +59,10 @@ struct StepArgs {
   // FWD: forward field of this launch's phases
   unsigned long long *acc_out;       // [2][M] zero on entry (cleared by the launch before last)
   unsigned long long *acc_clear;     // [2][M] cleared here for the next launch
+  // ADJ: adjoint of Eq. 1 -- coefficients G_m (Re, Im) and the gradient output
+  const float2 *G;                   // [M] upstream G_m = 2 dL/d conj(V_m)
+  float *grad;                       // [H*W] out: dL/dphi_j
+  float inv_n;                       // 1 / N
   float fx_scale;           // 2^fx_shift: fixed-point scale of the sums
   float inv_fx_n;           // 1 / (N 2^fx_shift)
   float angle_units;        // 1 (radians) or 1/(2 pi) (turns): units of the tables
@@ -135,10 +139,17 @@ __device__ __forceinline__ float2 coefficient(const StepArgs &a, int m, float me
   return make_float2(w, am >= 1e-30f ? atan2f(v.y, v.x) * a.angle_units : 0.f);
 }
 
+// Adjoint coefficient of trap m in polar form (|G_m|, arg G_m).
+__device__ __forceinline__ float2 adjoint_coefficient(const StepArgs &a, int m) {
+  const float2 g = a.G[m];
+  return make_float2(sqrtf(g.x * g.x + g.y * g.y), atan2f(g.y, g.x) * a.angle_units);
+}
+
 // Stages, with asynchronous copies (all in flight at once), the X (32 columns from x0) and Y
-// (rows y0 .. y0+rows-1) tables of traps [m0, m0+n), plus their coefficients when BACK.
+// (rows y0 .. y0+rows-1) tables of traps [m0, m0+n), plus their coefficients when BACK
+// (GSW coefficients, or adjoint coefficients when ADJ).
 // The caller synchronises the block afterwards.
-template <bool BACK>
+template <bool BACK, bool ADJ = false>
 __device__ __forceinline__ void stage_tables(const StepArgs &a, int m0, int n, const SubTile &st,
                                              float *Xs, float *Ys, float2 *Cs, bool xy = true,
                                              float mean = 0.f) {
@@ -153,7 +164,8 @@ __device__ __forceinline__ void stage_tables(const StepArgs &a, int m0, int n, c
     cp_async4(Ys + i, a.Y + (ok ? (size_t)(m0 + k) * a.H + st.y0 + r : 0), ok);
   }
   if (BACK)
-    for (int i = threadIdx.x; i < n; i += kThreads) Cs[i] = coefficient(a, m0 + i, mean);
+    for (int i = threadIdx.x; i < n; i += kThreads)
+      Cs[i] = ADJ ? adjoint_coefficient(a, m0 + i) : coefficient(a, m0 + i, mean);
   cp_async_wait_all();
 }
 
@@ -374,11 +386,16 @@ __global__ void __launch_bounds__(kFinalizeThreads) gsw_finalize_kernel(Finalize
     default: { constexpr int R = 14; BODY; } break; \
   }
 static_assert(kRowsMax == 14, "HOT_WITH_ROWS covers 1..14 rows");
+static_assert(kRowsMax % 2 == 0 && kRowsMax / 2 <= kWarps, "each warp finishes one row per half of a sub-tile");
 
 // Persistent blocks, one wave; the 8 warps of a block split the traps of each chunk.
 // BACK: weight update and back-projection -> a.phi.  FWD: forward field of the sub-tile phases.
-template <bool FAST, bool BACK, bool FWD>
+// ADJ (with BACK, without FWD): the adjoint of Eq. 1 instead -- the same superposition with
+// coefficients G_m, S_j = sum_m G_m e^{i Delta_j^m}, written as the gradient
+// dL/dphi_j = (1/N) Im[e^{-i phi_j} S_j] of a real loss L(V) (a.phi is read, not written).
+template <bool FAST, bool BACK, bool FWD, bool ADJ = false>
 __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
+  static_assert(!ADJ || (BACK && !FWD), "the adjoint is a back-projection without forward field");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float *Xs = reinterpret_cast<float *>(smem_raw);
   float *Ys = Xs + kXsFloats;
@@ -404,7 +421,7 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
   if (FWD)  // the buffer the next launch accumulates into
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
   float mean = 0.f;
-  if (BACK) {
+  if (BACK && !ADJ) {
     mean = mean_field_amplitude(a);
     for (int m = blockIdx.x + gridDim.x * threadIdx.x; m < a.M; m += gridDim.x * kThreads)
       a.w_out[m] = coefficient(a, m, mean).x;
@@ -422,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
       for (int ch = 0; ch < nchunks; ch++) {
         const int m0 = ch * mc, n = min(mc, a.M - m0);
         __syncthreads();  // earlier readers of the tables are done
-        stage_tables<true>(a, m0, n, st, Xs, Ys, Cs, !prestaged, mean);
+        stage_tables<true, ADJ>(a, m0, n, st, Xs, Ys, Cs, !prestaged, mean);
         prestaged = false;
         __syncthreads();
         const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
@@ -446,9 +463,18 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
             s.x += q.x;
             s.y += q.y;
           }
-          const float ph = atan2f(s.y, s.x);
-          if (col_ok) a.phi[(size_t)(st.y0 + r) * a.W + ix] = ph;
-          if (FWD) Ps[r * kTileW + lane] = phase_units<FAST>(ph);
+          const size_t j = (size_t)(st.y0 + r) * a.W + ix;
+          if (ADJ) {
+            if (col_ok) {
+              float sp, cp;
+              sincosf(a.phi[j], &sp, &cp);
+              a.grad[j] = (cp * s.y - sp * s.x) * a.inv_n;  // Im[(cos - i sin)(S.x + i S.y)] / N
+            }
+          } else {
+            const float ph = atan2f(s.y, s.x);
+            if (col_ok) a.phi[j] = ph;
+            if (FWD) Ps[r * kTileW + lane] = phase_units<FAST>(ph);
+          }
         }
       }
     } else if (FWD) {
@@ -503,6 +529,12 @@ __global__ void build_tables_kernel(int W, int H, int M, const double *abc, floa
       Yr[(size_t)m * H + (i - W)] = rf;
     }
   }
+}
+
+// Fixed-point field sums -> float32 complex fields V_m (for callers of hot_field).
+__global__ void sums_to_fields_kernel(int M, const long long *Vsum, double inv, float2 *V) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < M) V[m] = make_float2((float)((double)Vsum[m] * inv), (float)((double)Vsum[M + m] * inv));
 }
 
 // Sec. 5 encoding of the phases: uint8 g = rint(phi 256 / 2pi) mod 256 (FP32 decision).

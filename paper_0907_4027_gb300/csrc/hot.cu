@@ -182,8 +182,9 @@ void launch(hot_ctx *c, void (*kernel)(KArgs...), int grid, int block, int smem,
 
 // Launch k of a hot_gsw sequence (k = 0: forward field of the starting phases; k >= 1:
 // iteration k).  Accumulators rotate over three buffers, weights over two.
-template <bool FAST, bool BACK, bool FWD>
-int launch_tile(hot_ctx *c, bool pdl, int k) {
+template <bool FAST, bool BACK, bool FWD, bool ADJ = false>
+int launch_tile(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const float2 *G = nullptr,
+                float *grad = nullptr) {
   hot::StepArgs a;
   a.W = c->W;
   a.H = c->H;
@@ -202,9 +203,13 @@ int launch_tile(hot_ctx *c, bool pdl, int k) {
   a.fx_scale = ldexpf(1.0f, c->fx_shift);
   a.inv_fx_n = (float)(1.0 / ((double)c->W * (double)c->H * ldexp(1.0, c->fx_shift)));
   a.angle_units = FAST ? 1.0f : 0.15915494309189535f;
+  if (phi) a.phi = const_cast<float *>(phi);  // read only: forward field or adjoint of given phases
+  a.G = G;
+  a.grad = grad;
+  a.inv_n = (float)(1.0 / ((double)c->W * (double)c->H));
   const int smem = hot::step_smem_bytes(c->M, BACK);
   Probe p(c, BACK && FWD ? HOT_KERNEL_STEP : FWD ? HOT_KERNEL_FORWARD : HOT_KERNEL_OTHER);
-  launch(c, hot::gsw_step_kernel<FAST, BACK, FWD>, c->grid, hot::kThreads, smem, pdl, a);
+  launch(c, hot::gsw_step_kernel<FAST, BACK, FWD, ADJ>, c->grid, hot::kThreads, smem, pdl, a);
   return check_launch(c, "gsw_step_kernel");
 }
 
@@ -217,6 +222,8 @@ int set_step_smem(int M) {
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd));
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
   return HOT_OK;
 }
 
@@ -573,6 +580,28 @@ int hot_get_fields(hot_ctx *c, double *V, double *w) {
   }
   for (int m = 0; w && m < c->M; m++) w[m] = wf[m];
   return HOT_OK;
+}
+
+int hot_field(hot_ctx *c, const float *phi, float *V) {
+  if (!c || !phi || !V) return fail(HOT_EINVAL, "hot_field: NULL argument");
+  if (!c->M) return fail(HOT_ESTATE, "hot_field: no traps set");
+  const bool fast = c->precision == HOT_PREC_FAST;
+  int rc = fast ? launch_tile<true, false, true>(c, false, 0, phi) : launch_tile<false, false, true>(c, false, 0, phi);
+  if (rc == HOT_OK) rc = launch_finalize(c, false, 0);  // w stays in w[0]; accumulators cleared
+  if (rc != HOT_OK) return rc;
+  const double inv = 1.0 / ((double)c->W * (double)c->H * ldexp(1.0, c->fx_shift));
+  hot::sums_to_fields_kernel<<<(c->M + 255) / 256, 256, 0, c->st>>>(c->M, c->Vsum, inv, reinterpret_cast<float2 *>(V));
+  rc = check_launch(c, "sums_to_fields_kernel");
+  if (rc == HOT_OK) c->have_fields = true;
+  return rc;
+}
+
+int hot_field_adjoint(hot_ctx *c, const float *phi, const float *G, float *grad) {
+  if (!c || !phi || !G || !grad) return fail(HOT_EINVAL, "hot_field_adjoint: NULL argument");
+  if (!c->M) return fail(HOT_ESTATE, "hot_field_adjoint: no traps set");
+  const float2 *g = reinterpret_cast<const float2 *>(G);
+  return c->precision == HOT_PREC_FAST ? launch_tile<true, true, false, true>(c, false, 0, phi, g, grad)
+                                       : launch_tile<false, true, false, true>(c, false, 0, phi, g, grad);
 }
 
 int hot_sync(hot_ctx *c) {

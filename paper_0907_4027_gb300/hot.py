@@ -42,6 +42,8 @@ SIGNATURES = {
     "hot_phase_out": (_c_int, [_vp, _vp, _c_int, _c_int]),
     "hot_get_fields": (_c_int, [_vp, _vp, _vp]),
     "hot_sync": (_c_int, [_vp]),
+    "hot_field": (_c_int, [_vp, _vp, _vp]),
+    "hot_field_adjoint": (_c_int, [_vp, _vp, _vp, _vp]),
     "hot_kernel_launches": (ctypes.c_longlong, [_vp]),
     "hot_use_graphs": (_c_int, [_vp, _c_int]),
     "hot_profile": (_c_int, [_vp, _c_int]),
@@ -149,6 +151,17 @@ def hot_get_fields(ctx: int, M: int):
     w = np.empty(M)
     _ok(lib.hot_get_fields(_vp(ctx), V.ctypes.data_as(_vp), w.ctypes.data_as(_vp)), "hot_get_fields")
     return V[0::2] + 1j * V[1::2], w
+
+
+def hot_field(ctx: int, phi_dev, V_dev) -> None:
+    """Eq. 1 fields of device phases phi_dev (N float32) into V_dev (2M float32, Re/Im)."""
+    _ok(lib.hot_field(_vp(ctx), _vp(phi_dev.data_ptr()), _vp(V_dev.data_ptr())), "hot_field")
+
+
+def hot_field_adjoint(ctx: int, phi_dev, G_dev, grad_dev) -> None:
+    """Gradient (N float32) of a real loss of V for upstream G_dev = 2 dL/d conj V (2M float32)."""
+    _ok(lib.hot_field_adjoint(_vp(ctx), _vp(phi_dev.data_ptr()), _vp(G_dev.data_ptr()),
+                              _vp(grad_dev.data_ptr())), "hot_field_adjoint")
 
 
 def hot_sync(ctx: int) -> None:
