@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--workload", default="rand100_512")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision-report", action="store_true",
+                    help="errors of both precision modes against the FP64 oracle, per result")
     ap.add_argument("--cpu-sample-iters", type=int, default=0,
                     help="GSW iterations of the CPU-baseline sample (0: the workload's own count)")
     return ap.parse_args()
@@ -421,7 +423,9 @@ def run_adam(args):
         "metric": "Adam steps/s on -sum log I + 10 var I (1024x1024 px, M=256)", "value": w.iters / (ms * 1e-3),
         "unit": "steps/s", "n_gpus": 1, "steps": w.iters, "warmup": 3, "ms_per_step": ms / w.iters,
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(w, {"optimizer": "Adam lr 1e-2 (torch defaults otherwise)"}),
+        "config": {"workload": f"{w.name}: {w.W}x{w.H} px, M={w.M} traps, {w.iters} Adam steps on the phases, "
+                               f"{w.precision} sincos", "W": w.W, "H": w.H, "M": w.M, "steps": w.iters,
+                   "precision": w.precision, "seed": 0, "optimizer": "Adam lr 1e-2 (torch defaults otherwise)"},
         "final": {"loss": loss, "e": e, "u": u, "ms_total": ms},
         "gsw_same_traps": {str(k): v for k, v in gsw.items()},
     }
@@ -430,10 +434,71 @@ def run_adam(args):
     return 0
 
 
+def run_precision_report(args):
+    """Errors of HOT_PREC_ACCURATE and HOT_PREC_FAST against the FP64 oracle, per result, on
+    grid16_256 and rand100_512, with the time per GSW iteration of each mode."""
+    import torch
+    import oracle
+    from paper_0907_4027_gb300 import _build
+    _build.build()
+    from paper_0907_4027_gb300 import hot, workloads as wl
+
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name in ("grid16_256", "rand100_512"):
+        base = wl.NAMED[name]()
+        K = base.iters
+        r1 = oracle.gsw(base.geom, base.xyz, 1, base.phi0)
+        rK = oracle.gsw(base.geom, base.xyz, K, base.phi0)
+        for prec in ("accurate", "fast"):
+            w = wl.NAMED[name]()
+            w.precision = prec
+            h = hot.Hologram.from_workload(w, stream.cuda_stream)
+            h.gsw(1)
+            V1, _ = h.fields()
+            h.set_phase(w.phi0)
+            h.set_weights(np.ones(w.M))
+            h.gsw(K - 1)
+            VK, wK1 = h.fields()
+            e, u = h.gsw(1)
+            phiK = h.phase("f32").astype(np.float64)
+            g = h.phase("u8")
+            # time per iteration (marginal, graph replay)
+            phi0 = torch.tensor(w.phi0, dtype=torch.float32, device="cuda")
+            ts = []
+            for _ in range(5):
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                h.set_phase(phi0); ev[0].record(stream); h.gsw(K, metrics=False); ev[1].record(stream)
+                h.set_phase(phi0); ev[2].record(stream); h.gsw(1, metrics=False); ev[3].record(stream)
+                torch.cuda.synchronize()
+                ts.append((ev[0].elapsed_time(ev[1]) - ev[2].elapsed_time(ev[3])) / (K - 1))
+            h.close()
+            _, coef = oracle.update_weights(VK, wK1)
+            ophi, S = oracle.backproject(w.geom, w.xyz, coef, want_S=True)
+            dphi = np.abs(np.angle(np.exp(1j * (phiK - ophi))))
+            cond = np.abs(S) * dphi / np.sum(np.abs(coef))
+            og = oracle.quantize(ophi)
+            q = ophi / (2 * np.pi / 256)
+            near = np.abs(q - (np.floor(q) + 0.5)) * (2 * np.pi / 256) < 1e-4
+            out[f"{name}/{prec}"] = {
+                "V1_max_rel_err": float(np.max(np.abs(np.abs(V1) - np.abs(r1["V"])) / np.abs(r1["V"]))),
+                "V1_max_abs_err": float(np.max(np.abs(V1 - r1["V"]))),
+                "e_abs_err": abs(e - rK["e"]), "u_abs_err": abs(u - rK["u"]),
+                "phase_err_rad_median": float(np.median(dphi)), "phase_err_rad_p99": float(np.percentile(dphi, 99)),
+                "phase_err_conditioned_max": float(cond.max()),
+                "u8_differ": int(np.sum(g != og)), "u8_differ_not_near_boundary": int(np.sum((g != og) & ~near)),
+                "us_per_iteration": 1e3 * float(np.median(ts)),
+            }
+    print(json.dumps({"metric": "precision report (GPU vs FP64 oracle)", "results": out}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.precision_report:
+        return run_precision_report(args)
     if args.workload == "diff256_1024":
         return run_adam(args)
     return run_engine(args)

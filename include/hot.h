@@ -114,6 +114,15 @@ int hot_get_fields(hot_ctx *c, double *V, double *w);
  * one. */
 int hot_use_graphs(hot_ctx *c, int enable);
 
+/* Back-propagation from the traps with explicit complex coefficients (Sec. 4):
+ *   phi_j = arg sum_m c_m exp(i Delta_j^m),
+ * which become the context's phases.  With c_m = exp(i theta_m), theta_m random, this is the
+ * random superposition (SR) hologram of Eq. 3; GSW can continue from it (hot_gsw), and
+ * hot_gsw(c, 0, &e, &u) reports its efficiency and uniformity.  coef: HOST array of 2*M
+ * doubles interleaved (Re, Im).  The GSW weights are not changed.  HOT_ESTATE before
+ * hot_set_traps. */
+int hot_superposition(hot_ctx *c, const double *coef);
+
 /* Trap fields of arbitrary phases (Eq. 1) for the context's traps, without touching its GSW
  * state (phases, weights): V_m = (1/N) sum_j exp(i (phi_j - Delta_j^m)).
  * phi: DEVICE float32 [N] row-major; V: DEVICE float32 [2*M] output, interleaved (Re, Im).

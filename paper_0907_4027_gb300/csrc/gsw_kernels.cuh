@@ -59,8 +59,9 @@ struct StepArgs {
   // FWD: forward field of this launch's phases
   unsigned long long *acc_out;       // [2][M] zero on entry (cleared by the launch before last)
   unsigned long long *acc_clear;     // [2][M] cleared here for the next launch
-  // ADJ: adjoint of Eq. 1 -- coefficients G_m (Re, Im) and the gradient output
-  const float2 *G;                   // [M] upstream G_m = 2 dL/d conj(V_m)
+  // Explicit coefficients G_m (Re, Im) instead of the GSW update (superposition, adjoint),
+  // and the gradient output of the adjoint (ADJ)
+  const float2 *G;                   // [M] or NULL: coefficients of the back-projection
   float *grad;                       // [H*W] out: dL/dphi_j
   float inv_n;                       // 1 / N
   float fx_scale;           // 2^fx_shift: fixed-point scale of the sums
@@ -139,7 +140,7 @@ __device__ __forceinline__ float2 coefficient(const StepArgs &a, int m, float me
   return make_float2(w, am >= 1e-30f ? atan2f(v.y, v.x) * a.angle_units : 0.f);
 }
 
-// Adjoint coefficient of trap m in polar form (|G_m|, arg G_m).
+// Explicit coefficient of trap m (superposition or adjoint) in polar form (|G_m|, arg G_m).
 __device__ __forceinline__ float2 adjoint_coefficient(const StepArgs &a, int m) {
   const float2 g = a.G[m];
   return make_float2(sqrtf(g.x * g.x + g.y * g.y), atan2f(g.y, g.x) * a.angle_units);
@@ -165,7 +166,7 @@ __device__ __forceinline__ void stage_tables(const StepArgs &a, int m0, int n, c
   }
   if (BACK)
     for (int i = threadIdx.x; i < n; i += kThreads)
-      Cs[i] = ADJ ? adjoint_coefficient(a, m0 + i) : coefficient(a, m0 + i, mean);
+      Cs[i] = (ADJ || a.G) ? adjoint_coefficient(a, m0 + i) : coefficient(a, m0 + i, mean);
   cp_async_wait_all();
 }
 
@@ -421,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
   if (FWD)  // the buffer the next launch accumulates into
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
   float mean = 0.f;
-  if (BACK && !ADJ) {
+  if (BACK && !ADJ && !a.G) {
     mean = mean_field_amplitude(a);
     for (int m = blockIdx.x + gridDim.x * threadIdx.x; m < a.M; m += gridDim.x * kThreads)
       a.w_out[m] = coefficient(a, m, mean).x;

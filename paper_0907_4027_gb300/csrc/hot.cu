@@ -596,6 +596,31 @@ int hot_field(hot_ctx *c, const float *phi, float *V) {
   return rc;
 }
 
+int hot_superposition(hot_ctx *c, const double *coef) {
+  if (!c || !coef) return fail(HOT_EINVAL, "hot_superposition: NULL argument");
+  if (!c->M) return fail(HOT_ESTATE, "hot_superposition: no traps set");
+  std::vector<float> cf(2 * (size_t)c->M);
+  for (int i = 0; i < 2 * c->M; i++) {
+    if (!std::isfinite(coef[i])) return fail(HOT_EINVAL, "hot_superposition: coefficient %d not finite", i / 2);
+    cf[i] = (float)coef[i];
+  }
+  float2 *d = nullptr;
+  int rc = dalloc(&d, c->M);
+  if (rc != HOT_OK) return rc;
+  cudaError_t e = cudaMemcpyAsync(d, cf.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice, c->st);
+  if (e != cudaSuccess) rc = fail(HOT_ECUDA, "hot_superposition: %s", cudaGetErrorString(e));
+  if (rc == HOT_OK)
+    rc = c->precision == HOT_PREC_FAST ? launch_tile<true, true, false>(c, false, 0, nullptr, d)
+                                       : launch_tile<false, true, false>(c, false, 0, nullptr, d);
+  if (rc == HOT_OK) {
+    e = cudaStreamSynchronize(c->st);  // the coefficients are freed below
+    if (e != cudaSuccess) rc = fail(HOT_ECUDA, "hot_superposition: %s", cudaGetErrorString(e));
+  }
+  dfree(d);
+  c->have_fields = false;
+  return rc;
+}
+
 int hot_field_adjoint(hot_ctx *c, const float *phi, const float *G, float *grad) {
   if (!c || !phi || !G || !grad) return fail(HOT_EINVAL, "hot_field_adjoint: NULL argument");
   if (!c->M) return fail(HOT_ESTATE, "hot_field_adjoint: no traps set");

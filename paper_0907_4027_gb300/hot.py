@@ -43,6 +43,7 @@ SIGNATURES = {
     "hot_get_fields": (_c_int, [_vp, _vp, _vp]),
     "hot_sync": (_c_int, [_vp]),
     "hot_field": (_c_int, [_vp, _vp, _vp]),
+    "hot_superposition": (_c_int, [_vp, _vp]),
     "hot_field_adjoint": (_c_int, [_vp, _vp, _vp, _vp]),
     "hot_kernel_launches": (ctypes.c_longlong, [_vp]),
     "hot_use_graphs": (_c_int, [_vp, _c_int]),
@@ -153,6 +154,13 @@ def hot_get_fields(ctx: int, M: int):
     return V[0::2] + 1j * V[1::2], w
 
 
+def hot_superposition(ctx: int, coef) -> None:
+    """phi = arg sum_m coef_m e^{i Delta} becomes the phases (SR for coef = e^{i theta})."""
+    c = np.asarray(coef, dtype=np.complex128).reshape(-1)
+    a, p = _host_ptr(np.stack([c.real, c.imag], axis=-1).reshape(-1), np.float64)
+    _ok(lib.hot_superposition(_vp(ctx), p), "hot_superposition")
+
+
 def hot_field(ctx: int, phi_dev, V_dev) -> None:
     """Eq. 1 fields of device phases phi_dev (N float32) into V_dev (2M float32, Re/Im)."""
     _ok(lib.hot_field(_vp(ctx), _vp(phi_dev.data_ptr()), _vp(V_dev.data_ptr())), "hot_field")
@@ -252,6 +260,9 @@ class Hologram:
 
     def set_phase(self, phi):
         hot_set_phase(self.ctx, phi)
+
+    def superposition(self, coef):
+        hot_superposition(self.ctx, coef)
 
     def set_precision(self, precision):
         hot_set_precision(self.ctx, precision)

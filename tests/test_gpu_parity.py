@@ -214,3 +214,33 @@ def test_rand1000_1920_metrics_and_trap_subset(hot):
     if os.path.exists(path):
         g = json.load(open(path))
         assert abs(e - g["e"]) < ABS_EU and abs(u - g["u"]) < ABS_EU, (e, g["e"], u, g["u"])
+
+
+# ------------------------------------------------------------------ superposition (SR, Eq. 3)
+
+@pytest.mark.parametrize("precision", ["accurate", "fast"])
+def test_superposition_matches_oracle(hot, precision):
+    """Sec. 4 back-propagation with explicit coefficients: random complex c_m, and the SR
+    hologram of Eq. 3 (c_m = e^{i theta_m}) on the 9 x 9 grid of Sec. 5 followed by GSW."""
+    w = wl.random_case(70, 41, 17, seed=2, precision=precision)
+    rng = np.random.default_rng(5)
+    c = rng.normal(size=w.M) + 1j * rng.normal(size=w.M)
+    with make(hot, w) as h:
+        h.superposition(c)
+        phi = h.phase("f32")
+    check_phase_step(phi, w, c, TOL_S[precision])
+
+    g = wl.paper_grid(9, W=256)
+    g.precision = precision
+    th = np.random.default_rng(0).uniform(0, 2 * np.pi, g.M)
+    with make(hot, g) as h:
+        h.superposition(np.exp(1j * th))
+        phi_sr = h.phase("f32").astype(np.float64)
+        e_sr, u_sr = h.gsw(0)
+        e1, u1 = h.gsw(1)
+    o_sr = oracle.backproject(g.geom, g.xyz, np.exp(1j * th))
+    oe, ou = oracle.metrics(oracle.forward(g.geom, g.xyz, o_sr))
+    assert abs(e_sr - oe) < ABS_EU and abs(u_sr - ou) < ABS_EU
+    r1 = oracle.gsw(g.geom, g.xyz, 1, phi_sr)
+    assert abs(e1 - r1["e"]) < ABS_EU and abs(u1 - r1["u"]) < ABS_EU
+    assert u_sr < 0.15 and e_sr > 0.7 and u1 >= u_sr      # Sec. 5: SR is inefficient and non-uniform
