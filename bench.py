@@ -222,6 +222,12 @@ def run_engine(args):
         h.gsw(w.iters, metrics=False)
         h.phase(fmt, out=out)
 
+    # tiling picked by the autotuner (untimed setup; phases and weights are kept)
+    h.set_phase(phi0)
+    t_tune = time.perf_counter()
+    tuned = h.autotune(w.iters)
+    tuned["seconds"] = time.perf_counter() - t_tune
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -336,6 +342,9 @@ def run_engine(args):
             "config": workload_config(w, {
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                 "l2": "flushed between steps (256 MB write outside the step events)",
+                "tiling": {k: tuned[k] for k in ("rows", "blocks_per_sm", "chunk")},
+                "autotune": {"us_per_iter": tuned["us_per_iter"], "seconds": round(tuned["seconds"], 3),
+                             "search": "coordinate search over rows/blocks_per_sm/chunk, best of 3 graph replays"},
                 "timing": "CUDA events per step on the launching stream, summed; hot_gsw replays "
                           "one CUDA graph per call; roofline kernel times from a second pass of "
                           "the same steps with per-launch events"}),
@@ -493,10 +502,94 @@ def run_precision_report(args):
     return 0
 
 
+def run_batch(args):
+    """Batched form (batch64): 64 holograms, sizes from {512^2, 1024^2, 1920x1152}, M ~ U{8..2000},
+    30 GSW iterations per hologram in one CUDA graph (shortest-first groups, one launch per group
+    and iteration), autotuned tiling, fast sincos.  Holograms/s and per-hologram latency (device
+    timer stamps from the start of the graph to each hologram's completion), beside the same
+    holograms run one by one through hot_gsw."""
+    import torch
+    from paper_0907_4027_gb300 import _build
+    _build.build()
+    from paper_0907_4027_gb300 import hot, workloads as wl
+
+    ws = wl.batch64()
+    stream = torch.cuda.current_stream()
+    holos = [hot.Hologram.from_workload(w, stream.cuda_stream) for w in ws]
+    K = ws[0].iters
+    pairs = sum(w.N * w.M for w in ws) * K
+
+    def reset():
+        for h, w in zip(holos, ws):
+            h.set_phase(w.phi0)
+            h.set_weights(np.ones(w.M))
+
+    batch = hot.Batch(holos, stream.cuda_stream)
+    t_tune = time.perf_counter()
+    tuned = batch.autotune(2)
+    t_tune = time.perf_counter() - t_tune
+    tiling = batch.tiling()
+    reps = max(1, min(args.steps, 5))
+    total, lats = [], []
+    for i in range(reps + 1):
+        reset()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        batch.gsw(K)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        if i:  # i = 0: graph capture and warm-up
+            total.append(ev[0].elapsed_time(ev[1]))
+            lats.append(batch.latency())
+    batch_ms = float(np.median(total))
+    lat = np.concatenate(lats)
+    eu_batch = batch.metrics()
+    batch.close()
+    # the same holograms one by one (each its own hot_gsw graph, default tiling), in the given order
+    for h in holos:
+        h.gsw(K, metrics=False)
+    reset()
+    torch.cuda.synchronize()
+    ev_all = [torch.cuda.Event(enable_timing=True) for _ in range(len(holos) + 1)]
+    ev_all[0].record(stream)
+    for i, h in enumerate(holos):
+        h.gsw(K, metrics=False)
+        ev_all[i + 1].record(stream)
+    torch.cuda.synchronize()
+    seq_lat = np.array([ev_all[0].elapsed_time(ev_all[i + 1]) for i in range(len(holos))])
+    eu_seq = [h.metrics() for h in holos]
+    for h in holos:
+        h.close()
+    d_e = max(abs(x[0] - y[0]) for x, y in zip(eu_batch, eu_seq))
+    d_u = max(abs(x[1] - y[1]) for x, y in zip(eu_batch, eu_seq))
+    line = {
+        "metric": "holograms/s, batch of 64 uneven holograms (30 GSW iterations each)",
+        "value": len(ws) / (batch_ms * 1e-3), "unit": "holograms/s", "n_gpus": 1, "steps": reps,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch64: 64 holograms, sizes from {512^2, 1024^2, 1920x1152}, M ~ U{8..2000}, "
+                               "30 GSW iterations in one CUDA graph, fast sincos", "seed": 0},
+        "batch": {"ms": batch_ms, "updates_per_s": pairs / (batch_ms * 1e-3),
+                  "latency_ms_p50": float(np.percentile(lat, 50)),
+                  "latency_ms_p99": float(np.percentile(lat, 99)),
+                  "latency": "device %globaltimer: start of the first launch to each hologram's finalize",
+                  "tiling": tiling, "autotune": dict(tuned, seconds=t_tune, iters=2)},
+        "sequential": {"ms": float(seq_lat[-1]), "holograms_per_s": len(ws) / (seq_lat[-1] * 1e-3),
+                       "updates_per_s": pairs / (seq_lat[-1] * 1e-3),
+                       "latency_ms_p50": float(np.percentile(seq_lat, 50)),
+                       "latency_ms_p99": float(np.percentile(seq_lat, 99)),
+                       "note": "hot_gsw per hologram in the given order, default tiling; CUDA events"},
+        "batch_vs_sequential_max_abs_diff": {"e": d_e, "u": d_u},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch(args)
     if args.precision_report:
         return run_precision_report(args)
     if args.workload == "diff256_1024":

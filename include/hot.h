@@ -138,6 +138,78 @@ int hot_field(hot_ctx *c, const float *phi, float *V);
  * GSW state is not touched.  HOT_ESTATE before hot_set_traps. */
 int hot_field_adjoint(hot_ctx *c, const float *phi, const float *G, float *grad);
 
+/* Efficiency e and uniformity u (Eq. 4) of the last forward evaluation (hot_gsw, hot_field or
+ * hot_batch_gsw).  Synchronises.  HOT_ESTATE if none has run since the traps or phases changed. */
+int hot_get_metrics(hot_ctx *c, double *eff_out, double *unif_out);
+
+/* ---- tiling and autotuning ----------------------------------------------------------------
+ * The step kernels give every thread one pixel column of a sub-tile of `rows` rows
+ * (1..14: pixels per thread), run `blocks_per_sm` resident blocks of 256 threads per SM
+ * (1..4; the grid is one wave of SMs x blocks_per_sm persistent blocks) and stage the trap
+ * tables in shared memory `chunk` traps at a time (1..128).  The results do not depend on the
+ * tiling beyond FP32 rounding of the per-pixel sums.  Defaults: 14, as many as fit, 128. */
+
+/* Sets the tiling (0 selects a parameter's default) and rebuilds the work schedule.
+ * Synchronises the context's stream.  HOT_EINVAL out of range. */
+int hot_set_tiling(hot_ctx *c, int rows, int blocks_per_sm, int chunk);
+
+/* The tiling in effect (blocks_per_sm as launched).  Any output pointer may be NULL. */
+int hot_get_tiling(const hot_ctx *c, int *rows, int *blocks_per_sm, int *chunk);
+
+/* Autotuner: times hot_gsw(iters) (CUDA events, best of 3 graph replays) for candidate tilings
+ * by coordinate search over rows, blocks_per_sm and chunk, keeps the fastest, and reports it
+ * with its time per iteration in microseconds (outputs may be NULL).  The phases and weights
+ * are restored afterwards; the fields are stale until the next forward evaluation (HOT_ESTATE
+ * from hot_get_fields).  Synchronises.  HOT_ESTATE before hot_set_traps; iters >= 1. */
+int hot_autotune(hot_ctx *c, int iters, int *rows, int *blocks_per_sm, int *chunk, double *us_per_iter);
+
+/* ---- batches of holograms ------------------------------------------------------------------
+ * A batch runs GSW on several contexts at once -- SLMs of different sizes and trap counts.
+ * The holograms are ordered by their work per iteration (N x M pixel-trap pairs, smallest
+ * first) and cut into groups of at least `group_pairs` pairs per iteration (and at most 24
+ * holograms: their parameters travel in the kernel launch); each group runs
+ * its iterations with one kernel launch per iteration that covers all of its holograms (their
+ * row segments are dealt out to one wave of blocks in equal shares of pairs), and the groups
+ * run one after another, so that small holograms neither leave the GPU idle nor wait for the
+ * large ones.  Each hologram keeps its own tables, phases, weights and accumulators (its
+ * context's buffers); the iteration is the same as hot_gsw's (Sec. 3). */
+typedef struct hot_batch hot_batch;
+
+/* Groups count >= 1 contexts (same device, traps set, same precision mode) into a batch
+ * queued on cuda_stream (NULL: the legacy stream).  The batch refers to the contexts'
+ * buffers: recreate it after hot_set_traps changes a trap count, and destroy it before
+ * destroying its contexts.  The contexts must not be used concurrently with the batch. */
+int hot_batch_create(hot_batch **out, int count, hot_ctx *const *ctxs, void *cuda_stream);
+
+/* Tiling of the batch's launches (as hot_set_tiling; 0 selects a default) and the minimum
+ * work of a group in pixel-trap pairs per iteration (0: 2^26; 1: every hologram its own
+ * group; a value above the total: one group, all holograms in lockstep).  Rebuilds the
+ * schedule; synchronises the batch's stream. */
+int hot_batch_set_tiling(hot_batch *b, int rows, int blocks_per_sm, int chunk, double group_pairs);
+
+/* The batch's tiling, group threshold and number of groups (outputs may be NULL). */
+int hot_batch_get_tiling(const hot_batch *b, int *rows, int *blocks_per_sm, int *chunk, double *group_pairs,
+                         int *groups);
+
+/* Autotuner of the batch's tiling, as hot_autotune (the group threshold is kept): times
+ * hot_batch_gsw(iters) and restores every hologram's phases and weights. */
+int hot_batch_autotune(hot_batch *b, int iters, int *rows, int *blocks_per_sm, int *chunk, double *us_per_iter);
+
+/* Runs iters GSW iterations on every hologram of the batch (groups in order, one launch per
+ * group and iteration; the whole sequence is one CUDA graph, captured on first use for each
+ * iters).  Afterwards each context holds its new phases and weights, and hot_get_fields /
+ * hot_get_metrics / hot_phase_out report its final forward field.  Queued; returns at once. */
+int hot_batch_gsw(hot_batch *b, int iters);
+
+/* Per-hologram latency of the last hot_batch_gsw: ms[h] = time from the start of its first
+ * launch to the completion of hologram h (device %globaltimer stamps, ns resolution of the
+ * timer as implemented by the GPU).  ms: HOST array of count doubles, in the order the
+ * contexts were given.  Synchronises.  HOT_ESTATE before the first hot_batch_gsw. */
+int hot_batch_latency(hot_batch *b, double *ms, int count);
+
+/* Frees the batch (NULL-safe); its contexts are not touched. */
+void hot_batch_destroy(hot_batch *b);
+
 /* Waits for all work queued by the context. */
 int hot_sync(hot_ctx *c);
 

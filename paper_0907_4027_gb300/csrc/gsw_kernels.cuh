@@ -47,6 +47,7 @@ struct SubTile {
 
 struct StepArgs {
   int W, H, M;
+  int chunk;              // traps staged in shared memory at once (1..kChunk)
   const SubTile *sub;     // work schedule: sub-tiles
   const int *first;       // [gridDim.x + 1]: block b processes sub-tiles first[b] .. first[b+1]-1
   const float *X;         // [M][W] column phase parts (turns if accurate, radians if fast)
@@ -320,21 +321,27 @@ struct FinalizeArgs {
   long long *Vsum;                // [2][M] out: the sums (V_m = Vsum / (N 2^fx_shift))
   float *metrics;                 // [2] out: e, u (Eq. 4)
   float inv_fx_n;
+  unsigned long long *done;       // NULL, or out: %globaltimer (ns) when the hologram completed
 };
 
 constexpr int kFinalizeThreads = 1024;
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // One block, once per hot_gsw call: efficiency e = sum |V_m|^2 and uniformity
 // u = 1 - (max I - min I)/(max I + min I) (Eq. 4) of the final forward field (fixed order),
 // the field sums for the caller, the weights back into their home buffer, and every
 // accumulator cleared.
-__global__ void __launch_bounds__(kFinalizeThreads) gsw_finalize_kernel(FinalizeArgs a) {
+__device__ __forceinline__ void finalize_block(const FinalizeArgs &a) {
   struct Part {
     ff si;
     float mx, mn;
   };
   __shared__ Part part[kFinalizeThreads / 32];
-  grid_dependency_wait();
   Part p = {{0.f, 0.f}, -1.f, 3.0e38f};
   for (int m = threadIdx.x; m < a.M; m += kFinalizeThreads) {
     const long long sr = (long long)__ldcg(a.acc + m), si = (long long)__ldcg(a.acc + a.M + m);
@@ -368,6 +375,23 @@ __global__ void __launch_bounds__(kFinalizeThreads) gsw_finalize_kernel(Finalize
   }
 }
 
+__global__ void __launch_bounds__(kFinalizeThreads) gsw_finalize_kernel(FinalizeArgs a) {
+  grid_dependency_wait();
+  finalize_block(a);
+}
+
+// Batched: block h finalizes hologram h and stamps its completion time.
+__global__ void __launch_bounds__(kFinalizeThreads) gsw_finalize_batch_kernel(const FinalizeArgs *args) {
+  grid_dependency_wait();
+  const FinalizeArgs &a = args[blockIdx.x];
+  finalize_block(a);
+  __syncthreads();
+  if (threadIdx.x == 0 && a.done) {
+    __threadfence();
+    *a.done = global_timer_ns();
+  }
+}
+
 // Calls BODY with the compile-time constant R equal to the runtime value rows (1..kRowsMax).
 #define HOT_WITH_ROWS(rows, BODY)              \
   switch (rows) {                              \
@@ -394,19 +418,107 @@ static_assert(kRowsMax % 2 == 0 && kRowsMax / 2 <= kWarps, "each warp finishes o
 // ADJ (with BACK, without FWD): the adjoint of Eq. 1 instead -- the same superposition with
 // coefficients G_m, S_j = sum_m G_m e^{i Delta_j^m}, written as the gradient
 // dL/dphi_j = (1/N) Im[e^{-i phi_j} S_j] of a real loss L(V) (a.phi is read, not written).
+// Shared-memory views of a step block.
+struct StepSmem {
+  float *Xs, *Ys;
+  float2 *Cs, *Sp;
+  float *Ps;
+  __device__ __forceinline__ explicit StepSmem(unsigned char *raw) {
+    Xs = reinterpret_cast<float *>(raw);
+    Ys = Xs + kXsFloats;
+    Cs = reinterpret_cast<float2 *>(Ys + kYsFloats);
+    Sp = Cs + kChunk;                                                  // [kWarps][kHalfRows][kTileW]
+    Ps = reinterpret_cast<float *>(Sp + kWarps * kHalfRows * kTileW);  // [kRowsMax][kTileW] phases
+  }
+};
+
+// One sub-tile of the hologram a: back-projection (with the coefficients implied by `mean`,
+// or explicit ones) and/or forward field.  prestaged: the first chunk's X/Y tables are
+// already in shared memory (staged in the prologue) -- cleared after use.
+template <bool FAST, bool BACK, bool FWD, bool ADJ>
+__device__ __forceinline__ void process_subtile(const StepArgs &a, const SubTile st, float mean, bool &prestaged,
+                                                const StepSmem &sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mc = a.M < a.chunk ? a.M : a.chunk;
+  const int nchunks = (a.M + mc - 1) / mc;
+  const int ix = st.x0 + lane;
+  const bool col_ok = ix < a.W;
+
+  if (BACK) {
+    float2 S[kRowsMax];
+#pragma unroll
+    for (int r = 0; r < kRowsMax; r++) S[r] = make_float2(0.f, 0.f);
+    for (int ch = 0; ch < nchunks; ch++) {
+      const int m0 = ch * mc, n = min(mc, a.M - m0);
+      __syncthreads();  // earlier readers of the tables are done
+      stage_tables<true, ADJ>(a, m0, n, st, sm.Xs, sm.Ys, sm.Cs, !prestaged, mean);
+      prestaged = false;
+      __syncthreads();
+      const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
+      HOT_WITH_ROWS(st.rows, (back_traps<FAST, R>(sm.Xs, sm.Ys, sm.Cs, lo, hi, lane, S)));
+    }
+    // Sum the 8 warps' superpositions, half of the rows at a time, in warp order.
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      if (h * kHalfRows >= st.rows) break;
+      __syncthreads();  // Sp and the phase rows are free
+#pragma unroll
+      for (int i = 0; i < kHalfRows; i++)
+        if (h * kHalfRows + i < st.rows) sm.Sp[(warp * kHalfRows + i) * kTileW + lane] = S[h * kHalfRows + i];
+      __syncthreads();
+      if (warp < kHalfRows && h * kHalfRows + warp < st.rows) {
+        const int r = h * kHalfRows + warp;
+        float2 s = sm.Sp[warp * kTileW + lane];
+#pragma unroll
+        for (int w = 1; w < kWarps; w++) {
+          const float2 q = sm.Sp[(w * kHalfRows + warp) * kTileW + lane];
+          s.x += q.x;
+          s.y += q.y;
+        }
+        const size_t j = (size_t)(st.y0 + r) * a.W + ix;
+        if (ADJ) {
+          if (col_ok) {
+            float sp, cp;
+            sincosf(a.phi[j], &sp, &cp);
+            a.grad[j] = (cp * s.y - sp * s.x) * a.inv_n;  // Im[(cos - i sin)(S.x + i S.y)] / N
+          }
+        } else {
+          const float ph = atan2f(s.y, s.x);
+          if (col_ok) a.phi[j] = ph;
+          if (FWD) sm.Ps[r * kTileW + lane] = phase_units<FAST>(ph);
+        }
+      }
+    }
+  } else if (FWD) {
+    __syncthreads();  // earlier readers of the phases and of the tables are done
+    for (int r = warp; r < st.rows; r += kWarps)
+      sm.Ps[r * kTileW + lane] = col_ok ? phase_units<FAST>(a.phi[(size_t)(st.y0 + r) * a.W + ix]) : 0.0f;
+  }
+
+  if (FWD) {
+    __syncthreads();  // the phases are complete
+    float ph[kRowsMax];
+#pragma unroll
+    for (int r = 0; r < kRowsMax; r++) ph[r] = r < st.rows ? sm.Ps[r * kTileW + lane] : 0.0f;
+    for (int ch = 0; ch < nchunks; ch++) {
+      const int m0 = ch * mc, n = min(mc, a.M - m0);
+      if (!BACK || nchunks > 1) {  // with one chunk the back-projection's tables are still staged
+        if (ch) __syncthreads();
+        stage_tables<false>(a, m0, n, st, sm.Xs, sm.Ys, sm.Cs);
+        __syncthreads();
+      }
+      const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
+      HOT_WITH_ROWS(st.rows, (forward_traps<FAST, R>(sm.Xs, sm.Ys, lo, hi, lane, ph, col_ok ? 1.f : 0.f, a, m0)));
+    }
+  }
+}
+
 template <bool FAST, bool BACK, bool FWD, bool ADJ = false>
 __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
   static_assert(!ADJ || (BACK && !FWD), "the adjoint is a back-projection without forward field");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float *Xs = reinterpret_cast<float *>(smem_raw);
-  float *Ys = Xs + kXsFloats;
-  float2 *Cs = reinterpret_cast<float2 *>(Ys + kYsFloats);
-  float2 *Sp = Cs + kChunk;                                           // [kWarps][kHalfRows][kTileW]
-  float *Ps = reinterpret_cast<float *>(Sp + kWarps * kHalfRows * kTileW);  // [kRowsMax][kTileW] phases
-
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int mc = a.M < kChunk ? a.M : kChunk;
-  const int nchunks = (a.M + mc - 1) / mc;
+  const StepSmem sm(smem_raw);
+  const int mc = a.M < a.chunk ? a.M : a.chunk;
   const int t_begin = a.first[blockIdx.x], t_end = a.first[blockIdx.x + 1];
 
   // Prologue, overlapping the previous kernel: the trap tables are constant during hot_gsw,
@@ -415,7 +527,7 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
   bool prestaged = false;
   if (BACK && t_begin < t_end) {
     const SubTile st0 = a.sub[t_begin];
-    stage_tables<false>(a, 0, mc, st0, Xs, Ys, Cs);
+    stage_tables<false>(a, 0, mc, st0, sm.Xs, sm.Ys, sm.Cs);
     prestaged = true;
   }
   grid_dependency_wait();
@@ -427,81 +539,63 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
     for (int m = blockIdx.x + gridDim.x * threadIdx.x; m < a.M; m += gridDim.x * kThreads)
       a.w_out[m] = coefficient(a, m, mean).x;
   }
+  for (int t = t_begin; t < t_end; t++) process_subtile<FAST, BACK, FWD, ADJ>(a, a.sub[t], mean, prestaged, sm);
+}
 
+// Batched launch: the sub-tiles of up to kBatchMax holograms (SubTile::pad = hologram index)
+// in one grid.  The holograms' parameters travel in the launch itself (a __grid_constant__
+// argument read through the constant cache, as the single-hologram kernel reads its own).
+// Every block that meets a hologram computes its <|V|> and coefficients itself; the weights
+// of hologram h are written by block owner[h].
+constexpr int kBatchMax = 24;  // keeps the launch argument under 4 KB
+
+struct BatchArgs {
+  StepArgs holo[kBatchMax];
+  int owner[kBatchMax];
+  const SubTile *sub;
+  const int *first;  // [gridDim.x + 1]
+  int count;
+};
+static_assert(sizeof(BatchArgs) <= 4096, "launch argument above 4 KB");
+
+template <bool FAST, bool BACK, bool FWD>
+__global__ void __launch_bounds__(kThreads, 4) gsw_batch_kernel(const __grid_constant__ BatchArgs b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const StepSmem sm(smem_raw);
+  const int t_begin = b.first[blockIdx.x], t_end = b.first[blockIdx.x + 1];
+
+  allow_dependents();
+  bool prestaged = false;
+  if (BACK && t_begin < t_end) {
+    const SubTile st0 = b.sub[t_begin];
+    const StepArgs &a0 = b.holo[st0.pad];
+    stage_tables<false>(a0, 0, a0.M < a0.chunk ? a0.M : a0.chunk, st0, sm.Xs, sm.Ys, sm.Cs);
+    prestaged = true;
+  }
+  grid_dependency_wait();
+  if (FWD)  // clear the buffers the next launch accumulates into, for every hologram
+    for (int h = 0; h < b.count; h++) {
+      unsigned long long *clr = b.holo[h].acc_clear;
+      const int n2 = 2 * b.holo[h].M;
+      for (int i = blockIdx.x * kThreads + threadIdx.x; i < n2; i += gridDim.x * kThreads) clr[i] = 0ull;
+    }
+  int cur = -1;
+  float mean = 0.f;
   for (int t = t_begin; t < t_end; t++) {
-    const SubTile st = a.sub[t];
-    const int ix = st.x0 + lane;
-    const bool col_ok = ix < a.W;
-
-    if (BACK) {
-      float2 S[kRowsMax];
-#pragma unroll
-      for (int r = 0; r < kRowsMax; r++) S[r] = make_float2(0.f, 0.f);
-      for (int ch = 0; ch < nchunks; ch++) {
-        const int m0 = ch * mc, n = min(mc, a.M - m0);
-        __syncthreads();  // earlier readers of the tables are done
-        stage_tables<true, ADJ>(a, m0, n, st, Xs, Ys, Cs, !prestaged, mean);
-        prestaged = false;
-        __syncthreads();
-        const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
-        HOT_WITH_ROWS(st.rows, (back_traps<FAST, R>(Xs, Ys, Cs, lo, hi, lane, S)));
-      }
-      // Sum the 8 warps' superpositions, half of the rows at a time, in warp order.
-#pragma unroll
-      for (int h = 0; h < 2; h++) {
-        if (h * kHalfRows >= st.rows) break;
-        __syncthreads();  // Sp and the phase rows are free
-#pragma unroll
-        for (int i = 0; i < kHalfRows; i++)
-          if (h * kHalfRows + i < st.rows) Sp[(warp * kHalfRows + i) * kTileW + lane] = S[h * kHalfRows + i];
-        __syncthreads();
-        if (warp < kHalfRows && h * kHalfRows + warp < st.rows) {
-          const int r = h * kHalfRows + warp;
-          float2 s = Sp[warp * kTileW + lane];
-#pragma unroll
-          for (int w = 1; w < kWarps; w++) {
-            const float2 q = Sp[(w * kHalfRows + warp) * kTileW + lane];
-            s.x += q.x;
-            s.y += q.y;
-          }
-          const size_t j = (size_t)(st.y0 + r) * a.W + ix;
-          if (ADJ) {
-            if (col_ok) {
-              float sp, cp;
-              sincosf(a.phi[j], &sp, &cp);
-              a.grad[j] = (cp * s.y - sp * s.x) * a.inv_n;  // Im[(cos - i sin)(S.x + i S.y)] / N
-            }
-          } else {
-            const float ph = atan2f(s.y, s.x);
-            if (col_ok) a.phi[j] = ph;
-            if (FWD) Ps[r * kTileW + lane] = phase_units<FAST>(ph);
-          }
-        }
-      }
-    } else if (FWD) {
-      __syncthreads();  // earlier readers of the phases and of the tables are done
-      for (int r = warp; r < st.rows; r += kWarps)
-        Ps[r * kTileW + lane] = col_ok ? phase_units<FAST>(a.phi[(size_t)(st.y0 + r) * a.W + ix]) : 0.0f;
+    const SubTile st = b.sub[t];
+    const StepArgs &a = b.holo[st.pad];
+    if (BACK && st.pad != cur) {
+      mean = mean_field_amplitude(a);
+      if (b.owner[st.pad] == (int)blockIdx.x)
+        for (int m = threadIdx.x; m < a.M; m += kThreads) a.w_out[m] = coefficient(a, m, mean).x;
     }
-
-    if (FWD) {
-      __syncthreads();  // the phases are complete
-      float ph[kRowsMax];
-#pragma unroll
-      for (int r = 0; r < kRowsMax; r++) ph[r] = r < st.rows ? Ps[r * kTileW + lane] : 0.0f;
-      for (int ch = 0; ch < nchunks; ch++) {
-        const int m0 = ch * mc, n = min(mc, a.M - m0);
-        if (!BACK || nchunks > 1) {  // with one chunk the back-projection's tables are still staged
-          if (ch) __syncthreads();
-          stage_tables<false>(a, m0, n, st, Xs, Ys, Cs);
-          __syncthreads();
-        }
-        const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
-        HOT_WITH_ROWS(st.rows, (forward_traps<FAST, R>(Xs, Ys, lo, hi, lane, ph, col_ok ? 1.f : 0.f, a, m0)));
-      }
-    }
+    cur = st.pad;
+    process_subtile<FAST, BACK, FWD, false>(a, st, mean, prestaged, sm);
   }
 }
+
+// Start stamp of a batched sequence (%globaltimer, ns).
+__global__ void stamp_kernel(unsigned long long *t) { *t = global_timer_ns(); }
 
 // Per (trap, column) and (trap, row) phase parts of Eq. 2 reduced modulo one turn in FP64.
 // abc: [M][3] = a_m, b_m, c_m in turns (see the file header).  Writes turns and radians.

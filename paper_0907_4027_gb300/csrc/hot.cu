@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <iterator>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -64,6 +65,10 @@ struct hot_ctx {
   hot::SubTile *sub = nullptr;  // [n_sub]
   int *first = nullptr;         // [grid + 1]
   int sched_smem_M = -1;        // M the schedule's occupancy was computed for
+  // tiling (hot_set_tiling): rows per sub-tile (pixels per thread), resident blocks per SM
+  // (0: as many as fit), traps per staged chunk
+  int tile_rows = hot::kRowsMax, tile_bps = 0, tile_chunk = hot::kChunk;
+  int sched_bps = 0, sched_bps_max = 0;  // resident blocks per SM in the schedule; occupancy limit
   // state
   float *phi = nullptr;  // [N]
   int M = 0;
@@ -189,6 +194,7 @@ int launch_tile(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const f
   a.W = c->W;
   a.H = c->H;
   a.M = c->M;
+  a.chunk = c->tile_chunk;
   a.sub = c->sub;
   a.first = c->first;
   a.X = FAST ? c->Xr : c->Xt;
@@ -227,8 +233,9 @@ int set_step_smem(int M) {
   return HOT_OK;
 }
 
-// One wave of persistent blocks (SMs x resident blocks of the fused kernel); the W/32 x H row
-// segments are dealt out in equal contiguous runs, cut into sub-tiles of <= kRowsMax rows.
+// One wave of persistent blocks (SMs x resident blocks per SM: as many as fit, at most
+// tile_bps); the W/32 x H row segments are dealt out in equal contiguous runs, cut into
+// sub-tiles of <= tile_rows rows.
 int build_schedule(hot_ctx *c) {
   int rc = set_step_smem(c->M);
   if (rc != HOT_OK) return rc;
@@ -237,6 +244,9 @@ int build_schedule(hot_ctx *c) {
   HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_step_kernel<true, true, true>,
                                                          hot::kThreads, hot::step_smem_bytes(c->M, true)));
   if (per_sm < 1) per_sm = 1;
+  c->sched_bps_max = per_sm;
+  if (c->tile_bps > 0 && c->tile_bps < per_sm) per_sm = c->tile_bps;
+  c->sched_bps = per_sm;
   const int strips = (c->W + hot::kTileW - 1) / hot::kTileW;
   const long long U = (long long)strips * c->H;
   const int G = (int)std::min<long long>((long long)sms * per_sm, U);
@@ -250,7 +260,7 @@ int build_schedule(hot_ctx *c) {
       const int strip = (int)(s / c->H), row = (int)(s % c->H);
       const long long run_end = std::min<long long>(s1, (long long)(strip + 1) * c->H);
       const int L = (int)(run_end - s);
-      const int nsub = (L + hot::kRowsMax - 1) / hot::kRowsMax;
+      const int nsub = (L + c->tile_rows - 1) / c->tile_rows;
       for (int i = 0; i < nsub; i++) {
         const int r0 = row + (int)((long long)L * i / nsub), r1 = row + (int)((long long)L * (i + 1) / nsub);
         sub.push_back({strip * hot::kTileW, r0, r1 - r0, 0});
@@ -629,6 +639,17 @@ int hot_field_adjoint(hot_ctx *c, const float *phi, const float *G, float *grad)
                                        : launch_tile<false, true, false, true>(c, false, 0, phi, g, grad);
 }
 
+int hot_get_metrics(hot_ctx *c, double *eff_out, double *unif_out) {
+  if (!c) return fail(HOT_EINVAL, "hot_get_metrics: NULL context");
+  if (!c->M || !c->have_fields) return fail(HOT_ESTATE, "hot_get_metrics: no forward evaluation since the last change");
+  float m[2];
+  HOT_CUDA(cudaMemcpyAsync(m, c->metrics, sizeof m, cudaMemcpyDeviceToHost, c->st));
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  if (eff_out) *eff_out = m[0];
+  if (unif_out) *unif_out = m[1];
+  return HOT_OK;
+}
+
 int hot_sync(hot_ctx *c) {
   if (!c) return fail(HOT_EINVAL, "hot_sync: NULL context");
   HOT_CUDA(cudaStreamSynchronize(c->st));
@@ -674,6 +695,576 @@ int hot_profile_read(hot_ctx *c, double *ms, long long *launches) {
     if (launches) launches[k] = n[k];
   }
   return HOT_OK;
+}
+
+}  // extern "C"
+
+
+// ---------------------------------------------------------------------------------------------
+// Batches of holograms (hot_batch_*).
+struct hot_batch {
+  int count = 0, precision = HOT_PREC_ACCURATE, dev = 0;
+  std::vector<hot_ctx *> ctx;
+  cudaStream_t st = nullptr, cap = nullptr;
+  int sms = 0, per_sm_max = 1;
+  // tiling (hot_batch_set_tiling) and group threshold in pixel-trap pairs per iteration
+  int rows = hot::kRowsMax, bps = 0, chunk = hot::kChunk;
+  double group_pairs = 67108864.0;
+  struct Group {
+    std::vector<int> members;         // context indices (<= kBatchMax); SubTile::pad indexes this list
+    int grid = 0, n_sub = 0;
+    hot::SubTile *sub = nullptr;
+    int *first = nullptr;
+    std::vector<int> owner;                  // block that writes each hologram's weights
+    std::vector<hot::StepArgs> holo[6];      // parameters for launch k (k % 6; k = 0 uses set 0)
+    hot::FinalizeArgs *fin[6] = {};          // finalize descriptors for iters % 6
+  };
+  std::vector<Group> groups;
+  unsigned long long *stamps = nullptr;  // [count + 1]: completion of hologram h; [count]: start
+  bool ran = false;
+  struct Graph {
+    int iters;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+};
+
+namespace {
+
+template <bool FAST>
+int batch_set_smem() {
+  const int bytes = hot::step_smem_bytes(0, true);
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_batch_kernel<FAST, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_batch_kernel<FAST, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  return HOT_OK;
+}
+
+void batch_drop_graphs(hot_batch *b) {
+  for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+  b->graphs.clear();
+}
+
+void group_free(hot_batch::Group &g) {
+  dfree(g.sub);
+  dfree(g.first);
+  for (auto &p : g.fin) dfree(p);
+}
+
+void batch_free(hot_batch *b) {
+  batch_drop_graphs(b);
+  for (auto &g : b->groups) group_free(g);
+  b->groups.clear();
+  dfree(b->stamps);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  b->cap = nullptr;
+}
+
+// Step-kernel parameters of context c for launch k of a sequence (buffers rotate as in hot_gsw).
+hot::StepArgs step_args(const hot_ctx *c, int k, int chunk) {
+  hot::StepArgs a = {};
+  const bool fast = c->precision == HOT_PREC_FAST;
+  const size_t M2 = 2 * (size_t)c->M;
+  a.W = c->W;
+  a.H = c->H;
+  a.M = c->M;
+  a.chunk = chunk;
+  a.X = fast ? c->Xr : c->Xt;
+  a.Y = fast ? c->Yr : c->Yt;
+  a.phi = c->phi;
+  a.acc_in = c->acc + M2 * ((k + 2) % 3);
+  a.acc_out = c->acc + M2 * (k % 3);
+  a.acc_clear = c->acc + M2 * ((k + 1) % 3);
+  a.w_in = c->w + (size_t)c->M * ((k + 1) & 1);
+  a.w_out = c->w + (size_t)c->M * (k & 1);
+  a.fx_scale = ldexpf(1.0f, c->fx_shift);
+  a.inv_fx_n = (float)(1.0 / ((double)c->W * (double)c->H * ldexp(1.0, c->fx_shift)));
+  a.angle_units = fast ? 1.0f : 0.15915494309189535f;
+  a.inv_n = (float)(1.0 / ((double)c->W * (double)c->H));
+  return a;
+}
+
+double pairs_of(const hot_ctx *c) { return (double)c->W * (double)c->H * (double)c->M; }
+
+// One group's work schedule: the row segments of its holograms in order, each weighted by its
+// trap count, dealt out to one wave of G blocks in equal shares (a segment goes to the block
+// that holds the midpoint of its weight interval); each block's run of rows in a strip is cut
+// into equal sub-tiles of <= rows rows.
+int build_group(hot_batch *b, hot_batch::Group &g) {
+  const int count = (int)g.members.size();
+  const int per_sm = b->bps > 0 ? std::min(b->bps, b->per_sm_max) : b->per_sm_max;
+  long double T = 0;
+  long long segments = 0;
+  for (int h : g.members) {
+    const hot_ctx *c = b->ctx[h];
+    const long long seg = (long long)((c->W + hot::kTileW - 1) / hot::kTileW) * c->H;
+    segments += seg;
+    T += (long double)seg * c->M;
+  }
+  const int G = (int)std::min<long long>((long long)b->sms * per_sm, segments);
+  std::vector<hot::SubTile> sub;
+  std::vector<int> first(G + 1, 0), owner(count, -1);
+  long double w0 = 0;
+  int cur_b = 0;
+  for (int i = 0; i < count; i++) {
+    const hot_ctx *c = b->ctx[g.members[i]];
+    const int strips = (c->W + hot::kTileW - 1) / hot::kTileW;
+    for (int s = 0; s < strips; s++) {
+      auto block_of = [&](int row) {
+        const long double mid = w0 + ((long double)row + 0.5L) * c->M;
+        const int bb = (int)(mid * G / T);
+        return bb < 0 ? 0 : (bb >= G ? G - 1 : bb);
+      };
+      int r = 0;
+      while (r < c->H) {  // the run of rows of this strip that goes to block bb, cut evenly
+        const int bb = block_of(r);
+        int r1 = r + 1;
+        while (r1 < c->H && block_of(r1) == bb) r1++;
+        while (cur_b < bb) first[++cur_b] = (int)sub.size();
+        if (owner[i] < 0) owner[i] = bb;
+        const int L = r1 - r, nsub = (L + b->rows - 1) / b->rows;
+        for (int q = 0; q < nsub; q++) {
+          const int q0 = r + (int)((long long)L * q / nsub), q1 = r + (int)((long long)L * (q + 1) / nsub);
+          sub.push_back({s * hot::kTileW, q0, q1 - q0, i});
+        }
+        r = r1;
+      }
+      w0 += (long double)c->H * c->M;
+    }
+  }
+  while (cur_b < G) first[++cur_b] = (int)sub.size();
+  g.grid = G;
+  g.n_sub = (int)sub.size();
+  g.owner = owner;
+  for (int k = 0; k < 6; k++) {
+    g.holo[k].resize(count);
+    for (int i = 0; i < count; i++) g.holo[k][i] = step_args(b->ctx[g.members[i]], k == 0 ? 6 : k, b->chunk);
+  }
+  int rc = dalloc(&g.sub, sub.size());
+  if (rc == HOT_OK) rc = dalloc(&g.first, first.size());
+  for (int r6 = 0; rc == HOT_OK && r6 < 6; r6++) {  // finalize after `iters` iterations, iters % 6 == r6
+    rc = dalloc(&g.fin[r6], (size_t)count);
+    std::vector<hot::FinalizeArgs> fs(count);
+    for (int i = 0; i < count; i++) {
+      const hot_ctx *c = b->ctx[g.members[i]];
+      hot::FinalizeArgs &f = fs[i];
+      f.M = c->M;
+      f.acc = c->acc + 2 * (size_t)c->M * (r6 % 3);  // the last launch accumulated into acc[iters % 3]
+      f.acc_all = c->acc;
+      f.w_src = c->w + (size_t)c->M * (r6 & 1);       // and left the weights in w[iters & 1]
+      f.w_dst = c->w;
+      f.Vsum = c->Vsum;
+      f.metrics = c->metrics;
+      f.inv_fx_n = (float)(1.0 / ((double)c->W * (double)c->H * ldexp(1.0, c->fx_shift)));
+      f.done = b->stamps + g.members[i];
+    }
+    if (rc == HOT_OK && cudaMemcpy(g.fin[r6], fs.data(), sizeof(hot::FinalizeArgs) * count, cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = fail(HOT_ECUDA, "batch schedule: copy of descriptors failed");
+  }
+  if (rc == HOT_OK) {
+    cudaError_t e = cudaMemcpy(g.sub, sub.data(), sizeof(hot::SubTile) * sub.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g.first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = fail(HOT_ECUDA, "batch schedule: %s", cudaGetErrorString(e));
+  }
+  return rc;
+}
+
+// Orders the holograms by pairs per iteration (smallest first, stable), cuts them into
+// groups of >= group_pairs (a short last group joins the one before) and builds each group.
+int batch_schedule(hot_batch *b) {
+  HOT_CUDA(cudaStreamSynchronize(b->st));
+  batch_drop_graphs(b);
+  for (auto &g : b->groups) group_free(g);
+  b->groups.clear();
+  b->ran = false;
+  std::vector<int> order(b->count);
+  for (int h = 0; h < b->count; h++) order[h] = h;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return pairs_of(b->ctx[x]) < pairs_of(b->ctx[y]); });
+  std::vector<std::vector<int>> parts;
+  double sum = 0;
+  for (int h : order) {
+    if (parts.empty() || sum >= b->group_pairs || (int)parts.back().size() == hot::kBatchMax) {
+      parts.emplace_back();
+      sum = 0;
+    }
+    parts.back().push_back(h);
+    sum += pairs_of(b->ctx[h]);
+  }
+  if (parts.size() > 1 && sum < b->group_pairs && parts.back().size() + parts[parts.size() - 2].size() <= hot::kBatchMax) {
+    auto last = parts.back();
+    parts.pop_back();
+    parts.back().insert(parts.back().end(), last.begin(), last.end());
+  }
+  b->groups.resize(parts.size());
+  for (size_t i = 0; i < parts.size(); i++) {
+    b->groups[i].members = parts[i];
+    const int rc = build_group(b, b->groups[i]);
+    if (rc != HOT_OK) {
+      for (auto &g : b->groups) group_free(g);
+      b->groups.clear();
+      return rc;
+    }
+  }
+  return HOT_OK;
+}
+
+template <bool FAST, bool BACK>
+int batch_launch(hot_batch *b, const hot_batch::Group &g, int k, bool pdl) {
+  hot::BatchArgs a = {};
+  const int count = (int)g.members.size();
+  for (int i = 0; i < count; i++) {
+    a.holo[i] = g.holo[k % 6][i];
+    a.owner[i] = g.owner[i];
+  }
+  a.sub = g.sub;
+  a.first = g.first;
+  a.count = count;
+  hot_ctx tmp;  // launch() needs a context only for the stream
+  tmp.st = b->st;
+  launch(&tmp, hot::gsw_batch_kernel<FAST, BACK, true>, g.grid, hot::kThreads, hot::step_smem_bytes(0, true), pdl, a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(HOT_ECUDA, "launch of gsw_batch_kernel: %s", cudaGetErrorString(e));
+  return HOT_OK;
+}
+
+// A start stamp, then the groups in order: forward field of the starting phases (k = 0),
+// iterations 1..iters, and the per-hologram finalize with its completion stamp.
+int batch_enqueue(hot_batch *b, int iters) {
+  const bool fast = b->precision == HOT_PREC_FAST;
+  hot::stamp_kernel<<<1, 1, 0, b->st>>>(b->stamps + b->count);
+  cudaError_t e0 = cudaGetLastError();
+  if (e0 != cudaSuccess) return fail(HOT_ECUDA, "launch of stamp_kernel: %s", cudaGetErrorString(e0));
+  for (size_t gi = 0; gi < b->groups.size(); gi++) {
+    const hot_batch::Group &g = b->groups[gi];
+    int rc = fast ? batch_launch<true, false>(b, g, 0, true) : batch_launch<false, false>(b, g, 0, true);
+    for (int k = 1; k <= iters && rc == HOT_OK; k++)
+      rc = fast ? batch_launch<true, true>(b, g, k, true) : batch_launch<false, true>(b, g, k, true);
+    if (rc != HOT_OK) return rc;
+    hot_ctx tmp;
+    tmp.st = b->st;
+    launch(&tmp, hot::gsw_finalize_batch_kernel, (int)g.members.size(), hot::kFinalizeThreads, 0, true,
+           (const hot::FinalizeArgs *)g.fin[iters % 6]);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(HOT_ECUDA, "launch of gsw_finalize_batch_kernel: %s", cudaGetErrorString(e));
+  }
+  return HOT_OK;
+}
+
+int check_tiling(const char *who, int rows, int bps, int chunk) {
+  if (rows < 0 || rows > hot::kRowsMax) return fail(HOT_EINVAL, "%s: rows = %d not in [1, %d] (0: default)", who, rows, hot::kRowsMax);
+  if (bps < 0 || bps > 32) return fail(HOT_EINVAL, "%s: blocks_per_sm = %d not in [1, 32] (0: default)", who, bps);
+  if (chunk < 0 || chunk > hot::kChunk) return fail(HOT_EINVAL, "%s: chunk = %d not in [1, %d] (0: default)", who, chunk, hot::kChunk);
+  return HOT_OK;
+}
+
+struct Tiling {
+  int rows, bps, chunk;
+  bool operator==(const Tiling &o) const { return rows == o.rows && bps == o.bps && chunk == o.chunk; }
+};
+
+// Coordinate search: each parameter in turn takes the fastest of its candidates with the
+// others fixed; a candidate replaces the incumbent only if it is more than 1 % faster; at
+// most two passes.  apply(t) installs a tiling, time(&us) measures it.  Leaves `best` applied.
+template <typename Apply, typename Time>
+int tune_tiling(int max_bps, Tiling &best, double &best_us, Apply apply, Time time) {
+  static const int rows_c[] = {14, 12, 10, 8, 6, 4, 2};
+  static const int chunk_c[] = {128, 96, 64, 32};
+  int rc = apply(best);
+  if (rc == HOT_OK) rc = time(&best_us);
+  for (int pass = 0; rc == HOT_OK && pass < 2; pass++) {
+    bool changed = false;
+    for (int dim = 0; rc == HOT_OK && dim < 3; dim++) {
+      std::vector<int> cand;
+      if (dim == 0) cand.assign(std::begin(rows_c), std::end(rows_c));
+      if (dim == 1)
+        for (int v = max_bps; v >= 1; v--) cand.push_back(v);
+      if (dim == 2) cand.assign(std::begin(chunk_c), std::end(chunk_c));
+      for (int v : cand) {
+        Tiling t = best;
+        (dim == 0 ? t.rows : dim == 1 ? t.bps : t.chunk) = v;
+        if (t == best) continue;
+        double us = 0;
+        rc = apply(t);
+        if (rc == HOT_OK) rc = time(&us);
+        if (rc != HOT_OK) break;
+        if (us < 0.99 * best_us) {
+          best = t;
+          best_us = us;
+          changed = true;
+        }
+      }
+    }
+    if (!changed) break;
+  }
+  const int rc2 = apply(best);
+  return rc != HOT_OK ? rc : rc2;
+}
+
+// Device copies of phases and weights that an autotuner restores before every timed run.
+struct Saved {
+  float *phi = nullptr, *w = nullptr;
+  ~Saved() {
+    dfree(phi);
+    dfree(w);
+  }
+};
+
+int save_state(hot_ctx *c, Saved &s, cudaStream_t st) {
+  const size_t N = (size_t)c->W * c->H;
+  int rc = dalloc(&s.phi, N);
+  if (rc == HOT_OK) rc = dalloc(&s.w, (size_t)c->M);
+  if (rc != HOT_OK) return rc;
+  HOT_CUDA(cudaMemcpyAsync(s.phi, c->phi, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  HOT_CUDA(cudaMemcpyAsync(s.w, c->w, c->M * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  return HOT_OK;
+}
+
+int restore_state(hot_ctx *c, const Saved &s, cudaStream_t st) {
+  HOT_CUDA(cudaMemcpyAsync(c->phi, s.phi, (size_t)c->W * c->H * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  HOT_CUDA(cudaMemcpyAsync(c->w, s.w, c->M * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  return HOT_OK;
+}
+
+// Best of three timed runs after one untimed run (graph capture, warm-up), in microseconds
+// per iteration; restore() is queued before each run, outside the timed events.
+template <typename Restore, typename Run>
+int time_runs(cudaStream_t st, int iters, double *us, Restore restore, Run run) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  HOT_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(HOT_ECUDA, "autotune: cudaEventCreate failed");
+  }
+  double best = 1e300;
+  int rc = HOT_OK;
+  for (int r = 0; rc == HOT_OK && r < 4; r++) {
+    rc = restore();
+    if (rc == HOT_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = fail(HOT_ECUDA, "autotune: event record failed");
+    if (rc == HOT_OK) rc = run();
+    if (rc == HOT_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = fail(HOT_ECUDA, "autotune: event record failed");
+    float ms = 0.f;
+    if (rc == HOT_OK) {
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) rc = fail(HOT_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    }
+    if (rc == HOT_OK && r > 0) best = std::min(best, (double)ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == HOT_OK) *us = best * 1000.0 / iters;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hot_set_tiling(hot_ctx *c, int rows, int blocks_per_sm, int chunk) {
+  if (!c) return fail(HOT_EINVAL, "hot_set_tiling: NULL context");
+  int rc = check_tiling("hot_set_tiling", rows, blocks_per_sm, chunk);
+  if (rc != HOT_OK) return rc;
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  c->tile_rows = rows ? rows : hot::kRowsMax;
+  c->tile_bps = blocks_per_sm;
+  c->tile_chunk = chunk ? chunk : hot::kChunk;
+  drop_graphs(c);
+  return c->M ? build_schedule(c) : HOT_OK;
+}
+
+int hot_get_tiling(const hot_ctx *c, int *rows, int *blocks_per_sm, int *chunk) {
+  if (!c) return fail(HOT_EINVAL, "hot_get_tiling: NULL context");
+  if (rows) *rows = c->tile_rows;
+  if (blocks_per_sm) *blocks_per_sm = c->sched_bps;
+  if (chunk) *chunk = c->tile_chunk;
+  return HOT_OK;
+}
+
+int hot_autotune(hot_ctx *c, int iters, int *rows, int *blocks_per_sm, int *chunk, double *us_per_iter) {
+  if (!c) return fail(HOT_EINVAL, "hot_autotune: NULL context");
+  if (!c->M) return fail(HOT_ESTATE, "hot_autotune: no traps set");
+  if (iters < 1) return fail(HOT_EINVAL, "hot_autotune: iters = %d < 1", iters);
+  Saved saved;
+  int rc = save_state(c, saved, c->st);
+  if (rc != HOT_OK) return rc;
+  const bool profiling = c->profiling;
+  c->profiling = false;
+  Tiling best = {c->tile_rows, c->sched_bps, c->tile_chunk};
+  double best_us = 0;
+  rc = tune_tiling(
+      c->sched_bps_max, best, best_us,
+      [&](const Tiling &t) { return hot_set_tiling(c, t.rows, t.bps, t.chunk); },
+      [&](double *us) {
+        return time_runs(c->st, iters, us, [&]() { return restore_state(c, saved, c->st); },
+                         [&]() { return hot_gsw(c, iters, nullptr, nullptr); });
+      });
+  c->profiling = profiling;
+  const int rc2 = restore_state(c, saved, c->st);
+  cudaStreamSynchronize(c->st);
+  c->have_fields = false;
+  if (rc != HOT_OK) return rc;
+  if (rc2 != HOT_OK) return rc2;
+  if (rows) *rows = best.rows;
+  if (blocks_per_sm) *blocks_per_sm = best.bps;
+  if (chunk) *chunk = best.chunk;
+  if (us_per_iter) *us_per_iter = best_us;
+  return HOT_OK;
+}
+
+int hot_batch_create(hot_batch **out, int count, hot_ctx *const *ctxs, void *cuda_stream) {
+  if (!out) return fail(HOT_EINVAL, "hot_batch_create: out is NULL");
+  *out = nullptr;
+  if (count < 1 || !ctxs) return fail(HOT_EINVAL, "hot_batch_create: no contexts");
+  for (int i = 0; i < count; i++) {
+    if (!ctxs[i]) return fail(HOT_EINVAL, "hot_batch_create: context %d is NULL", i);
+    if (!ctxs[i]->M) return fail(HOT_ESTATE, "hot_batch_create: context %d has no traps", i);
+    if (ctxs[i]->precision != ctxs[0]->precision)
+      return fail(HOT_EINVAL, "hot_batch_create: contexts differ in precision mode");
+    if (ctxs[i]->dev != ctxs[0]->dev) return fail(HOT_EINVAL, "hot_batch_create: contexts on different devices");
+    for (int j = 0; j < i; j++)
+      if (ctxs[j] == ctxs[i]) return fail(HOT_EINVAL, "hot_batch_create: context %d given twice", i);
+  }
+  hot_batch *b = new (std::nothrow) hot_batch;
+  if (!b) return fail(HOT_ENOMEM, "hot_batch_create: out of host memory");
+  b->count = count;
+  b->ctx.assign(ctxs, ctxs + count);
+  b->st = static_cast<cudaStream_t>(cuda_stream);
+  b->precision = ctxs[0]->precision;
+  b->dev = ctxs[0]->dev;
+  const bool fast = b->precision == HOT_PREC_FAST;
+  int rc = fast ? batch_set_smem<true>() : batch_set_smem<false>();
+  if (rc == HOT_OK && cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev) != cudaSuccess)
+    rc = fail(HOT_ECUDA, "hot_batch_create: device query failed");
+  if (rc == HOT_OK) {
+    int per_sm = 0;
+    cudaError_t e = fast ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_batch_kernel<true, true, true>,
+                                                                        hot::kThreads, hot::step_smem_bytes(0, true))
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_batch_kernel<false, true, true>,
+                                                                        hot::kThreads, hot::step_smem_bytes(0, true));
+    if (e != cudaSuccess) rc = fail(HOT_ECUDA, "hot_batch_create: occupancy query: %s", cudaGetErrorString(e));
+    b->per_sm_max = per_sm < 1 ? 1 : per_sm;
+  }
+  if (rc == HOT_OK) rc = dalloc(&b->stamps, (size_t)count + 1);
+  if (rc == HOT_OK) rc = batch_schedule(b);
+  if (rc != HOT_OK) {
+    batch_free(b);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return HOT_OK;
+}
+
+int hot_batch_set_tiling(hot_batch *b, int rows, int blocks_per_sm, int chunk, double group_pairs) {
+  if (!b) return fail(HOT_EINVAL, "hot_batch_set_tiling: NULL batch");
+  int rc = check_tiling("hot_batch_set_tiling", rows, blocks_per_sm, chunk);
+  if (rc != HOT_OK) return rc;
+  if (!(group_pairs >= 0) || !std::isfinite(group_pairs))
+    return fail(HOT_EINVAL, "hot_batch_set_tiling: group_pairs must be finite and >= 0");
+  b->rows = rows ? rows : hot::kRowsMax;
+  b->bps = blocks_per_sm;
+  b->chunk = chunk ? chunk : hot::kChunk;
+  b->group_pairs = group_pairs > 0 ? group_pairs : 67108864.0;
+  return batch_schedule(b);
+}
+
+int hot_batch_get_tiling(const hot_batch *b, int *rows, int *blocks_per_sm, int *chunk, double *group_pairs,
+                         int *groups) {
+  if (!b) return fail(HOT_EINVAL, "hot_batch_get_tiling: NULL batch");
+  if (rows) *rows = b->rows;
+  if (blocks_per_sm) *blocks_per_sm = b->bps > 0 ? std::min(b->bps, b->per_sm_max) : b->per_sm_max;
+  if (chunk) *chunk = b->chunk;
+  if (group_pairs) *group_pairs = b->group_pairs;
+  if (groups) *groups = (int)b->groups.size();
+  return HOT_OK;
+}
+
+int hot_batch_gsw(hot_batch *b, int iters) {
+  if (!b) return fail(HOT_EINVAL, "hot_batch_gsw: NULL batch");
+  if (iters < 0) return fail(HOT_EINVAL, "hot_batch_gsw: iters = %d < 0", iters);
+  for (auto &g : b->graphs)
+    if (g.iters == iters) {
+      HOT_CUDA(cudaGraphLaunch(g.exec, b->st));
+      for (auto *c : b->ctx) c->have_fields = true;
+      b->ran = true;
+      return HOT_OK;
+    }
+  if (!b->cap) HOT_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  if (b->graphs.size() >= 8) {
+    cudaGraphExecDestroy(b->graphs.front().exec);
+    b->graphs.erase(b->graphs.begin());
+  }
+  cudaStream_t user = b->st;
+  HOT_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  b->st = b->cap;
+  int rc = batch_enqueue(b, iters);
+  b->st = user;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+  if (rc != HOT_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(HOT_ECUDA, "hot_batch_gsw: graph capture: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(HOT_ECUDA, "hot_batch_gsw: graph instantiation: %s", cudaGetErrorString(e));
+  b->graphs.push_back({iters, exec});
+  HOT_CUDA(cudaGraphLaunch(exec, b->st));
+  for (auto *c : b->ctx) c->have_fields = true;
+  b->ran = true;
+  return HOT_OK;
+}
+
+int hot_batch_autotune(hot_batch *b, int iters, int *rows, int *blocks_per_sm, int *chunk, double *us_per_iter) {
+  if (!b) return fail(HOT_EINVAL, "hot_batch_autotune: NULL batch");
+  if (iters < 1) return fail(HOT_EINVAL, "hot_batch_autotune: iters = %d < 1", iters);
+  std::vector<Saved> saved(b->count);
+  int rc = HOT_OK;
+  for (int h = 0; rc == HOT_OK && h < b->count; h++) rc = save_state(b->ctx[h], saved[h], b->st);
+  if (rc != HOT_OK) return rc;
+  auto restore = [&]() {
+    for (int h = 0; h < b->count; h++) {
+      const int r = restore_state(b->ctx[h], saved[h], b->st);
+      if (r != HOT_OK) return r;
+    }
+    return (int)HOT_OK;
+  };
+  Tiling best = {b->rows, b->bps > 0 ? std::min(b->bps, b->per_sm_max) : b->per_sm_max, b->chunk};
+  double best_us = 0;
+  const double gp = b->group_pairs;
+  rc = tune_tiling(
+      b->per_sm_max, best, best_us, [&](const Tiling &t) { return hot_batch_set_tiling(b, t.rows, t.bps, t.chunk, gp); },
+      [&](double *us) { return time_runs(b->st, iters, us, restore, [&]() { return hot_batch_gsw(b, iters); }); });
+  const int rc2 = restore();
+  cudaStreamSynchronize(b->st);
+  for (auto *c : b->ctx) c->have_fields = false;
+  b->ran = false;
+  if (rc != HOT_OK) return rc;
+  if (rc2 != HOT_OK) return rc2;
+  if (rows) *rows = best.rows;
+  if (blocks_per_sm) *blocks_per_sm = best.bps;
+  if (chunk) *chunk = best.chunk;
+  if (us_per_iter) *us_per_iter = best_us;
+  return HOT_OK;
+}
+
+int hot_batch_latency(hot_batch *b, double *ms, int count) {
+  if (!b || !ms) return fail(HOT_EINVAL, "hot_batch_latency: NULL argument");
+  if (count != b->count) return fail(HOT_EINVAL, "hot_batch_latency: count = %d, the batch has %d", count, b->count);
+  if (!b->ran) return fail(HOT_ESTATE, "hot_batch_latency: no hot_batch_gsw since the batch was (re)scheduled");
+  std::vector<unsigned long long> t(count + 1);
+  HOT_CUDA(cudaMemcpyAsync(t.data(), b->stamps, sizeof(unsigned long long) * (count + 1), cudaMemcpyDeviceToHost, b->st));
+  HOT_CUDA(cudaStreamSynchronize(b->st));
+  for (int h = 0; h < count; h++) ms[h] = (double)(long long)(t[h] - t[count]) * 1e-6;
+  return HOT_OK;
+}
+
+void hot_batch_destroy(hot_batch *b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->st);
+  batch_free(b);
+  delete b;
 }
 
 }  // extern "C"
@@ -916,6 +1507,7 @@ extern "C" int hot_field_noalloc(int width, int height, double pitch_m, double w
   a.W = width;
   a.H = height;
   a.M = M;
+  a.chunk = hot::kChunk;
   a.sub = d_sub;
   a.first = d_first;
   a.X = fast ? Xr : Xt;

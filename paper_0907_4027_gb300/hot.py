@@ -30,6 +30,7 @@ _STATUS = {0: "HOT_OK", -1: "HOT_EINVAL", -2: "HOT_ENOMEM", -3: "HOT_ECUDA", -4:
 
 _c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
 
 # Every symbol declared in include/hot.h with its C signature.
 SIGNATURES = {
@@ -42,6 +43,17 @@ SIGNATURES = {
     "hot_phase_out": (_c_int, [_vp, _vp, _c_int, _c_int]),
     "hot_get_fields": (_c_int, [_vp, _vp, _vp]),
     "hot_sync": (_c_int, [_vp]),
+    "hot_get_metrics": (_c_int, [_vp, _dp, _dp]),
+    "hot_batch_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _vp, _vp]),
+    "hot_batch_gsw": (_c_int, [_vp, _c_int]),
+    "hot_batch_destroy": (None, [_vp]),
+    "hot_batch_set_tiling": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_double]),
+    "hot_batch_get_tiling": (_c_int, [_vp, _ip, _ip, _ip, _dp, _ip]),
+    "hot_batch_autotune": (_c_int, [_vp, _c_int, _ip, _ip, _ip, _dp]),
+    "hot_batch_latency": (_c_int, [_vp, _vp, _c_int]),
+    "hot_set_tiling": (_c_int, [_vp, _c_int, _c_int, _c_int]),
+    "hot_get_tiling": (_c_int, [_vp, _ip, _ip, _ip]),
+    "hot_autotune": (_c_int, [_vp, _c_int, _ip, _ip, _ip, _dp]),
     "hot_field": (_c_int, [_vp, _vp, _vp]),
     "hot_superposition": (_c_int, [_vp, _vp]),
     "hot_field_adjoint": (_c_int, [_vp, _vp, _vp, _vp]),
@@ -172,6 +184,111 @@ def hot_field_adjoint(ctx: int, phi_dev, G_dev, grad_dev) -> None:
                               _vp(grad_dev.data_ptr())), "hot_field_adjoint")
 
 
+def hot_get_metrics(ctx: int):
+    e, u = ctypes.c_double(), ctypes.c_double()
+    _ok(lib.hot_get_metrics(_vp(ctx), ctypes.byref(e), ctypes.byref(u)), "hot_get_metrics")
+    return e.value, u.value
+
+
+def hot_batch_create(ctxs, cuda_stream: int | None = None) -> int:
+    arr = (_vp * len(ctxs))(*[_vp(c) for c in ctxs])
+    b = _vp()
+    _ok(lib.hot_batch_create(ctypes.byref(b), len(ctxs), ctypes.cast(arr, _vp), _vp(cuda_stream or 0)),
+        "hot_batch_create")
+    return b.value
+
+
+def hot_batch_gsw(batch: int, iters: int) -> None:
+    _ok(lib.hot_batch_gsw(_vp(batch), int(iters)), "hot_batch_gsw")
+
+
+def hot_batch_destroy(batch: int) -> None:
+    lib.hot_batch_destroy(_vp(batch))
+
+
+def hot_set_tiling(ctx: int, rows: int = 0, blocks_per_sm: int = 0, chunk: int = 0) -> None:
+    _ok(lib.hot_set_tiling(_vp(ctx), int(rows), int(blocks_per_sm), int(chunk)), "hot_set_tiling")
+
+
+def hot_get_tiling(ctx: int) -> dict:
+    r, b, c = _c_int(), _c_int(), _c_int()
+    _ok(lib.hot_get_tiling(_vp(ctx), ctypes.byref(r), ctypes.byref(b), ctypes.byref(c)), "hot_get_tiling")
+    return {"rows": r.value, "blocks_per_sm": b.value, "chunk": c.value}
+
+
+def hot_autotune(ctx: int, iters: int) -> dict:
+    r, b, c, us = _c_int(), _c_int(), _c_int(), ctypes.c_double()
+    _ok(lib.hot_autotune(_vp(ctx), int(iters), ctypes.byref(r), ctypes.byref(b), ctypes.byref(c),
+                         ctypes.byref(us)), "hot_autotune")
+    return {"rows": r.value, "blocks_per_sm": b.value, "chunk": c.value, "us_per_iter": us.value}
+
+
+def hot_batch_set_tiling(batch: int, rows: int = 0, blocks_per_sm: int = 0, chunk: int = 0,
+                         group_pairs: float = 0.0) -> None:
+    _ok(lib.hot_batch_set_tiling(_vp(batch), int(rows), int(blocks_per_sm), int(chunk), float(group_pairs)),
+        "hot_batch_set_tiling")
+
+
+def hot_batch_get_tiling(batch: int) -> dict:
+    r, b, c, g = _c_int(), _c_int(), _c_int(), _c_int()
+    gp = ctypes.c_double()
+    _ok(lib.hot_batch_get_tiling(_vp(batch), ctypes.byref(r), ctypes.byref(b), ctypes.byref(c), ctypes.byref(gp),
+                                 ctypes.byref(g)), "hot_batch_get_tiling")
+    return {"rows": r.value, "blocks_per_sm": b.value, "chunk": c.value, "group_pairs": gp.value,
+            "groups": g.value}
+
+
+def hot_batch_autotune(batch: int, iters: int) -> dict:
+    r, b, c, us = _c_int(), _c_int(), _c_int(), ctypes.c_double()
+    _ok(lib.hot_batch_autotune(_vp(batch), int(iters), ctypes.byref(r), ctypes.byref(b), ctypes.byref(c),
+                               ctypes.byref(us)), "hot_batch_autotune")
+    return {"rows": r.value, "blocks_per_sm": b.value, "chunk": c.value, "us_per_iter": us.value}
+
+
+def hot_batch_latency(batch: int, count: int) -> np.ndarray:
+    ms = np.empty(count)
+    _ok(lib.hot_batch_latency(_vp(batch), ms.ctypes.data_as(_vp), int(count)), "hot_batch_latency")
+    return ms
+
+
+class Batch:
+    """GSW on several Holograms at once (one launch per iteration for all of them)."""
+
+    def __init__(self, holos, stream: int | None = None):
+        self.holos = list(holos)
+        self.handle = hot_batch_create([h.ctx for h in self.holos], stream)
+
+    def gsw(self, iters: int):
+        hot_batch_gsw(self.handle, iters)
+
+    def set_tiling(self, rows: int = 0, blocks_per_sm: int = 0, chunk: int = 0, group_pairs: float = 0.0):
+        hot_batch_set_tiling(self.handle, rows, blocks_per_sm, chunk, group_pairs)
+
+    def tiling(self) -> dict:
+        return hot_batch_get_tiling(self.handle)
+
+    def autotune(self, iters: int) -> dict:
+        return hot_batch_autotune(self.handle, iters)
+
+    def latency(self) -> np.ndarray:
+        """Per-hologram ms from the start of the last gsw() to that hologram's completion."""
+        return hot_batch_latency(self.handle, len(self.holos))
+
+    def metrics(self):
+        return [hot_get_metrics(h.ctx) for h in self.holos]
+
+    def close(self):
+        if self.handle:
+            hot_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def hot_sync(ctx: int) -> None:
     _ok(lib.hot_sync(_vp(ctx)), "hot_sync")
 
@@ -277,11 +394,24 @@ class Hologram:
     def fields(self):
         return hot_get_fields(self.ctx, self.M)
 
+    def metrics(self):
+        return hot_get_metrics(self.ctx)
+
     def sync(self):
         hot_sync(self.ctx)
 
     def use_graphs(self, enable: bool = True):
         hot_use_graphs(self.ctx, enable)
+
+    def set_tiling(self, rows: int = 0, blocks_per_sm: int = 0, chunk: int = 0):
+        hot_set_tiling(self.ctx, rows, blocks_per_sm, chunk)
+
+    def tiling(self) -> dict:
+        return hot_get_tiling(self.ctx)
+
+    def autotune(self, iters: int) -> dict:
+        """Picks the fastest tiling for hot_gsw(iters); phases and weights are kept."""
+        return hot_autotune(self.ctx, iters)
 
     def profile(self, enable: bool = True):
         hot_profile(self.ctx, enable)
