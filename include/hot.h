@@ -138,6 +138,36 @@ int hot_field(hot_ctx *c, const float *phi, float *V);
  * GSW state is not touched.  HOT_ESTATE before hot_set_traps. */
 int hot_field_adjoint(hot_ctx *c, const float *phi, const float *G, float *grad);
 
+/* ---- row bands: the sharded form --------------------------------------------------------
+ * Eq. 1 is a sum over pixels, so the pixels can be split into row bands, one per GPU: each
+ * band computes partial sums of V_m over its rows, the partial sums are added over the bands
+ * (one all-reduce of 2M int64 per iteration), and every band then derives the same weights and
+ * coefficients (Sec. 3) from the same global sums and back-projects its own rows.  The sums
+ * are 64-bit fixed-point integers, so the all-reduce is exact and independent of its order. */
+
+/* Makes the context rows y0 .. y0+height-1 of a width x total_height hologram (its pixel
+ * coordinates and the 1/N of Eq. 1 are those of the whole hologram).  total_height = height,
+ * y0 = 0 is the plain context.  Rebuilds the phase tables if traps are set; synchronises.
+ * HOT_EINVAL if the band does not fit. */
+int hot_set_band(hot_ctx *c, int total_height, int y0);
+
+/* The launch sequence of hot_gsw, one launch per call, for a caller that adds the partial
+ * sums over the bands between launches (not captured as a graph):
+ *   hot_sharded_begin(c)      launch 0: partial sums of V for the current phases;
+ *   hot_sharded_sums(c, k, &p) DEVICE pointer to launch k's partial sums: int64 [2][M] (Re
+ *                             parts, then Im parts; two's complement), to be replaced in
+ *                             place, in stream order on the context's stream, by their sum over
+ *                             all bands before the next launch;
+ *   hot_sharded_step(c, k)    launch k = 1, 2, ...: weight update, back-projection of the band,
+ *                             partial sums of the new forward field;
+ *   hot_sharded_end(c, K, &e, &u) after launch K: the metrics (Eq. 4) and fields of the summed
+ *                             sums, weights home; e, u nullable (synchronises when given).
+ * Launches are queued on the context's stream.  HOT_ESTATE for a call out of this order. */
+int hot_sharded_begin(hot_ctx *c);
+int hot_sharded_step(hot_ctx *c, int k);
+int hot_sharded_sums(hot_ctx *c, int k, void **sums_dev);
+int hot_sharded_end(hot_ctx *c, int iters, double *eff_out, double *unif_out);
+
 /* Efficiency e and uniformity u (Eq. 4) of the last forward evaluation (hot_gsw, hot_field or
  * hot_batch_gsw).  Synchronises.  HOT_ESTATE if none has run since the traps or phases changed. */
 int hot_get_metrics(hot_ctx *c, double *eff_out, double *unif_out);

@@ -599,8 +599,10 @@ __global__ void stamp_kernel(unsigned long long *t) { *t = global_timer_ns(); }
 
 // Per (trap, column) and (trap, row) phase parts of Eq. 2 reduced modulo one turn in FP64.
 // abc: [M][3] = a_m, b_m, c_m in turns (see the file header).  Writes turns and radians.
-__global__ void build_tables_kernel(int W, int H, int M, const double *abc, float *Xt, float *Yt,
-                                    float *Xr, float *Yr) {
+// A row band (rows y_off .. y_off+H-1 of a hologram of H_total rows) takes the row parts of
+// its global rows.
+__global__ void build_tables_kernel(int W, int H, int H_total, int y_off, int M, const double *abc, float *Xt,
+                                    float *Yt, float *Xr, float *Yr) {
   const long long total = (long long)M * (W + H);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -611,7 +613,7 @@ __global__ void build_tables_kernel(int W, int H, int M, const double *abc, floa
       const double q = (double)(i - W / 2);
       t = fma(cm * q, q, am * q);
     } else {
-      const double q = (double)((i - W) - H / 2);
+      const double q = (double)((i - W) + y_off - H_total / 2);
       t = fma(cm * q, q, bm * q);
     }
     t -= rint(t);  // [-1/2, 1/2] turns

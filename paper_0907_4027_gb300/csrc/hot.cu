@@ -56,6 +56,7 @@ void dfree(T *&p) {
 
 struct hot_ctx {
   int W = 0, H = 0;
+  int H_total = 0, y_off = 0;  // row band: rows y_off .. y_off+H-1 of a W x H_total hologram
   double pitch = 0, lam = 0, focal = 0;
   cudaStream_t st = nullptr;
   int dev = 0;
@@ -69,6 +70,7 @@ struct hot_ctx {
   // (0: as many as fit), traps per staged chunk
   int tile_rows = hot::kRowsMax, tile_bps = 0, tile_chunk = hot::kChunk;
   int sched_bps = 0, sched_bps_max = 0;  // resident blocks per SM in the schedule; occupancy limit
+  int shard_k = -1;                      // last launch of a sharded sequence (hot_sharded_*)
   // state
   float *phi = nullptr;  // [N]
   int M = 0;
@@ -104,6 +106,16 @@ struct hot_ctx {
 namespace {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
+
+// Pixels of the whole hologram (all row bands): the normalisation 1/N of Eq. 1.
+double n_total(const hot_ctx *c) { return (double)c->W * (double)c->H_total; }
+
+// Fixed-point scale of the field sums: |sum| <= N (whole hologram), kept below 2^61.
+int fixed_point_shift(long long n) {
+  int bits = 0;
+  while ((1LL << bits) < n) bits++;
+  return 61 - bits;
+}
 
 void drop_graphs(hot_ctx *c) {
   for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
@@ -207,12 +219,12 @@ int launch_tile(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const f
   a.w_in = c->w + (size_t)c->M * ((k + 1) & 1);
   a.w_out = c->w + (size_t)c->M * (k & 1);
   a.fx_scale = ldexpf(1.0f, c->fx_shift);
-  a.inv_fx_n = (float)(1.0 / ((double)c->W * (double)c->H * ldexp(1.0, c->fx_shift)));
+  a.inv_fx_n = (float)(1.0 / (n_total(c) * ldexp(1.0, c->fx_shift)));
   a.angle_units = FAST ? 1.0f : 0.15915494309189535f;
   if (phi) a.phi = const_cast<float *>(phi);  // read only: forward field or adjoint of given phases
   a.G = G;
   a.grad = grad;
-  a.inv_n = (float)(1.0 / ((double)c->W * (double)c->H));
+  a.inv_n = (float)(1.0 / (n_total(c)));
   const int smem = hot::step_smem_bytes(c->M, BACK);
   Probe p(c, BACK && FWD ? HOT_KERNEL_STEP : FWD ? HOT_KERNEL_FORWARD : HOT_KERNEL_OTHER);
   launch(c, hot::gsw_step_kernel<FAST, BACK, FWD, ADJ>, c->grid, hot::kThreads, smem, pdl, a);
@@ -304,7 +316,7 @@ int launch_finalize(hot_ctx *c, bool pdl, int iters) {
   f.w_dst = c->w;
   f.Vsum = c->Vsum;
   f.metrics = c->metrics;
-  f.inv_fx_n = (float)(1.0 / ((double)c->W * (double)c->H * ldexp(1.0, c->fx_shift)));
+  f.inv_fx_n = (float)(1.0 / (n_total(c) * ldexp(1.0, c->fx_shift)));
   Probe p(c, HOT_KERNEL_FINISH);
   launch(c, hot::gsw_finalize_kernel, 1, hot::kFinalizeThreads, 0, pdl, f);
   return check_launch(c, "gsw_finalize_kernel");
@@ -314,6 +326,16 @@ int launch_finalize(hot_ctx *c, bool pdl, int iters) {
 // Inside the sequence every kernel is a programmatic dependent of the one before it (except
 // when profiling, where events separate the launches); the first one waits normally for
 // whatever preceded hot_gsw in the stream (trap tables, phases).
+// Phase tables of the context's traps (Eq. 2 split into column and row parts).
+int launch_build_tables(hot_ctx *c) {
+  const long long total = (long long)c->M * (c->W + c->H);
+  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  Probe p(c, HOT_KERNEL_OTHER);
+  hot::build_tables_kernel<<<blocks, 256, 0, c->st>>>(c->W, c->H, c->H_total, c->y_off, c->M, c->abc, c->Xt, c->Yt,
+                                                      c->Xr, c->Yr);
+  return check_launch(c, "build_tables_kernel");
+}
+
 int enqueue_gsw(hot_ctx *c, int iters) {
   const bool pdl = !c->profiling;
   int rc = launch_step(c, false, true, false, 0);       // V^1 = F(phi^0)
@@ -384,11 +406,8 @@ int hot_create(hot_ctx **out, int width, int height, double pitch_m, double wave
   c->lam = wavelength_m;
   c->focal = focal_m;
   c->st = static_cast<cudaStream_t>(cuda_stream);
-  {  // fixed-point scale of the field sums: |sum| <= N, kept below 2^61
-    int bits = 0;
-    while ((1LL << bits) < (long long)width * height) bits++;
-    c->fx_shift = 61 - bits;
-  }
+  c->H_total = height;
+  c->fx_shift = fixed_point_shift((long long)width * height);
   int rc = HOT_OK;
   cudaError_t e = cudaGetDevice(&c->dev);
   if (e != cudaSuccess) rc = fail(HOT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
@@ -485,12 +504,8 @@ int hot_set_traps(hot_ctx *c, int M, const double *xyz_m, const double *w0) {
   free(abc);
   free(wh);
   if (e != cudaSuccess) return fail(HOT_ECUDA, "hot_set_traps: %s", cudaGetErrorString(e));
-  const long long total = (long long)M * (c->W + c->H);
-  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-  Probe p(c, HOT_KERNEL_OTHER);
-  hot::build_tables_kernel<<<blocks, 256, 0, c->st>>>(c->W, c->H, M, c->abc, c->Xt, c->Yt, c->Xr, c->Yr);
   c->have_fields = false;
-  return check_launch(c, "build_tables_kernel");
+  return launch_build_tables(c);
 }
 
 int hot_set_weights(hot_ctx *c, const double *w) {
@@ -583,7 +598,7 @@ int hot_get_fields(hot_ctx *c, double *V, double *w) {
   if (V) HOT_CUDA(cudaMemcpyAsync(vs.data(), c->Vsum, sizeof(long long) * 2 * c->M, cudaMemcpyDeviceToHost, c->st));
   if (w) HOT_CUDA(cudaMemcpyAsync(wf.data(), c->w, sizeof(float) * c->M, cudaMemcpyDeviceToHost, c->st));
   HOT_CUDA(cudaStreamSynchronize(c->st));
-  const double inv = 1.0 / ((double)c->W * (double)c->H * ldexp(1.0, c->fx_shift));
+  const double inv = 1.0 / (n_total(c) * ldexp(1.0, c->fx_shift));
   for (int m = 0; V && m < c->M; m++) {  // fixed-point sums -> V_m
     V[2 * m] = (double)vs[m] * inv;
     V[2 * m + 1] = (double)vs[c->M + m] * inv;
@@ -599,7 +614,7 @@ int hot_field(hot_ctx *c, const float *phi, float *V) {
   int rc = fast ? launch_tile<true, false, true>(c, false, 0, phi) : launch_tile<false, false, true>(c, false, 0, phi);
   if (rc == HOT_OK) rc = launch_finalize(c, false, 0);  // w stays in w[0]; accumulators cleared
   if (rc != HOT_OK) return rc;
-  const double inv = 1.0 / ((double)c->W * (double)c->H * ldexp(1.0, c->fx_shift));
+  const double inv = 1.0 / (n_total(c) * ldexp(1.0, c->fx_shift));
   hot::sums_to_fields_kernel<<<(c->M + 255) / 256, 256, 0, c->st>>>(c->M, c->Vsum, inv, reinterpret_cast<float2 *>(V));
   rc = check_launch(c, "sums_to_fields_kernel");
   if (rc == HOT_OK) c->have_fields = true;
@@ -637,6 +652,66 @@ int hot_field_adjoint(hot_ctx *c, const float *phi, const float *G, float *grad)
   const float2 *g = reinterpret_cast<const float2 *>(G);
   return c->precision == HOT_PREC_FAST ? launch_tile<true, true, false, true>(c, false, 0, phi, g, grad)
                                        : launch_tile<false, true, false, true>(c, false, 0, phi, g, grad);
+}
+
+int hot_set_band(hot_ctx *c, int total_height, int y0) {
+  if (!c) return fail(HOT_EINVAL, "hot_set_band: NULL context");
+  if (total_height < c->H || y0 < 0 || y0 > total_height - c->H || (long long)c->W * total_height >= (1LL << 31))
+    return fail(HOT_EINVAL, "hot_set_band: rows %d .. %d not inside a hologram of %d rows", y0, y0 + c->H - 1,
+                total_height);
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  drop_graphs(c);
+  c->H_total = total_height;
+  c->y_off = y0;
+  c->fx_shift = fixed_point_shift((long long)c->W * total_height);
+  c->have_fields = false;
+  c->shard_k = -1;
+  return c->M ? launch_build_tables(c) : HOT_OK;
+}
+
+int hot_sharded_begin(hot_ctx *c) {
+  if (!c) return fail(HOT_EINVAL, "hot_sharded_begin: NULL context");
+  if (!c->M) return fail(HOT_ESTATE, "hot_sharded_begin: no traps set");
+  c->shard_k = -1;
+  c->have_fields = false;
+  const int rc = launch_step(c, false, true, false, 0);
+  if (rc == HOT_OK) c->shard_k = 0;
+  return rc;
+}
+
+int hot_sharded_step(hot_ctx *c, int k) {
+  if (!c) return fail(HOT_EINVAL, "hot_sharded_step: NULL context");
+  if (c->shard_k < 0 || k != c->shard_k + 1)
+    return fail(HOT_ESTATE, "hot_sharded_step: launch %d does not follow launch %d", k, c->shard_k);
+  const int rc = launch_step(c, true, true, false, k);
+  if (rc == HOT_OK) c->shard_k = k;
+  return rc;
+}
+
+int hot_sharded_sums(hot_ctx *c, int k, void **sums_dev) {
+  if (!c || !sums_dev) return fail(HOT_EINVAL, "hot_sharded_sums: NULL argument");
+  if (c->shard_k < 0 || k != c->shard_k)
+    return fail(HOT_ESTATE, "hot_sharded_sums: launch %d is not the last one (%d)", k, c->shard_k);
+  *sums_dev = c->acc + 2 * (size_t)c->M * (k % 3);
+  return HOT_OK;
+}
+
+int hot_sharded_end(hot_ctx *c, int iters, double *eff_out, double *unif_out) {
+  if (!c) return fail(HOT_EINVAL, "hot_sharded_end: NULL context");
+  if (c->shard_k < 0 || iters != c->shard_k)
+    return fail(HOT_ESTATE, "hot_sharded_end: iters = %d, last launch %d", iters, c->shard_k);
+  const int rc = launch_finalize(c, false, iters);
+  c->shard_k = -1;
+  if (rc != HOT_OK) return rc;
+  c->have_fields = true;
+  if (eff_out || unif_out) {
+    float m[2];
+    HOT_CUDA(cudaMemcpyAsync(m, c->metrics, sizeof m, cudaMemcpyDeviceToHost, c->st));
+    HOT_CUDA(cudaStreamSynchronize(c->st));
+    if (eff_out) *eff_out = m[0];
+    if (unif_out) *unif_out = m[1];
+  }
+  return HOT_OK;
 }
 
 int hot_get_metrics(hot_ctx *c, double *eff_out, double *unif_out) {
@@ -777,13 +852,13 @@ hot::StepArgs step_args(const hot_ctx *c, int k, int chunk) {
   a.w_in = c->w + (size_t)c->M * ((k + 1) & 1);
   a.w_out = c->w + (size_t)c->M * (k & 1);
   a.fx_scale = ldexpf(1.0f, c->fx_shift);
-  a.inv_fx_n = (float)(1.0 / ((double)c->W * (double)c->H * ldexp(1.0, c->fx_shift)));
+  a.inv_fx_n = (float)(1.0 / (n_total(c) * ldexp(1.0, c->fx_shift)));
   a.angle_units = fast ? 1.0f : 0.15915494309189535f;
-  a.inv_n = (float)(1.0 / ((double)c->W * (double)c->H));
+  a.inv_n = (float)(1.0 / (n_total(c)));
   return a;
 }
 
-double pairs_of(const hot_ctx *c) { return (double)c->W * (double)c->H * (double)c->M; }
+double pairs_of(const hot_ctx *c) { return n_total(c) * (double)c->M; }
 
 // One group's work schedule: the row segments of its holograms in order, each weighted by its
 // trap count, dealt out to one wave of G blocks in equal shares (a segment goes to the block
@@ -854,7 +929,7 @@ int build_group(hot_batch *b, hot_batch::Group &g) {
       f.w_dst = c->w;
       f.Vsum = c->Vsum;
       f.metrics = c->metrics;
-      f.inv_fx_n = (float)(1.0 / ((double)c->W * (double)c->H * ldexp(1.0, c->fx_shift)));
+      f.inv_fx_n = (float)(1.0 / (n_total(c) * ldexp(1.0, c->fx_shift)));
       f.done = b->stamps + g.members[i];
     }
     if (rc == HOT_OK && cudaMemcpy(g.fin[r6], fs.data(), sizeof(hot::FinalizeArgs) * count, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -1497,7 +1572,7 @@ extern "C" int hot_field_noalloc(int width, int height, double pitch_m, double w
   HOT_CUDA(cudaGetLastError());
   const long long total = (long long)M * (width + height);
   const int tb = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-  hot::build_tables_kernel<<<tb, 256, 0, st>>>(width, height, M, abc, Xt, Yt, Xr, Yr);
+  hot::build_tables_kernel<<<tb, 256, 0, st>>>(width, height, height, 0, M, abc, Xt, Yt, Xr, Yr);
   HOT_CUDA(cudaGetLastError());
 
   int bits = 0;

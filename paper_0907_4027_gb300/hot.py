@@ -52,6 +52,11 @@ SIGNATURES = {
     "hot_batch_autotune": (_c_int, [_vp, _c_int, _ip, _ip, _ip, _dp]),
     "hot_batch_latency": (_c_int, [_vp, _vp, _c_int]),
     "hot_set_tiling": (_c_int, [_vp, _c_int, _c_int, _c_int]),
+    "hot_set_band": (_c_int, [_vp, _c_int, _c_int]),
+    "hot_sharded_begin": (_c_int, [_vp]),
+    "hot_sharded_step": (_c_int, [_vp, _c_int]),
+    "hot_sharded_sums": (_c_int, [_vp, _c_int, ctypes.POINTER(_vp)]),
+    "hot_sharded_end": (_c_int, [_vp, _c_int, _dp, _dp]),
     "hot_get_tiling": (_c_int, [_vp, _ip, _ip, _ip]),
     "hot_autotune": (_c_int, [_vp, _c_int, _ip, _ip, _ip, _dp]),
     "hot_field": (_c_int, [_vp, _vp, _vp]),
@@ -206,6 +211,31 @@ def hot_batch_destroy(batch: int) -> None:
     lib.hot_batch_destroy(_vp(batch))
 
 
+def hot_set_band(ctx: int, total_height: int, y0: int) -> None:
+    _ok(lib.hot_set_band(_vp(ctx), int(total_height), int(y0)), "hot_set_band")
+
+
+def hot_sharded_begin(ctx: int) -> None:
+    _ok(lib.hot_sharded_begin(_vp(ctx)), "hot_sharded_begin")
+
+
+def hot_sharded_step(ctx: int, k: int) -> None:
+    _ok(lib.hot_sharded_step(_vp(ctx), int(k)), "hot_sharded_step")
+
+
+def hot_sharded_sums(ctx: int, k: int) -> int:
+    """Device address of launch k's partial sums, int64 [2][M]."""
+    p = _vp()
+    _ok(lib.hot_sharded_sums(_vp(ctx), int(k), ctypes.byref(p)), "hot_sharded_sums")
+    return p.value
+
+
+def hot_sharded_end(ctx: int, iters: int):
+    e, u = ctypes.c_double(), ctypes.c_double()
+    _ok(lib.hot_sharded_end(_vp(ctx), int(iters), ctypes.byref(e), ctypes.byref(u)), "hot_sharded_end")
+    return e.value, u.value
+
+
 def hot_set_tiling(ctx: int, rows: int = 0, blocks_per_sm: int = 0, chunk: int = 0) -> None:
     _ok(lib.hot_set_tiling(_vp(ctx), int(rows), int(blocks_per_sm), int(chunk)), "hot_set_tiling")
 
@@ -348,6 +378,14 @@ def hot_field_noalloc(width: int, height: int, pitch_m: float, wavelength_m: flo
 
 # ---- convenience class -------------------------------------------------------------
 
+class _DeviceArray:
+    """A device buffer owned by the library, exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 2, "strides": None}
+
+
 class Hologram:
     """One GSW context: a W x H SLM with the given optics (metres)."""
 
@@ -405,6 +443,25 @@ class Hologram:
 
     def set_tiling(self, rows: int = 0, blocks_per_sm: int = 0, chunk: int = 0):
         hot_set_tiling(self.ctx, rows, blocks_per_sm, chunk)
+
+    def set_band(self, total_height: int, y0: int):
+        """This context holds rows y0 .. y0+H-1 of a W x total_height hologram."""
+        hot_set_band(self.ctx, total_height, y0)
+
+    # the sharded launch sequence (see paper_0907_4027_gb300.sharded)
+    def sharded_begin(self):
+        hot_sharded_begin(self.ctx)
+
+    def sharded_step(self, k: int):
+        hot_sharded_step(self.ctx, k)
+
+    def sharded_sums(self, k: int):
+        """Launch k's partial sums as a zero-copy torch int64 tensor [2*M] on the device."""
+        import torch
+        return torch.as_tensor(_DeviceArray(hot_sharded_sums(self.ctx, k), 2 * self.M, "<i8"), device="cuda")
+
+    def sharded_end(self, iters: int):
+        return hot_sharded_end(self.ctx, iters)
 
     def tiling(self) -> dict:
         return hot_get_tiling(self.ctx)

@@ -244,3 +244,23 @@ def test_superposition_matches_oracle(hot, precision):
     r1 = oracle.gsw(g.geom, g.xyz, 1, phi_sr)
     assert abs(e1 - r1["e"]) < ABS_EU and abs(u1 - r1["u"]) < ABS_EU
     assert u_sr < 0.15 and e_sr > 0.7 and u1 >= u_sr      # Sec. 5: SR is inefficient and non-uniform
+
+
+@pytest.mark.parametrize("n", [3, 9])
+def test_paper_grid_at_20hz_budget_matches_oracle(hot, n):
+    """Sec. 5 grids (n x n, 4 um spacing, 768^2 SLM): the random superposition, then GSW from
+    it with the iteration count of the paper's 20 Hz budget; e and u against the oracle."""
+    w = wl.paper_grid(n, 768)
+    w.precision = "fast"
+    coef = np.exp(1j * np.random.default_rng(n).uniform(0.0, 2.0 * np.pi, w.M))
+    k = max(1, int(50.0 / (0.44 * w.M)))
+    with make(hot, w) as h:
+        h.superposition(coef)
+        phi_sr = h.phase("f32")
+        e_sr, u_sr = h.gsw(0)
+        e, u = h.gsw(k)
+    oe_sr, ou_sr = oracle.metrics(oracle.forward(w.geom, w.xyz, oracle.backproject(w.geom, w.xyz, coef)))
+    r = oracle.gsw(w.geom, w.xyz, k, phi_sr.astype(np.float64))
+    assert abs(e_sr - oe_sr) < ABS_EU and abs(u_sr - ou_sr) < ABS_EU
+    assert abs(e - r["e"]) < ABS_EU and abs(u - r["u"]) < ABS_EU, (e, r["e"], u, r["u"])
+    assert e > 0.8  # Sec. 5: the efficiency stays high at the 20 Hz budget
