@@ -34,6 +34,8 @@ METRIC = "GSW pixel-trap updates/s (512x512 px, M=100, 30 iterations)"
 UNIT = "updates/s"
 SFU_LANES_PER_SM = 16          # sin.approx / cos.approx results per clock per SM (sm_103a)
 SFU_OPS_PER_UPDATE = 4         # one sin + one cos in the forward field, one each in back-projection
+FMA_LANES_PER_SM = 128         # FP32 FMA results per clock per SM (sm_103a)
+FMA_OPS_PER_UPDATE = 8         # separable mode: one complex multiply-add (4 FMA) in each step
 L2_FLUSH_BYTES = 256 << 20     # > 129 MB L2
 
 
@@ -44,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--workload", default="rand100_512")
+    ap.add_argument("--precision", default=None, choices=["accurate", "fast", "separable"],
+                    help="override the workload's mode (separable: its own FP32-FMA roofline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision-report", action="store_true",
                     help="errors of both precision modes against the FP64 oracle, per result")
@@ -181,10 +185,10 @@ def kernel_source_hash() -> str:
     return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per launch of the fused step kernel from the committed ncu summary, if the
-    summary was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"gsw_step_{workload}.md")
+def profiled_traffic(workload: str, kernel: str = "step"):
+    """DRAM bytes per launch of the fused step kernel (gsw_step / gsw_sep) from the committed
+    ncu summary, if the summary was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"gsw_{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -211,6 +215,9 @@ def run_engine(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w = wl.NAMED[args.workload]()
+    if args.precision:
+        w.precision = args.precision
+    sep = w.precision == "separable"
     stream = torch.cuda.current_stream()
     h = hot.Hologram(w.W, w.H, w.pitch, w.wavelength, w.focal, stream.cuda_stream, w.precision)
     h.set_traps(w.xyz, w.w0)
@@ -288,17 +295,26 @@ def run_engine(args):
 
     # roofline of the dominant kernel (weight update + back-projection + forward field of one
     # GSW iteration per launch)
+    # Dominant kernel: the fused step kernel, one launch per GSW iteration (one unit of work
+    # per pair).  Its duration in the real pipeline (graph replay, each launch a programmatic
+    # dependent of the previous one) is the marginal time of an iteration; the profiled pass
+    # (launches one by one between CUDA events) gives the unpipelined duration and the shares.
     step_kernel_ms, step_kernel_n = prof["step"]
+    units_per_launch = 1.0
     avg_launch_s = iter_ms * 1e-3
-    achieved = w.N * w.M / avg_launch_s
+    achieved = w.N * w.M * units_per_launch / avg_launch_s
     dev = torch.cuda.get_device_properties(local)
     sm_max_mhz = 2070.0
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks_path):
         sm_max_mhz = float(json.load(open(peaks_path)).get("sm_max_mhz", sm_max_mhz))
-    peak = dev.multi_processor_count * SFU_LANES_PER_SM * sm_max_mhz * 1e6 / SFU_OPS_PER_UPDATE
-    sfu_measured = hot.hot_sfu_rate(0)[0]
-    traffic = profiled_traffic(args.workload)
+    if sep:
+        lanes, ops, pipe = FMA_LANES_PER_SM, FMA_OPS_PER_UPDATE, "FP32 FMA"
+    else:
+        lanes, ops, pipe = SFU_LANES_PER_SM, SFU_OPS_PER_UPDATE, "SFU"
+    peak = dev.multi_processor_count * lanes * sm_max_mhz * 1e6 / ops
+    lanes_measured = hot.hot_sfu_rate(3 if sep else 0)[0]
+    traffic = profiled_traffic(args.workload, "sep" if sep else "step")
     kernel_share = {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4)
                     for k, v in prof.items()}
 
@@ -348,12 +364,14 @@ def run_engine(args):
             "holograms_per_s": world * args.steps / (total_ms * 1e-3),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "updates/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "gsw_step_kernel<fast, back, fwd> (one GSW iteration per launch)",
-                         "peak_basis": f"{dev.multi_processor_count} SMs x {SFU_LANES_PER_SM} SFU "
-                                       f"lanes/clk x {sm_max_mhz:.0f} MHz / {SFU_OPS_PER_UPDATE} "
-                                       "SFU ops per update",
-                         "sfu_lanes_per_clk_per_sm_measured": round(sfu_measured, 2),
+                         "kernel": ("gsw_sep_kernel<back, fwd>" if sep else
+                                    f"gsw_step_kernel<{w.precision}, back, fwd>") + " (one GSW iteration per launch)",
+                         "peak_basis": f"{dev.multi_processor_count} SMs x {lanes} {pipe} "
+                                       f"lanes/clk x {sm_max_mhz:.0f} MHz / {ops} "
+                                       f"{pipe} ops per update",
+                         "lanes_per_clk_per_sm_measured": round(lanes_measured, 2),
                          "avg_launch_us": avg_launch_s * 1e6,
+                         "units_per_launch": units_per_launch,
                          "launch_timing": f"marginal iteration time of graph-replayed hot_gsw({w.iters}) "
                                           f"vs hot_gsw({k_small}), CUDA events, median of {n_roof}",
                          "avg_launch_us_unpipelined": step_kernel_ms * 1e3 / max(step_kernel_n, 1)},

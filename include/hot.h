@@ -48,7 +48,10 @@ typedef enum {
 
 typedef enum {
   HOT_PREC_ACCURATE = 0, /* sincospif on the exactly reduced phase (FP32, ~1 ulp) */
-  HOT_PREC_FAST = 1      /* sin.approx / cos.approx (SFU) on the reduced phase */
+  HOT_PREC_FAST = 1,     /* sin.approx / cos.approx (SFU) on the reduced phase */
+  HOT_PREC_SEPARABLE = 2 /* Eq. 2 factorised: e^{i Delta} = e^{i X_m(ix)} e^{i Y_m(iy)} from FP32
+                            complex tables (FP64 cos/sin once per entry); per pair one complex
+                            multiply-add in each step, no transcendental function */
 } hot_precision;
 
 typedef enum {
@@ -80,7 +83,9 @@ int hot_set_weights(hot_ctx *c, const double *w);
  * host memory (on_device = 0) or device memory (on_device = 1). */
 int hot_set_phase(hot_ctx *c, const float *phi, int on_device);
 
-/* Selects HOT_PREC_ACCURATE or HOT_PREC_FAST for the following calls. */
+/* Selects HOT_PREC_ACCURATE, HOT_PREC_FAST or HOT_PREC_SEPARABLE for the following calls
+ * (switching to or from HOT_PREC_SEPARABLE synchronises and rebuilds the work schedule).
+ * HOT_EINVAL for another value. */
 int hot_set_precision(hot_ctx *c, int precision);
 
 /* Runs `iters` GSW iterations (Sec. 3, Fig. 2) from the current phases and weights:
@@ -92,8 +97,25 @@ int hot_set_precision(hot_ctx *c, int precision);
  * eff_out / unif_out (host, nullable): if either is non-NULL the call synchronises and
  * writes them; otherwise it returns once the work is queued.  Readings where the paper
  * is silent: if |V_m| < 1e-30 the unit field is taken as 1 and w_m is kept; arg(0) = 0.
+ * By default each iteration is one kernel launch, the sequence replayed as a CUDA graph; with
+ * hot_use_persistent the iterations run in one cooperative launch whose blocks meet at a
+ * grid-wide barrier between iterations.  There a barrier wait longer than the wait limit
+ * (hot_set_wait_limit) makes the kernel leave early, and the next synchronising call
+ * (this one with eff_out/unif_out, hot_sync, hot_get_fields, hot_get_metrics) returns
+ * HOT_ETIMEOUT: the accumulators are reset and the phases are undefined.
  * HOT_ESTATE before hot_set_traps; HOT_EINVAL if iters < 0. */
 int hot_gsw(hot_ctx *c, int iters, double *eff_out, double *unif_out);
+
+/* enable != 0: hot_gsw runs as one persistent cooperative launch plus the finalize kernel;
+ * 0 (the default): one launch per iteration, replayed as a CUDA graph (hot_use_graphs), whose
+ * programmatic dependent launches overlap consecutive iterations.  Both forms use the same
+ * schedule and arithmetic and give the same bits. */
+int hot_use_persistent(hot_ctx *c, int enable);
+
+/* Longest wait at one grid barrier of the persistent kernel, in seconds (default 2; 0 makes
+ * every wait run out at once, which exercises the HOT_ETIMEOUT path).  HOT_EINVAL outside
+ * [0, 60]. */
+int hot_set_wait_limit(hot_ctx *c, double seconds);
 
 /* Writes the current phases (N pixels, row-major) to dst in format fmt (hot_format):
  * float32 radians in (-pi, pi] or uint8 grey levels (Sec. 5: 256 levels linear in
@@ -240,7 +262,8 @@ int hot_batch_latency(hot_batch *b, double *ms, int count);
 /* Frees the batch (NULL-safe); its contexts are not touched. */
 void hot_batch_destroy(hot_batch *b);
 
-/* Waits for all work queued by the context. */
+/* Waits for all work queued by the context.  HOT_ETIMEOUT if a barrier wait of the persistent
+ * kernel ran out since the last check (see hot_gsw). */
 int hot_sync(hot_ctx *c);
 
 /* Number of kernels the context has launched since creation (instrumentation). */
@@ -270,7 +293,8 @@ void hot_destroy(hot_ctx *c);
  * throughput of the special-function unit that bounds hot_gsw in HOT_PREC_FAST mode, in
  * lane results per clock per SM, with a dependency-free loop of 1024 threads per SM whose
  * arguments change every iteration (clock64-timed).  op: 0 = sin.approx and cos.approx of
- * one argument (the pattern of the GSW kernels), 1 = sin.approx alone, 2 = ex2.approx.
+ * one argument (the pattern of the GSW kernels), 1 = sin.approx alone, 2 = ex2.approx,
+ * 3 = FP32 fused multiply-add (the pipe that bounds HOT_PREC_SEPARABLE).
  * *per_clk_per_sm receives the rate and *sms (nullable) the SM count.  Synchronises the
  * device; takes a few milliseconds. */
 int hot_sfu_rate(int op, double *per_clk_per_sm, int *sms);

@@ -52,6 +52,8 @@ struct StepArgs {
   const int *first;       // [gridDim.x + 1]: block b processes sub-tiles first[b] .. first[b+1]-1
   const float *X;         // [M][W] column phase parts (turns if accurate, radians if fast)
   const float *Y;         // [M][H] row phase parts (same unit)
+  const float2 *Xc;       // [M][W] e^{i 2pi X} (separable variant)
+  const float2 *Yc;       // [M][H] e^{i 2pi Y} (separable variant)
   float *phi;             // [H*W] pixel phases, radians
   // BACK: weight update and coefficients from the previous launch's forward field
   const unsigned long long *acc_in;  // [2][M] fixed-point sums of the previous forward: Re, Im
@@ -114,6 +116,11 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid
   const int n = valid ? 4 : 0;  // 0 source bytes: the destination is zero-filled
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -136,7 +143,7 @@ __device__ __forceinline__ float2 field_from_sums(const StepArgs &a, int m) {
 __device__ __forceinline__ float2 coefficient(const StepArgs &a, int m, float mean) {
   const float2 v = field_from_sums(a, m);
   const float am = sqrtf(v.x * v.x + v.y * v.y);
-  float w = a.w_in[m];
+  float w = __ldcg(a.w_in + m);  // written by other blocks (L2, not a possibly stale L1 line)
   if (am >= 1e-30f) w = w * mean / am;
   return make_float2(w, am >= 1e-30f ? atan2f(v.y, v.x) * a.angle_units : 0.f);
 }
@@ -597,12 +604,353 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_batch_kernel(const __grid_con
 // Start stamp of a batched sequence (%globaltimer, ns).
 __global__ void stamp_kernel(unsigned long long *t) { *t = global_timer_ns(); }
 
+// ---------------------------------------------------------------------------------------------
+// Separable variant.  Eq. 2 is a sum of a column part and a row part, so every pair's
+// exponential factorises: e^{i Delta_j^m} = Xc_m(ix) Yc_m(iy), with both factors tabulated once
+// per trap (FP64 cos/sin of the exactly reduced turns, stored as FP32 complex).  Per pair the
+// back-projection then takes one complex multiply-add,
+//   S_j += Yc_m(iy) [c_m Xc_m(ix)]           (the bracket once per trap and lane),
+// and the forward field another,
+//   V_m += conj(Xc_m(ix)) sum_iy u_j conj(Yc_m(iy))   with u_j = e^{i phi_j},
+// i.e. 8 FP32 FMA per pixel-trap update and no per-pair transcendental function (one sincos
+// per pixel and iteration gives u_j from the stored phase).  The coefficients are kept
+// complex, c_m = w_m V_m/|V_m| (Sec. 3).
+// The work decomposition, staging, reductions and fixed-point sums are the direct kernel's.
+constexpr int kSepUsFloats = kRowsMax * kTileW * 2;
+
+__host__ __device__ constexpr int sep_smem_bytes(int chunk) {
+  return chunk * (kTileW + kYStride) * 8 + chunk * 8 + kWarps * kHalfRows * kTileW * 8 + kSepUsFloats * 4;
+}
+
+struct SepSmem {
+  float2 *Xs, *Ys, *Cs, *Sp, *Us;
+  __device__ __forceinline__ SepSmem(unsigned char *raw, int chunk) {
+    Xs = reinterpret_cast<float2 *>(raw);  // [chunk][kTileW]
+    Ys = Xs + chunk * kTileW;              // [chunk][kYStride]
+    Cs = Ys + chunk * kYStride;            // [chunk]
+    Sp = Cs + chunk;                       // [kWarps][kHalfRows][kTileW]
+    Us = Sp + kWarps * kHalfRows * kTileW; // [kRowsMax][kTileW] unit phasors of the sub-tile
+  }
+};
+
+// Sec. 3 coefficient of trap m in complex form: w_m' V_m/|V_m| with w_m' = w_m <|V|>/|V_m|
+// (R4: |V_m| = 0 keeps w_m and takes the unit field 1).
+__device__ __forceinline__ float2 complex_coefficient(const StepArgs &a, int m, float mean) {
+  const float2 v = field_from_sums(a, m);
+  const float am = sqrtf(v.x * v.x + v.y * v.y);
+  const float w = __ldcg(a.w_in + m);
+  if (am < 1e-30f) return make_float2(w, 0.f);
+  const float s = w * mean / (am * am);
+  return make_float2(s * v.x, s * v.y);
+}
+
+template <bool BACK, bool ADJ = false>
+__device__ __forceinline__ void stage_sep(const StepArgs &a, int m0, int n, const SubTile &st, const SepSmem &sm,
+                                          bool xy = true, float mean = 0.f) {
+  for (int i = threadIdx.x; xy && i < n * kTileW; i += kThreads) {
+    const int k = i / kTileW, col = st.x0 + (i % kTileW);
+    const bool ok = col < a.W;
+    cp_async8(sm.Xs + i, a.Xc + (ok ? (size_t)(m0 + k) * a.W + col : 0), ok);
+  }
+  for (int i = threadIdx.x; xy && i < n * kYStride; i += kThreads) {
+    const int k = i / kYStride, r = i % kYStride;
+    const bool ok = r < st.rows;
+    cp_async8(sm.Ys + i, a.Yc + (ok ? (size_t)(m0 + k) * a.H + st.y0 + r : 0), ok);
+  }
+  if (BACK)
+    for (int i = threadIdx.x; i < n; i += kThreads)
+      sm.Cs[i] = (ADJ || a.G) ? a.G[m0 + i] : complex_coefficient(a, m0 + i, mean);
+  cp_async_wait_all();
+}
+
+// S_r += Yc_m(r) (c_m Xc_m(lane)) for traps [lo, hi) of the staged chunk.
+template <int R>
+__device__ __forceinline__ void back_traps_sep(const SepSmem &sm, int lo, int hi, int lane, float2 (&S)[kRowsMax]) {
+  for (int k = lo; k < hi; k++) {
+    const float2 x = sm.Xs[k * kTileW + lane], c = sm.Cs[k];
+    const float2 b = make_float2(c.x * x.x - c.y * x.y, c.x * x.y + c.y * x.x);
+    const float4 *yq = reinterpret_cast<const float4 *>(sm.Ys + k * kYStride);
+#pragma unroll
+    for (int q = 0; q < (R + 1) / 2; q++) {
+      const float4 y2 = yq[q];
+      const float2 yy[2] = {make_float2(y2.x, y2.y), make_float2(y2.z, y2.w)};
+#pragma unroll
+      for (int j = 0; j < 2; j++) {
+        const int r = 2 * q + j;
+        if (r < R) {
+          S[r].x = fmaf(yy[j].x, b.x, fmaf(-yy[j].y, b.y, S[r].x));
+          S[r].y = fmaf(yy[j].x, b.y, fmaf(yy[j].y, b.x, S[r].y));
+        }
+      }
+    }
+  }
+}
+
+// Forward field of traps [lo, hi): conj(Xc_m(lane)) sum_r u_r conj(Yc_m(r)), summed over the
+// warp 8 traps at a time and added in fixed point (as forward_traps).  u is zero outside the
+// image, so no mask is needed.
+template <int R>
+__device__ __forceinline__ void forward_traps_sep(const SepSmem &sm, int lo, int hi, int lane,
+                                                  const float2 (&u)[kRowsMax], const StepArgs &a, int m0) {
+  for (int g = lo; g < hi; g += kGroup) {
+    float2 acc[kGroup];
+#pragma unroll
+    for (int i = 0; i < kGroup; i++) {
+      acc[i] = make_float2(0.f, 0.f);
+      const int k = g + i;
+      if (k < hi) {
+        const float4 *yq = reinterpret_cast<const float4 *>(sm.Ys + k * kYStride);
+        float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < (R + 1) / 2; q++) {
+          const float4 y2 = yq[q];
+          const float2 yy[2] = {make_float2(y2.x, y2.y), make_float2(y2.z, y2.w)};
+#pragma unroll
+          for (int j = 0; j < 2; j++) {
+            const int r = 2 * q + j;
+            if (r < R) {
+              t.x = fmaf(u[r].x, yy[j].x, fmaf(u[r].y, yy[j].y, t.x));
+              t.y = fmaf(u[r].y, yy[j].x, fmaf(-u[r].x, yy[j].y, t.y));
+            }
+          }
+        }
+        const float2 x = sm.Xs[k * kTileW + lane];
+        acc[i] = make_float2(t.x * x.x + t.y * x.y, t.y * x.x - t.x * x.y);
+      }
+    }
+    const float2 v = warp_reduce8(acc, lane);
+    const int k = g + ((lane >> 2) & 7);
+    if ((lane & 3) == 0 && k < hi) {
+      atomicAdd(a.acc_out + m0 + k, (unsigned long long)__float2ll_rn(v.x * a.fx_scale));
+      atomicAdd(a.acc_out + a.M + m0 + k, (unsigned long long)__float2ll_rn(v.y * a.fx_scale));
+    }
+  }
+}
+
+template <bool BACK, bool FWD, bool ADJ>
+__device__ __forceinline__ void process_subtile_sep(const StepArgs &a, const SubTile st, float mean, bool &prestaged,
+                                                    const SepSmem &sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mc = a.M < a.chunk ? a.M : a.chunk;
+  const int nchunks = (a.M + mc - 1) / mc;
+  const int ix = st.x0 + lane;
+  const bool col_ok = ix < a.W;
+
+  if (BACK) {
+    float2 S[kRowsMax];
+#pragma unroll
+    for (int r = 0; r < kRowsMax; r++) S[r] = make_float2(0.f, 0.f);
+    for (int ch = 0; ch < nchunks; ch++) {
+      const int m0 = ch * mc, n = min(mc, a.M - m0);
+      __syncthreads();  // earlier readers of the tables are done
+      stage_sep<true, ADJ>(a, m0, n, st, sm, !prestaged, mean);
+      prestaged = false;
+      __syncthreads();
+      const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
+      HOT_WITH_ROWS(st.rows, (back_traps_sep<R>(sm, lo, hi, lane, S)));
+    }
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      if (h * kHalfRows >= st.rows) break;
+      __syncthreads();  // Sp and the phasor rows are free
+#pragma unroll
+      for (int i = 0; i < kHalfRows; i++)
+        if (h * kHalfRows + i < st.rows) sm.Sp[(warp * kHalfRows + i) * kTileW + lane] = S[h * kHalfRows + i];
+      __syncthreads();
+      if (warp < kHalfRows && h * kHalfRows + warp < st.rows) {
+        const int r = h * kHalfRows + warp;
+        float2 s = sm.Sp[warp * kTileW + lane];
+#pragma unroll
+        for (int w = 1; w < kWarps; w++) {
+          const float2 q = sm.Sp[(w * kHalfRows + warp) * kTileW + lane];
+          s.x += q.x;
+          s.y += q.y;
+        }
+        const size_t j = (size_t)(st.y0 + r) * a.W + ix;
+        if (ADJ) {
+          if (col_ok) {
+            float sp, cp;
+            sincosf(a.phi[j], &sp, &cp);
+            a.grad[j] = (cp * s.y - sp * s.x) * a.inv_n;  // Im[(cos - i sin)(S.x + i S.y)] / N
+          }
+        } else {
+          const float ph = atan2f(s.y, s.x);
+          if (col_ok) a.phi[j] = ph;
+          if (FWD) {  // u = e^{i phi} of the stored phase (so that a resumed run is identical)
+            float2 u = make_float2(0.f, 0.f);
+            if (col_ok) sincosf(ph, &u.y, &u.x);
+            sm.Us[r * kTileW + lane] = u;
+          }
+        }
+      }
+    }
+  } else if (FWD) {
+    __syncthreads();  // earlier readers of the phasors and of the tables are done
+    for (int r = warp; r < st.rows; r += kWarps) {
+      float2 u = make_float2(0.f, 0.f);
+      if (col_ok) sincosf(a.phi[(size_t)(st.y0 + r) * a.W + ix], &u.y, &u.x);
+      sm.Us[r * kTileW + lane] = u;
+    }
+  }
+
+  if (FWD) {
+    __syncthreads();  // the phasors are complete
+    float2 u[kRowsMax];
+#pragma unroll
+    for (int r = 0; r < kRowsMax; r++) u[r] = r < st.rows ? sm.Us[r * kTileW + lane] : make_float2(0.f, 0.f);
+    for (int ch = 0; ch < nchunks; ch++) {
+      const int m0 = ch * mc, n = min(mc, a.M - m0);
+      if (!BACK || nchunks > 1) {  // with one chunk the back-projection's tables are still staged
+        if (ch) __syncthreads();
+        stage_sep<false>(a, m0, n, st, sm);
+        __syncthreads();
+      }
+      const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
+      HOT_WITH_ROWS(st.rows, (forward_traps_sep<R>(sm, lo, hi, lane, u, a, m0)));
+    }
+  }
+}
+
+template <bool BACK, bool FWD, bool ADJ = false>
+__global__ void __launch_bounds__(kThreads, 3) gsw_sep_kernel(StepArgs a) {
+  static_assert(!ADJ || (BACK && !FWD), "the adjoint is a back-projection without forward field");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SepSmem sm(smem_raw, a.chunk);
+  const int mc = a.M < a.chunk ? a.M : a.chunk;
+  const int t_begin = a.first[blockIdx.x], t_end = a.first[blockIdx.x + 1];
+
+  allow_dependents();
+  bool prestaged = false;
+  if (BACK && t_begin < t_end) {
+    stage_sep<false>(a, 0, mc, a.sub[t_begin], sm);
+    prestaged = true;
+  }
+  grid_dependency_wait();
+  if (FWD)
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
+  float mean = 0.f;
+  if (BACK && !ADJ && !a.G) {
+    mean = mean_field_amplitude(a);
+    for (int m = blockIdx.x + gridDim.x * threadIdx.x; m < a.M; m += gridDim.x * kThreads)
+      a.w_out[m] = coefficient(a, m, mean).x;
+  }
+  for (int t = t_begin; t < t_end; t++) process_subtile_sep<BACK, FWD, ADJ>(a, a.sub[t], mean, prestaged, sm);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Persistent form: all launches of a hot_gsw call (the forward field of the starting phases and
+// iterations 1..K) in one cooperative launch whose blocks are all resident, separated by a
+// grid-wide barrier instead of kernel boundaries.  The arithmetic, the schedule and the
+// fixed-point sums are those of the per-iteration kernels, so the results are the same bits.
+// A block that owns a single sub-tile and a single trap chunk keeps that sub-tile's trap tables
+// in shared memory for the whole call; only the coefficients are staged per iteration.
+
+// Grid-wide barrier with a bounded wait.  count: arrivals since the launch began (zeroed
+// before each launch; barrier j is passed when it reaches j x gridDim.x); err: set to 1 when a
+// wait runs out (after limit_ns of %globaltimer), after which every block leaves at its next
+// barrier and the host reports HOT_ETIMEOUT.
+struct GridSync {
+  unsigned int *count;
+  int *err;
+  long long limit_ns;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_acquire_s32(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Every block calls this the same number of times.  epoch (thread 0's copy) is the arrival
+// count that ends the previous barrier.  Returns false in every thread of the block if a wait
+// ran out.
+__device__ __forceinline__ bool grid_sync(const GridSync &g, unsigned int &epoch) {
+  __shared__ int ok;
+  __syncthreads();  // the block's writes and atomics of this phase are issued
+  if (threadIdx.x == 0) {
+    int good = 1;
+    __threadfence();  // ordered after the block's writes by the barrier above
+    epoch += gridDim.x;
+    atomicAdd(g.count, 1u);
+    const long long t0 = (long long)global_timer_ns();
+    while (ld_acquire_u32(g.count) < epoch) {
+      if (ld_acquire_s32(g.err)) {
+        good = 0;
+        break;
+      }
+      if ((long long)global_timer_ns() - t0 > g.limit_ns) {
+        atomicExch(g.err, 1);
+        good = 0;
+        break;
+      }
+    }
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Parameters of the persistent kernels: launch k of the sequence uses step[k % 6] (the
+// accumulators rotate over three buffers and the weights over two, as in hot_gsw).
+struct PersistArgs {
+  StepArgs step[6];
+  int iters;
+  GridSync sync;
+};
+
+constexpr int kModeAccurate = 0, kModeFast = 1, kModeSeparable = 2;
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 3 : 4)
+    gsw_persistent_kernel(const __grid_constant__ PersistArgs p) {
+  constexpr bool FAST = MODE == kModeFast;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const StepArgs &a0 = p.step[0];
+  const int mc = a0.M < a0.chunk ? a0.M : a0.chunk;
+  const int t_begin = a0.first[blockIdx.x], t_end = a0.first[blockIdx.x + 1];
+  const bool resident = t_end - t_begin == 1 && a0.M <= a0.chunk;  // tables stay in shared memory
+  unsigned int epoch = 0u;
+
+  for (int k = 0; k <= p.iters; k++) {
+    const StepArgs &a = p.step[k % 6];
+    if (k > 0 && !grid_sync(p.sync, epoch)) return;
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
+    float mean = 0.f;
+    if (k > 0) {
+      mean = mean_field_amplitude(a);
+      for (int m = blockIdx.x + gridDim.x * threadIdx.x; m < a.M; m += gridDim.x * kThreads)
+        a.w_out[m] = coefficient(a, m, mean).x;
+    }
+    for (int t = t_begin; t < t_end; t++) {
+      bool prestaged = resident && k > 0;
+      if constexpr (MODE == kModeSeparable) {
+        const SepSmem sm(smem_raw, mc);
+        if (k == 0)
+          process_subtile_sep<false, true, false>(a, a.sub[t], 0.f, prestaged, sm);
+        else
+          process_subtile_sep<true, true, false>(a, a.sub[t], mean, prestaged, sm);
+      } else {
+        const StepSmem sm(smem_raw);
+        if (k == 0)
+          process_subtile<FAST, false, true, false>(a, a.sub[t], 0.f, prestaged, sm);
+        else
+          process_subtile<FAST, true, true, false>(a, a.sub[t], mean, prestaged, sm);
+      }
+    }
+  }
+}
+
 // Per (trap, column) and (trap, row) phase parts of Eq. 2 reduced modulo one turn in FP64.
 // abc: [M][3] = a_m, b_m, c_m in turns (see the file header).  Writes turns and radians.
 // A row band (rows y_off .. y_off+H-1 of a hologram of H_total rows) takes the row parts of
 // its global rows.
 __global__ void build_tables_kernel(int W, int H, int H_total, int y_off, int M, const double *abc, float *Xt,
-                                    float *Yt, float *Xr, float *Yr) {
+                                    float *Yt, float *Xr, float *Yr, float2 *Xc, float2 *Yc) {
   const long long total = (long long)M * (W + H);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -618,12 +966,16 @@ __global__ void build_tables_kernel(int W, int H, int H_total, int y_off, int M,
     }
     t -= rint(t);  // [-1/2, 1/2] turns
     const float tf = (float)t, rf = (float)(t * 6.283185307179586476925286766559);
+    double sn = 0.0, cs = 1.0;
+    if (Xc) sincospi(2.0 * t, &sn, &cs);
     if (i < W) {
       Xt[(size_t)m * W + i] = tf;
       Xr[(size_t)m * W + i] = rf;
+      if (Xc) Xc[(size_t)m * W + i] = make_float2((float)cs, (float)sn);
     } else {
       Yt[(size_t)m * H + (i - W)] = tf;
       Yr[(size_t)m * H + (i - W)] = rf;
+      if (Yc) Yc[(size_t)m * H + (i - W)] = make_float2((float)cs, (float)sn);
     }
   }
 }

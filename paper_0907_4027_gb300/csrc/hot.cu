@@ -76,6 +76,7 @@ struct hot_ctx {
   int M = 0;
   double *abc = nullptr;                                       // [M][3]
   float *Xt = nullptr, *Yt = nullptr, *Xr = nullptr, *Yr = nullptr;  // tables
+  float2 *Xc = nullptr, *Yc = nullptr;                               // complex tables (separable)
   float *w = nullptr;                                          // [2][M] weights (home: w[0])
   unsigned long long *acc = nullptr;                           // [3][2][M] fixed-point field sums
   long long *Vsum = nullptr;                                   // [2][M] sums of the last forward
@@ -100,6 +101,10 @@ struct hot_ctx {
   };
   bool use_graphs = true;
   cudaStream_t cap = nullptr;  // capture stream (capture is not allowed on the legacy stream)
+  // persistent form (one cooperative launch per hot_gsw): grid barrier state [count, gen, err]
+  bool persistent = false;
+  double wait_limit_s = 2.0;
+  unsigned int *sync = nullptr;
   std::vector<Graph> graphs;
 };
 
@@ -129,6 +134,8 @@ void free_traps(hot_ctx *c) {
   dfree(c->Yt);
   dfree(c->Xr);
   dfree(c->Yr);
+  dfree(c->Xc);
+  dfree(c->Yc);
   dfree(c->w);
   dfree(c->acc);
   dfree(c->Vsum);
@@ -199,9 +206,8 @@ void launch(hot_ctx *c, void (*kernel)(KArgs...), int grid, int block, int smem,
 
 // Launch k of a hot_gsw sequence (k = 0: forward field of the starting phases; k >= 1:
 // iteration k).  Accumulators rotate over three buffers, weights over two.
-template <bool FAST, bool BACK, bool FWD, bool ADJ = false>
-int launch_tile(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const float2 *G = nullptr,
-                float *grad = nullptr) {
+hot::StepArgs make_step_args(const hot_ctx *c, int k, const float *phi, const float2 *G, float *grad) {
+  const bool fast = c->precision == HOT_PREC_FAST;
   hot::StepArgs a;
   a.W = c->W;
   a.H = c->H;
@@ -209,8 +215,10 @@ int launch_tile(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const f
   a.chunk = c->tile_chunk;
   a.sub = c->sub;
   a.first = c->first;
-  a.X = FAST ? c->Xr : c->Xt;
-  a.Y = FAST ? c->Yr : c->Yt;
+  a.X = fast ? c->Xr : c->Xt;
+  a.Y = fast ? c->Yr : c->Yt;
+  a.Xc = c->Xc;
+  a.Yc = c->Yc;
   a.phi = c->phi;
   const size_t M2 = 2 * (size_t)c->M;
   a.acc_in = c->acc + M2 * ((k + 2) % 3);
@@ -220,15 +228,44 @@ int launch_tile(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const f
   a.w_out = c->w + (size_t)c->M * (k & 1);
   a.fx_scale = ldexpf(1.0f, c->fx_shift);
   a.inv_fx_n = (float)(1.0 / (n_total(c) * ldexp(1.0, c->fx_shift)));
-  a.angle_units = FAST ? 1.0f : 0.15915494309189535f;
+  a.angle_units = fast ? 1.0f : 0.15915494309189535f;
   if (phi) a.phi = const_cast<float *>(phi);  // read only: forward field or adjoint of given phases
   a.G = G;
   a.grad = grad;
   a.inv_n = (float)(1.0 / (n_total(c)));
+  return a;
+}
+
+// Traps staged at once by the separable kernel (its shared memory is sized by it).
+int sep_chunk(const hot_ctx *c) { return std::max(1, std::min(c->M, c->tile_chunk)); }
+
+template <bool FAST, bool BACK, bool FWD, bool ADJ = false>
+int launch_tile(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const float2 *G = nullptr,
+                float *grad = nullptr) {
+  const hot::StepArgs a = make_step_args(c, k, phi, G, grad);
   const int smem = hot::step_smem_bytes(c->M, BACK);
   Probe p(c, BACK && FWD ? HOT_KERNEL_STEP : FWD ? HOT_KERNEL_FORWARD : HOT_KERNEL_OTHER);
   launch(c, hot::gsw_step_kernel<FAST, BACK, FWD, ADJ>, c->grid, hot::kThreads, smem, pdl, a);
   return check_launch(c, "gsw_step_kernel");
+}
+
+template <bool BACK, bool FWD, bool ADJ = false>
+int launch_sep(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const float2 *G = nullptr,
+               float *grad = nullptr) {
+  hot::StepArgs a = make_step_args(c, k, phi, G, grad);
+  a.chunk = sep_chunk(c);
+  Probe p(c, BACK && FWD ? HOT_KERNEL_STEP : FWD ? HOT_KERNEL_FORWARD : HOT_KERNEL_OTHER);
+  launch(c, hot::gsw_sep_kernel<BACK, FWD, ADJ>, c->grid, hot::kThreads, hot::sep_smem_bytes(a.chunk), pdl, a);
+  return check_launch(c, "gsw_sep_kernel");
+}
+
+// The step kernel of the context's mode (accurate / fast direct evaluation, or separable).
+template <bool BACK, bool FWD, bool ADJ = false>
+int launch_mode(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const float2 *G = nullptr,
+                float *grad = nullptr) {
+  if (c->precision == HOT_PREC_SEPARABLE) return launch_sep<BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
+  if (c->precision == HOT_PREC_FAST) return launch_tile<true, BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
+  return launch_tile<false, BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
 }
 
 // Raises the dynamic shared-memory limit of every step-kernel variant to what M needs.
@@ -242,6 +279,14 @@ int set_step_smem(int M) {
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd));
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
+  const int sep = hot::sep_smem_bytes(hot::kChunk);
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_sep_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sep));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_sep_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sep));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_sep_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sep));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_sep_kernel<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sep));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_persistent_kernel<hot::kModeAccurate>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_persistent_kernel<hot::kModeFast>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_persistent_kernel<hot::kModeSeparable>, cudaFuncAttributeMaxDynamicSharedMemorySize, sep));
   return HOT_OK;
 }
 
@@ -249,12 +294,31 @@ int set_step_smem(int M) {
 // tile_bps); the W/32 x H row segments are dealt out in equal contiguous runs, cut into
 // sub-tiles of <= tile_rows rows.
 int build_schedule(hot_ctx *c) {
+  drop_graphs(c);  // graphs hold the old schedule
   int rc = set_step_smem(c->M);
   if (rc != HOT_OK) return rc;
   int sms = 0, per_sm = 0;
   HOT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
-  HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_step_kernel<true, true, true>,
-                                                         hot::kThreads, hot::step_smem_bytes(c->M, true)));
+  // the per-iteration and the persistent kernels share the schedule (so that they compute the
+  // same bits): as many blocks per SM as both can keep resident
+  int per_sm_p = 0;
+  if (c->precision == HOT_PREC_SEPARABLE) {
+    const int smem = hot::sep_smem_bytes(sep_chunk(c));
+    HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_sep_kernel<true, true>, hot::kThreads, smem));
+    HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_p, hot::gsw_persistent_kernel<hot::kModeSeparable>,
+                                                           hot::kThreads, smem));
+  } else {
+    const int smem = hot::step_smem_bytes(c->M, true);
+    HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_step_kernel<true, true, true>,
+                                                           hot::kThreads, smem));
+    HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_p, hot::gsw_persistent_kernel<hot::kModeFast>,
+                                                           hot::kThreads, smem));
+    int per_sm_a = 0;
+    HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, hot::gsw_persistent_kernel<hot::kModeAccurate>,
+                                                           hot::kThreads, smem));
+    per_sm_p = std::min(per_sm_p, per_sm_a);
+  }
+  per_sm = std::min(per_sm, per_sm_p);
   if (per_sm < 1) per_sm = 1;
   c->sched_bps_max = per_sm;
   if (c->tile_bps > 0 && c->tile_bps < per_sm) per_sm = c->tile_bps;
@@ -299,10 +363,9 @@ int build_schedule(hot_ctx *c) {
 // One step-kernel launch (launch k of the sequence): weight update + back-projection and/or
 // forward field.
 int launch_step(hot_ctx *c, bool back, bool fwd, bool pdl, int k) {
-  const bool fast = c->precision == HOT_PREC_FAST;
-  if (back && fwd) return fast ? launch_tile<true, true, true>(c, pdl, k) : launch_tile<false, true, true>(c, pdl, k);
-  if (back) return fast ? launch_tile<true, true, false>(c, pdl, k) : launch_tile<false, true, false>(c, pdl, k);
-  return fast ? launch_tile<true, false, true>(c, pdl, k) : launch_tile<false, false, true>(c, pdl, k);
+  if (back && fwd) return launch_mode<true, true>(c, pdl, k);
+  if (back) return launch_mode<true, false>(c, pdl, k);
+  return launch_mode<false, true>(c, pdl, k);
 }
 
 // After the last launch (k = iters): Eq. 4 metrics, field sums, weights home, accumulators cleared.
@@ -332,11 +395,67 @@ int launch_build_tables(hot_ctx *c) {
   const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
   Probe p(c, HOT_KERNEL_OTHER);
   hot::build_tables_kernel<<<blocks, 256, 0, c->st>>>(c->W, c->H, c->H_total, c->y_off, c->M, c->abc, c->Xt, c->Yt,
-                                                      c->Xr, c->Yr);
+                                                      c->Xr, c->Yr, c->Xc, c->Yc);
   return check_launch(c, "build_tables_kernel");
 }
 
+// The whole sequence of enqueue_gsw's step launches as one cooperative launch (all blocks
+// resident; the grid is one wave by construction of the schedule).
+int launch_persistent(hot_ctx *c, int iters) {
+  hot::PersistArgs p;
+  for (int j = 0; j < 6; j++) {
+    p.step[j] = make_step_args(c, j, nullptr, nullptr, nullptr);
+    if (c->precision == HOT_PREC_SEPARABLE) p.step[j].chunk = sep_chunk(c);
+  }
+  p.iters = iters;
+  p.sync.count = c->sync;
+  p.sync.err = reinterpret_cast<int *>(c->sync + 2);
+  p.sync.limit_ns = (long long)(c->wait_limit_s * 1e9);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c->grid);
+  cfg.blockDim = dim3(hot::kThreads);
+  cfg.stream = c->st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  HOT_CUDA(cudaMemsetAsync(c->sync, 0, sizeof(unsigned int), c->st));  // arrival count
+  Probe probe(c, HOT_KERNEL_STEP);
+  if (c->precision == HOT_PREC_SEPARABLE) {
+    cfg.dynamicSmemBytes = hot::sep_smem_bytes(sep_chunk(c));
+    cudaLaunchKernelEx(&cfg, hot::gsw_persistent_kernel<hot::kModeSeparable>, p);
+  } else if (c->precision == HOT_PREC_FAST) {
+    cfg.dynamicSmemBytes = hot::step_smem_bytes(c->M, true);
+    cudaLaunchKernelEx(&cfg, hot::gsw_persistent_kernel<hot::kModeFast>, p);
+  } else {
+    cfg.dynamicSmemBytes = hot::step_smem_bytes(c->M, true);
+    cudaLaunchKernelEx(&cfg, hot::gsw_persistent_kernel<hot::kModeAccurate>, p);
+  }
+  return check_launch(c, "gsw_persistent_kernel");
+}
+
+// Reads the barrier's error flag (synchronises): after a wait ran out, the accumulators and the
+// barrier are reset and HOT_ETIMEOUT is returned; the phases are then undefined.
+int check_wait_error(hot_ctx *c, const char *who) {
+  unsigned int st[3] = {0, 0, 0};
+  HOT_CUDA(cudaMemcpyAsync(st, c->sync, sizeof st, cudaMemcpyDeviceToHost, c->st));
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  if (!st[2]) return HOT_OK;
+  HOT_CUDA(cudaMemsetAsync(c->sync, 0, sizeof st, c->st));
+  if (c->M) HOT_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * 6 * c->M, c->st));
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  c->have_fields = false;
+  return fail(HOT_ETIMEOUT, "%s: a grid barrier wait of the persistent kernel ran out (limit %.3g s)", who,
+              c->wait_limit_s);
+}
+
 int enqueue_gsw(hot_ctx *c, int iters) {
+  if (c->persistent) {
+    int rc = launch_persistent(c, iters);
+    if (rc == HOT_OK) rc = launch_finalize(c, false, iters);
+    return rc;
+  }
   const bool pdl = !c->profiling;
   int rc = launch_step(c, false, true, false, 0);       // V^1 = F(phi^0)
   for (int k = 1; k <= iters && rc == HOT_OK; k++)
@@ -414,6 +533,9 @@ int hot_create(hot_ctx **out, int width, int height, double pitch_m, double wave
   const size_t N = (size_t)width * height;
   if (rc == HOT_OK) rc = dalloc(&c->phi, N);
   if (rc == HOT_OK) rc = dalloc(&c->metrics, 2);
+  if (rc == HOT_OK) rc = dalloc(&c->sync, 3);
+  if (rc == HOT_OK && cudaMemsetAsync(c->sync, 0, 3 * sizeof(unsigned int), c->st) != cudaSuccess)
+    rc = fail(HOT_ECUDA, "hot_create: clearing the barrier state failed");
   if (rc == HOT_OK) {
     e = cudaMemsetAsync(c->phi, 0, N * sizeof(float), c->st);
     if (e != cudaSuccess) rc = fail(HOT_ECUDA, "hot_create: %s", cudaGetErrorString(e));
@@ -440,6 +562,7 @@ void hot_destroy(hot_ctx *c) {
   dfree(c->first);
   dfree(c->metrics);
   dfree(c->u8);
+  dfree(c->sync);
   delete c;
 }
 
@@ -485,6 +608,8 @@ int hot_set_traps(hot_ctx *c, int M, const double *xyz_m, const double *w0) {
     if (rc == HOT_OK) rc = dalloc(&c->Xr, (size_t)M * c->W);
     if (rc == HOT_OK) rc = dalloc(&c->Yt, (size_t)M * c->H);
     if (rc == HOT_OK) rc = dalloc(&c->Yr, (size_t)M * c->H);
+    if (rc == HOT_OK) rc = dalloc(&c->Xc, (size_t)M * c->W);
+    if (rc == HOT_OK) rc = dalloc(&c->Yc, (size_t)M * c->H);
     if (rc == HOT_OK) rc = dalloc(&c->w, 2 * (size_t)M);
     if (rc == HOT_OK) rc = dalloc(&c->acc, 6 * (size_t)M);
     if (rc == HOT_OK) rc = dalloc(&c->Vsum, 2 * (size_t)M);
@@ -536,9 +661,12 @@ int hot_set_phase(hot_ctx *c, const float *phi, int on_device) {
 
 int hot_set_precision(hot_ctx *c, int precision) {
   if (!c) return fail(HOT_EINVAL, "hot_set_precision: NULL context");
-  if (precision != HOT_PREC_ACCURATE && precision != HOT_PREC_FAST)
+  if (precision != HOT_PREC_ACCURATE && precision != HOT_PREC_FAST && precision != HOT_PREC_SEPARABLE)
     return fail(HOT_EINVAL, "hot_set_precision: unknown mode %d", precision);
+  const bool resched = (precision == HOT_PREC_SEPARABLE) != (c->precision == HOT_PREC_SEPARABLE);
+  if (resched) HOT_CUDA(cudaStreamSynchronize(c->st));
   c->precision = precision;
+  if (resched && c->M) return build_schedule(c);  // the two kernels' occupancies differ
   return HOT_OK;
 }
 
@@ -546,10 +674,14 @@ int hot_gsw(hot_ctx *c, int iters, double *eff_out, double *unif_out) {
   if (!c) return fail(HOT_EINVAL, "hot_gsw: NULL context");
   if (iters < 0) return fail(HOT_EINVAL, "hot_gsw: iters = %d < 0", iters);
   if (!c->M) return fail(HOT_ESTATE, "hot_gsw: no traps set");
-  const int rc = (c->use_graphs && !c->profiling) ? launch_gsw_graph(c, iters) : enqueue_gsw(c, iters);
+  const int rc = (c->use_graphs && !c->profiling && !c->persistent) ? launch_gsw_graph(c, iters) : enqueue_gsw(c, iters);
   if (rc != HOT_OK) return rc;
   c->have_fields = true;
   if (eff_out || unif_out) {
+    if (c->persistent) {
+      const int rc2 = check_wait_error(c, "hot_gsw");
+      if (rc2 != HOT_OK) return rc2;
+    }
     float m[2];
     HOT_CUDA(cudaMemcpyAsync(m, c->metrics, sizeof m, cudaMemcpyDeviceToHost, c->st));
     HOT_CUDA(cudaStreamSynchronize(c->st));
@@ -593,6 +725,8 @@ int hot_get_fields(hot_ctx *c, double *V, double *w) {
   if (!c) return fail(HOT_EINVAL, "hot_get_fields: NULL context");
   if (!c->M) return fail(HOT_ESTATE, "hot_get_fields: no traps set");
   if (V && !c->have_fields) return fail(HOT_ESTATE, "hot_get_fields: no forward evaluation since the last change");
+  const int rc = check_wait_error(c, "hot_get_fields");
+  if (rc != HOT_OK) return rc;
   std::vector<long long> vs(V ? 2 * c->M : 0);
   std::vector<float> wf(w ? c->M : 0);
   if (V) HOT_CUDA(cudaMemcpyAsync(vs.data(), c->Vsum, sizeof(long long) * 2 * c->M, cudaMemcpyDeviceToHost, c->st));
@@ -610,8 +744,7 @@ int hot_get_fields(hot_ctx *c, double *V, double *w) {
 int hot_field(hot_ctx *c, const float *phi, float *V) {
   if (!c || !phi || !V) return fail(HOT_EINVAL, "hot_field: NULL argument");
   if (!c->M) return fail(HOT_ESTATE, "hot_field: no traps set");
-  const bool fast = c->precision == HOT_PREC_FAST;
-  int rc = fast ? launch_tile<true, false, true>(c, false, 0, phi) : launch_tile<false, false, true>(c, false, 0, phi);
+  int rc = launch_mode<false, true>(c, false, 0, phi);
   if (rc == HOT_OK) rc = launch_finalize(c, false, 0);  // w stays in w[0]; accumulators cleared
   if (rc != HOT_OK) return rc;
   const double inv = 1.0 / (n_total(c) * ldexp(1.0, c->fx_shift));
@@ -635,8 +768,7 @@ int hot_superposition(hot_ctx *c, const double *coef) {
   cudaError_t e = cudaMemcpyAsync(d, cf.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice, c->st);
   if (e != cudaSuccess) rc = fail(HOT_ECUDA, "hot_superposition: %s", cudaGetErrorString(e));
   if (rc == HOT_OK)
-    rc = c->precision == HOT_PREC_FAST ? launch_tile<true, true, false>(c, false, 0, nullptr, d)
-                                       : launch_tile<false, true, false>(c, false, 0, nullptr, d);
+    rc = launch_mode<true, false>(c, false, 0, nullptr, d);
   if (rc == HOT_OK) {
     e = cudaStreamSynchronize(c->st);  // the coefficients are freed below
     if (e != cudaSuccess) rc = fail(HOT_ECUDA, "hot_superposition: %s", cudaGetErrorString(e));
@@ -650,8 +782,7 @@ int hot_field_adjoint(hot_ctx *c, const float *phi, const float *G, float *grad)
   if (!c || !phi || !G || !grad) return fail(HOT_EINVAL, "hot_field_adjoint: NULL argument");
   if (!c->M) return fail(HOT_ESTATE, "hot_field_adjoint: no traps set");
   const float2 *g = reinterpret_cast<const float2 *>(G);
-  return c->precision == HOT_PREC_FAST ? launch_tile<true, true, false, true>(c, false, 0, phi, g, grad)
-                                       : launch_tile<false, true, false, true>(c, false, 0, phi, g, grad);
+  return launch_mode<true, false, true>(c, false, 0, phi, g, grad);
 }
 
 int hot_set_band(hot_ctx *c, int total_height, int y0) {
@@ -717,6 +848,8 @@ int hot_sharded_end(hot_ctx *c, int iters, double *eff_out, double *unif_out) {
 int hot_get_metrics(hot_ctx *c, double *eff_out, double *unif_out) {
   if (!c) return fail(HOT_EINVAL, "hot_get_metrics: NULL context");
   if (!c->M || !c->have_fields) return fail(HOT_ESTATE, "hot_get_metrics: no forward evaluation since the last change");
+  const int rc = check_wait_error(c, "hot_get_metrics");
+  if (rc != HOT_OK) return rc;
   float m[2];
   HOT_CUDA(cudaMemcpyAsync(m, c->metrics, sizeof m, cudaMemcpyDeviceToHost, c->st));
   HOT_CUDA(cudaStreamSynchronize(c->st));
@@ -728,6 +861,19 @@ int hot_get_metrics(hot_ctx *c, double *eff_out, double *unif_out) {
 int hot_sync(hot_ctx *c) {
   if (!c) return fail(HOT_EINVAL, "hot_sync: NULL context");
   HOT_CUDA(cudaStreamSynchronize(c->st));
+  return check_wait_error(c, "hot_sync");
+}
+
+int hot_use_persistent(hot_ctx *c, int enable) {
+  if (!c) return fail(HOT_EINVAL, "hot_use_persistent: NULL context");
+  c->persistent = enable != 0;
+  return HOT_OK;
+}
+
+int hot_set_wait_limit(hot_ctx *c, double seconds) {
+  if (!c) return fail(HOT_EINVAL, "hot_set_wait_limit: NULL context");
+  if (!(seconds >= 0.0) || seconds > 60.0) return fail(HOT_EINVAL, "hot_set_wait_limit: %g s not in [0, 60]", seconds);
+  c->wait_limit_s = seconds;
   return HOT_OK;
 }
 
@@ -1194,6 +1340,8 @@ int hot_batch_create(hot_batch **out, int count, hot_ctx *const *ctxs, void *cud
     if (!ctxs[i]->M) return fail(HOT_ESTATE, "hot_batch_create: context %d has no traps", i);
     if (ctxs[i]->precision != ctxs[0]->precision)
       return fail(HOT_EINVAL, "hot_batch_create: contexts differ in precision mode");
+    if (ctxs[i]->precision == HOT_PREC_SEPARABLE)
+      return fail(HOT_EINVAL, "hot_batch_create: the separable mode is not batched");
     if (ctxs[i]->dev != ctxs[0]->dev) return fail(HOT_EINVAL, "hot_batch_create: contexts on different devices");
     for (int j = 0; j < i; j++)
       if (ctxs[j] == ctxs[i]) return fail(HOT_EINVAL, "hot_batch_create: context %d given twice", i);
@@ -1361,15 +1509,17 @@ __global__ void __launch_bounds__(1024) sfu_rate_kernel(float *out, long long *c
   for (int it = 0; it < iters; it++) {
 #pragma unroll
     for (int i = 0; i < 8; i++) {
-      x[i] += step;  // a new argument every iteration
+      if (OP != 3) x[i] += step;  // a new argument every iteration
       if (OP == 0) {
         acc[i] = fmaf(hot::sin_approx(x[i]), hot::cos_approx(x[i]), acc[i]);
       } else if (OP == 1) {
         acc[i] += hot::sin_approx(x[i]);
-      } else {
+      } else if (OP == 2) {
         float y;
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x[i] * 0.001f));
         acc[i] += y;
+      } else {
+        acc[i] = fmaf(acc[i], 0.999f, x[i]);  // FP32 FMA pipe: 8 independent chains
       }
     }
   }
@@ -1385,7 +1535,7 @@ __global__ void __launch_bounds__(1024) sfu_rate_kernel(float *out, long long *c
 }  // namespace
 
 extern "C" int hot_sfu_rate(int op, double *per_clk_per_sm, int *sms) {
-  if (!per_clk_per_sm || op < 0 || op > 2) return fail(HOT_EINVAL, "hot_sfu_rate: invalid argument");
+  if (!per_clk_per_sm || op < 0 || op > 3) return fail(HOT_EINVAL, "hot_sfu_rate: invalid argument");
   int dev = 0, n = 0;
   HOT_CUDA(cudaGetDevice(&dev));
   HOT_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
@@ -1398,7 +1548,8 @@ extern "C" int hot_sfu_rate(int op, double *per_clk_per_sm, int *sms) {
   for (int rep = 0; rc == HOT_OK && rep < 2; rep++) {  // the first run warms up
     if (op == 0) sfu_rate_kernel<0><<<n, threads>>>(out, cyc, iters, 1e-4f);
     else if (op == 1) sfu_rate_kernel<1><<<n, threads>>>(out, cyc, iters, 1e-4f);
-    else sfu_rate_kernel<2><<<n, threads>>>(out, cyc, iters, 1e-4f);
+    else if (op == 2) sfu_rate_kernel<2><<<n, threads>>>(out, cyc, iters, 1e-4f);
+    else sfu_rate_kernel<3><<<n, threads>>>(out, cyc, iters, 1e-4f);
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, sizeof(long long) * n, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) rc = fail(HOT_ECUDA, "hot_sfu_rate: %s", cudaGetErrorString(e));
@@ -1572,7 +1723,7 @@ extern "C" int hot_field_noalloc(int width, int height, double pitch_m, double w
   HOT_CUDA(cudaGetLastError());
   const long long total = (long long)M * (width + height);
   const int tb = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-  hot::build_tables_kernel<<<tb, 256, 0, st>>>(width, height, height, 0, M, abc, Xt, Yt, Xr, Yr);
+  hot::build_tables_kernel<<<tb, 256, 0, st>>>(width, height, height, 0, M, abc, Xt, Yt, Xr, Yr, nullptr, nullptr);
   HOT_CUDA(cudaGetLastError());
 
   int bits = 0;

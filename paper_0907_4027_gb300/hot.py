@@ -22,7 +22,8 @@ if not os.path.exists(_LIB_PATH):
 lib = ctypes.CDLL(_LIB_PATH)
 
 HOT_OK, HOT_EINVAL, HOT_ENOMEM, HOT_ECUDA, HOT_ETIMEOUT, HOT_ESTATE = 0, -1, -2, -3, -4, -5
-HOT_PREC_ACCURATE, HOT_PREC_FAST = 0, 1
+HOT_PREC_ACCURATE, HOT_PREC_FAST, HOT_PREC_SEPARABLE = 0, 1, 2
+PRECISIONS = {"accurate": HOT_PREC_ACCURATE, "fast": HOT_PREC_FAST, "separable": HOT_PREC_SEPARABLE}
 HOT_FMT_F32, HOT_FMT_U8 = 0, 1
 HOT_MAX_TRAPS = 4096
 _STATUS = {0: "HOT_OK", -1: "HOT_EINVAL", -2: "HOT_ENOMEM", -3: "HOT_ECUDA", -4: "HOT_ETIMEOUT",
@@ -64,6 +65,8 @@ SIGNATURES = {
     "hot_field_adjoint": (_c_int, [_vp, _vp, _vp, _vp]),
     "hot_kernel_launches": (ctypes.c_longlong, [_vp]),
     "hot_use_graphs": (_c_int, [_vp, _c_int]),
+    "hot_use_persistent": (_c_int, [_vp, _c_int]),
+    "hot_set_wait_limit": (_c_int, [_vp, _c_double]),
     "hot_profile": (_c_int, [_vp, _c_int]),
     "hot_profile_read": (_c_int, [_vp, _vp, _vp]),
     "hot_destroy": (None, [_vp]),
@@ -139,7 +142,7 @@ def hot_set_phase(ctx: int, phi) -> None:
 
 def hot_set_precision(ctx: int, precision) -> None:
     if isinstance(precision, str):
-        precision = {"accurate": HOT_PREC_ACCURATE, "fast": HOT_PREC_FAST}[precision]
+        precision = PRECISIONS[precision]
     _ok(lib.hot_set_precision(_vp(ctx), int(precision)), "hot_set_precision")
 
 
@@ -335,6 +338,14 @@ def hot_use_graphs(ctx: int, enable: bool) -> None:
     _ok(lib.hot_use_graphs(_vp(ctx), int(bool(enable))), "hot_use_graphs")
 
 
+def hot_use_persistent(ctx: int, enable: bool) -> None:
+    _ok(lib.hot_use_persistent(_vp(ctx), int(bool(enable))), "hot_use_persistent")
+
+
+def hot_set_wait_limit(ctx: int, seconds: float) -> None:
+    _ok(lib.hot_set_wait_limit(_vp(ctx), float(seconds)), "hot_set_wait_limit")
+
+
 def hot_profile(ctx: int, enable: bool) -> None:
     _ok(lib.hot_profile(_vp(ctx), int(bool(enable))), "hot_profile")
 
@@ -352,8 +363,8 @@ def hot_destroy(ctx: int) -> None:
 
 
 def hot_sfu_rate(op: int = 0):
-    """(SFU lane results per clock per SM, SM count) for op 0 = sin+cos of one argument,
-    1 = sin alone, 2 = ex2 (measured on the current device)."""
+    """(lane results per clock per SM, SM count) for op 0 = sin+cos of one argument,
+    1 = sin alone, 2 = ex2, 3 = FP32 FMA (measured on the current device)."""
     r, n = ctypes.c_double(), _c_int()
     _ok(lib.hot_sfu_rate(int(op), ctypes.byref(r), ctypes.byref(n)), "hot_sfu_rate")
     return r.value, n.value
@@ -368,7 +379,7 @@ def hot_field_noalloc(width: int, height: int, pitch_m: float, wavelength_m: flo
     memory); xyz_dev (M, 3) float64, phi_dev (N,) float32, V_dev (2M,) float64 output,
     eu_dev (2,) float64 output or None.  Queued on cuda_stream."""
     if isinstance(precision, str):
-        precision = {"accurate": HOT_PREC_ACCURATE, "fast": HOT_PREC_FAST}[precision]
+        precision = PRECISIONS[precision]
     M = int(xyz_dev.numel() // 3)
     _ok(lib.hot_field_noalloc(int(width), int(height), float(pitch_m), float(wavelength_m), float(focal_m), M,
                               _vp(xyz_dev.data_ptr()), _vp(phi_dev.data_ptr()), int(precision),
@@ -443,6 +454,12 @@ class Hologram:
 
     def set_tiling(self, rows: int = 0, blocks_per_sm: int = 0, chunk: int = 0):
         hot_set_tiling(self.ctx, rows, blocks_per_sm, chunk)
+
+    def use_persistent(self, enable: bool = True):
+        hot_use_persistent(self.ctx, enable)
+
+    def set_wait_limit(self, seconds: float):
+        hot_set_wait_limit(self.ctx, seconds)
 
     def set_band(self, total_height: int, y0: int):
         """This context holds rows y0 .. y0+H-1 of a W x total_height hologram."""

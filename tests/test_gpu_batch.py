@@ -184,3 +184,10 @@ def test_batch_autotune_keeps_state(hot):
             h.close()
     for w, (V, wt, eu) in zip(ws, got):
         check_against_oracle(w, V, wt, eu)
+
+
+def test_separable_mode_is_not_batched(hot):
+    w = wl.random_case(64, 32, 5, seed=1, precision="separable")
+    with hot.Hologram.from_workload(w) as h:
+        with pytest.raises(hot.HotError, match="HOT_EINVAL"):
+            hot.Batch([h]).close()

@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 REL_V = 1e-4
 ABS_EU = 1e-3
-TOL_S = {"accurate": 2e-6, "fast": 2e-5}
+TOL_S = {"accurate": 2e-6, "fast": 2e-5, "separable": 4e-6}
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
@@ -60,7 +60,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("precision", ["accurate", "fast"])
+@pytest.mark.parametrize("precision", ["accurate", "fast", "separable"])
 @pytest.mark.parametrize("W,H,M", CASES)
 def test_one_iteration_matches_oracle(hot, W, H, M, precision):
     w = wl.random_case(W, H, M, seed=W + H + M, precision=precision)
@@ -104,10 +104,11 @@ def test_degenerate_inputs(hot):
     assert rel_err(V, r["V"]) < REL_V and abs(e - r["e"]) < ABS_EU and abs(u - r["u"]) < ABS_EU
 
 
-@pytest.mark.parametrize("precision", ["accurate", "fast"])
+@pytest.mark.parametrize("precision", ["accurate", "fast", "separable"])
 def test_resume_graphs_and_determinism(hot, precision):
-    """Two calls (3 + 2 iterations) equal one call of 5, bit for bit; replaying the captured
-    CUDA graph equals launching the kernels one by one; a second run repeats the first."""
+    """Two calls (3 + 2 iterations) equal one call of 5, bit for bit; the persistent kernel
+    (one cooperative launch), the per-iteration kernels launched one by one and their CUDA
+    graph replay give the same bits; a second run repeats the first."""
     w = wl.random_case(70, 45, 20, seed=5, precision=precision)
     with make(hot, w) as a, make(hot, w) as b, make(hot, w) as c, make(hot, w) as d:
         a.gsw(5)
@@ -115,6 +116,7 @@ def test_resume_graphs_and_determinism(hot, precision):
         b.gsw(2)
         c.use_graphs(False)
         c.gsw(5)
+        d.use_persistent(True)
         d.gsw(5)
         d.set_phase(w.phi0)
         d.set_weights(np.ones(w.M))
@@ -159,10 +161,14 @@ def quantized_agreement(gpu_u8, ophi, S, eps_S):
     return int(diff.sum()), int((diff & ~excused).sum()), int(excused.sum())
 
 
-@pytest.mark.parametrize("name", ["grid16_256", "rand100_512"])
-def test_full_workload_matches_oracle(hot, name):
-    """grid16_256 (accurate, 10 iterations) and rand100_512 (fast, 30 iterations, 8-bit)."""
+@pytest.mark.parametrize("name,precision", [("grid16_256", None), ("rand100_512", None),
+                                            ("rand100_512", "separable")])
+def test_full_workload_matches_oracle(hot, name, precision):
+    """grid16_256 (accurate, 10 iterations) and rand100_512 (fast, 30 iterations, 8-bit), and
+    rand100_512 in the separable mode."""
     w = wl.NAMED[name]()
+    if precision:
+        w.precision = precision
     K = w.iters
     with make(hot, w) as h:
         e0, u0 = h.gsw(0)
@@ -218,7 +224,7 @@ def test_rand1000_1920_metrics_and_trap_subset(hot):
 
 # ------------------------------------------------------------------ superposition (SR, Eq. 3)
 
-@pytest.mark.parametrize("precision", ["accurate", "fast"])
+@pytest.mark.parametrize("precision", ["accurate", "fast", "separable"])
 def test_superposition_matches_oracle(hot, precision):
     """Sec. 4 back-propagation with explicit coefficients: random complex c_m, and the SR
     hologram of Eq. 3 (c_m = e^{i theta_m}) on the 9 x 9 grid of Sec. 5 followed by GSW."""
@@ -264,3 +270,42 @@ def test_paper_grid_at_20hz_budget_matches_oracle(hot, n):
     assert abs(e_sr - oe_sr) < ABS_EU and abs(u_sr - ou_sr) < ABS_EU
     assert abs(e - r["e"]) < ABS_EU and abs(u - r["u"]) < ABS_EU, (e, r["e"], u, r["u"])
     assert e > 0.8  # Sec. 5: the efficiency stays high at the 20 Hz budget
+
+
+@pytest.mark.parametrize("precision", ["fast", "separable"])
+@pytest.mark.parametrize("W,H,M", [(600, 300, 300), (64, 16, 1)])
+def test_persistent_equals_per_iteration_launches(hot, W, H, M, precision):
+    """Several sub-tiles per block and several trap chunks (600 x 300, M = 300), and a block
+    per sub-tile with resident tables (64 x 16): the persistent kernel gives the bits of the
+    per-iteration kernels."""
+    w = wl.random_case(W, H, M, seed=W + M, precision=precision)
+    out = []
+    for persistent in (True, False):
+        with make(hot, w) as h:
+            h.use_persistent(persistent)
+            eu = h.gsw(4)
+            out.append((h.phase("f32"), h.fields(), eu))
+    (pa, (Va, wa), eua), (pb, (Vb, wb), eub) = out
+    assert np.array_equal(pa, pb) and np.array_equal(Va, Vb) and np.array_equal(wa, wb) and eua == eub
+
+
+def test_barrier_wait_limit_reports_timeout_and_recovers(hot):
+    """A zero wait limit makes the grid barrier's waits run out: the call reports HOT_ETIMEOUT
+    (no hang, no fault), and the context computes correctly again afterwards."""
+    w = wl.random_case(128, 64, 9, seed=6, precision="fast")
+    with make(hot, w) as h:
+        h.use_persistent(True)
+        h.set_wait_limit(0.0)
+        with pytest.raises(hot.HotError, match="HOT_ETIMEOUT"):
+            h.gsw(5)
+        h.set_wait_limit(2.0)
+        h.set_phase(w.phi0)
+        h.set_weights(np.ones(w.M))
+        e, u = h.gsw(2)
+        V, _ = h.fields()
+    r = oracle.gsw(w.geom, w.xyz, 2, w.phi0)
+    assert abs(e - r["e"]) < ABS_EU and abs(u - r["u"]) < ABS_EU
+    for bad in (-1.0, 61.0):
+        with make(hot, w) as h:
+            with pytest.raises(hot.HotError, match="HOT_EINVAL"):
+                h.set_wait_limit(bad)

@@ -57,7 +57,7 @@ def emulate(bands, iters):
     return [h.sharded_end(iters) for h in bands]
 
 
-@pytest.mark.parametrize("precision", ["accurate", "fast"])
+@pytest.mark.parametrize("precision", ["accurate", "fast", "separable"])
 @pytest.mark.parametrize("W,H,M,world", [(100, 37, 13, 2), (64, 64, 130, 3), (33, 20, 3, 4)])
 def test_bands_match_unsharded_and_oracle(env, W, H, M, world, precision):
     torch, hot = env
