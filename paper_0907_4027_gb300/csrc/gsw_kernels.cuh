@@ -107,7 +107,7 @@ constexpr int kHalfRows = kRowsMax / 2;
 constexpr int kXsFloats = kChunk * kTileW;
 constexpr int kYsFloats = kChunk * kYStride;
 constexpr int kSmemBytes = (kXsFloats + kYsFloats) * 4 + kChunk * 8 + kWarps * kHalfRows * kTileW * 8 +
-                           kRowsMax * kTileW * 4;
+                           kRowsMax * kTileW * 4 + kChunk * 8;
 
 __host__ __device__ constexpr int step_smem_bytes(int, bool) { return kSmemBytes; }
 
@@ -138,14 +138,25 @@ __device__ __forceinline__ float2 field_from_sums(const StepArgs &a, int m) {
   return make_float2((float)sr * a.inv_fx_n, (float)si * a.inv_fx_n);
 }
 
-// Sec. 3 weight update and back-projection coefficient of trap m in polar form
-// (w_m, arg V_m): w_m <- w_m <|V|>/|V_m|; if |V_m| < 1e-30 the unit field is 1 and w_m stays.
-__device__ __forceinline__ float2 coefficient(const StepArgs &a, int m, float mean) {
-  const float2 v = field_from_sums(a, m);
+// Sec. 3 weight update and back-projection coefficient of a trap with field v and weight w:
+// w <- w <|V|>/|V_m|; if |V_m| < 1e-30 the unit field is 1 and w stays.  Polar form
+// (w', arg V_m in table units), or complex form w' V_m/|V_m| (COMPLEX).
+template <bool COMPLEX>
+__device__ __forceinline__ float2 update_from(float2 v, float w, float mean, float units) {
   const float am = sqrtf(v.x * v.x + v.y * v.y);
-  float w = __ldcg(a.w_in + m);  // written by other blocks (L2, not a possibly stale L1 line)
+  if (COMPLEX) {
+    if (am < 1e-30f) return make_float2(w, 0.f);
+    const float s = w * mean / (am * am);
+    return make_float2(s * v.x, s * v.y);
+  }
   if (am >= 1e-30f) w = w * mean / am;
-  return make_float2(w, am >= 1e-30f ? atan2f(v.y, v.x) * a.angle_units : 0.f);
+  return make_float2(w, am >= 1e-30f ? atan2f(v.y, v.x) * units : 0.f);
+}
+
+// The coefficient of trap m from the previous forward's sums and weights (both written by
+// other blocks: read from L2, not from a possibly stale L1 line).
+__device__ __forceinline__ float2 coefficient(const StepArgs &a, int m, float mean) {
+  return update_from<false>(field_from_sums(a, m), __ldcg(a.w_in + m), mean, a.angle_units);
 }
 
 // Explicit coefficient of trap m (superposition or adjoint) in polar form (|G_m|, arg G_m).
@@ -161,7 +172,7 @@ __device__ __forceinline__ float2 adjoint_coefficient(const StepArgs &a, int m) 
 template <bool BACK, bool ADJ = false>
 __device__ __forceinline__ void stage_tables(const StepArgs &a, int m0, int n, const SubTile &st,
                                              float *Xs, float *Ys, float2 *Cs, bool xy = true,
-                                             float mean = 0.f) {
+                                             float mean = 0.f, bool coef = true) {
   for (int i = threadIdx.x; xy && i < n * kTileW; i += kThreads) {
     const int k = i / kTileW, col = st.x0 + (i % kTileW);
     const bool ok = col < a.W;
@@ -172,7 +183,7 @@ __device__ __forceinline__ void stage_tables(const StepArgs &a, int m0, int n, c
     const bool ok = r < st.rows;
     cp_async4(Ys + i, a.Y + (ok ? (size_t)(m0 + k) * a.H + st.y0 + r : 0), ok);
   }
-  if (BACK)
+  if (BACK && coef)
     for (int i = threadIdx.x; i < n; i += kThreads)
       Cs[i] = (ADJ || a.G) ? adjoint_coefficient(a, m0 + i) : coefficient(a, m0 + i, mean);
   cp_async_wait_all();
@@ -297,26 +308,58 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
   return {hi, e - (hi - s)};
 }
 
-// <|V|> of the previous forward (mean of |V_m| over the traps, Sec. 3), computed by every
-// block in the same fixed order (thread-strided float-float sums, warp shuffles, warps in
-// order), so that all blocks obtain the same value bit for bit.
-__device__ __forceinline__ float mean_field_amplitude(const StepArgs &a) {
+// Weight update a thread writes after its block's work (prefetched in the prologue).
+struct LateWeight {
+  int m;     // first trap (m >= M: none)
+  float2 v;  // its field
+  float w;   // its weight before the update
+};
+
+// Start of a GSW step: the previous forward's fields are read once, every load issued before
+// any is used.  Returns <|V|> (mean of |V_m| over the traps, Sec. 3) computed by every block in
+// the same fixed order (thread-strided float-float sums, warp shuffles, warps in order), so
+// that all blocks obtain the same value bit for bit; writes the coefficients of traps
+// [0, mc) into C0 (polar, or complex when COMPLEX); and prefetches into lw the weight of trap
+// own + stride * threadIdx.x, which write_weights stores after the block's work.
+template <bool COMPLEX>
+__device__ __forceinline__ float gsw_prologue(const StepArgs &a, int mc, float2 *C0, int own, int stride,
+                                              LateWeight &lw) {
   __shared__ ff part[kWarps];
+  const int t = threadIdx.x;
+  lw.m = own + stride * t;
+  lw.v = make_float2(0.f, 0.f);
+  lw.w = 0.f;
+  if (lw.m < a.M) {
+    lw.v = field_from_sums(a, lw.m);
+    lw.w = __ldcg(a.w_in + lw.m);
+  }
+  const float w0 = t < mc ? __ldcg(a.w_in + t) : 0.f;
+  float2 v0 = make_float2(0.f, 0.f);
   ff s = {0.f, 0.f};
-  for (int m = threadIdx.x; m < a.M; m += kThreads) {
+  for (int m = t; m < a.M; m += kThreads) {
     const float2 v = field_from_sums(a, m);
+    if (m == t) v0 = v;
     s = ff_add(s, {sqrtf(v.x * v.x + v.y * v.y), 0.f});
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1)
     s = ff_add(s, {__shfl_down_sync(0xffffffffu, s.hi, o), __shfl_down_sync(0xffffffffu, s.lo, o)});
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  if ((t & 31) == 0) part[t >> 5] = s;
   __syncthreads();
   ff q = part[0];
 #pragma unroll
   for (int i = 1; i < kWarps; i++) q = ff_add(q, part[i]);
-  return (q.hi + q.lo) / (float)a.M;
+  const float mean = (q.hi + q.lo) / (float)a.M;
+  if (t < mc) C0[t] = update_from<COMPLEX>(v0, w0, mean, a.angle_units);
+  return mean;
+}
+
+// The weight updates prefetched by gsw_prologue (traps lw.m, lw.m + stride * kThreads, ...).
+__device__ __forceinline__ void write_weights(const StepArgs &a, const LateWeight &lw, int stride, float mean) {
+  if (lw.m < a.M) a.w_out[lw.m] = update_from<false>(lw.v, lw.w, mean, 1.f).x;
+  for (int m = lw.m + stride * kThreads; m < a.M; m += stride * kThreads)
+    a.w_out[m] = update_from<false>(field_from_sums(a, m), __ldcg(a.w_in + m), mean, 1.f).x;
 }
 
 struct FinalizeArgs {
@@ -430,21 +473,24 @@ struct StepSmem {
   float *Xs, *Ys;
   float2 *Cs, *Sp;
   float *Ps;
+  float2 *C0;  // [kChunk] coefficients of the first trap chunk, from the step's prologue
   __device__ __forceinline__ explicit StepSmem(unsigned char *raw) {
     Xs = reinterpret_cast<float *>(raw);
     Ys = Xs + kXsFloats;
     Cs = reinterpret_cast<float2 *>(Ys + kYsFloats);
     Sp = Cs + kChunk;                                                  // [kWarps][kHalfRows][kTileW]
     Ps = reinterpret_cast<float *>(Sp + kWarps * kHalfRows * kTileW);  // [kRowsMax][kTileW] phases
+    C0 = reinterpret_cast<float2 *>(Ps + kRowsMax * kTileW);
   }
 };
 
 // One sub-tile of the hologram a: back-projection (with the coefficients implied by `mean`,
 // or explicit ones) and/or forward field.  prestaged: the first chunk's X/Y tables are
-// already in shared memory (staged in the prologue) -- cleared after use.
+// already in shared memory (staged in the prologue) -- cleared after use.  C0: the first
+// chunk's coefficients, computed by the step's prologue (NULL: staged with the tables).
 template <bool FAST, bool BACK, bool FWD, bool ADJ>
 __device__ __forceinline__ void process_subtile(const StepArgs &a, const SubTile st, float mean, bool &prestaged,
-                                                const StepSmem &sm) {
+                                                const StepSmem &sm, const float2 *C0 = nullptr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int mc = a.M < a.chunk ? a.M : a.chunk;
   const int nchunks = (a.M + mc - 1) / mc;
@@ -457,12 +503,14 @@ __device__ __forceinline__ void process_subtile(const StepArgs &a, const SubTile
     for (int r = 0; r < kRowsMax; r++) S[r] = make_float2(0.f, 0.f);
     for (int ch = 0; ch < nchunks; ch++) {
       const int m0 = ch * mc, n = min(mc, a.M - m0);
+      const bool pre = C0 && ch == 0;
       __syncthreads();  // earlier readers of the tables are done
-      stage_tables<true, ADJ>(a, m0, n, st, sm.Xs, sm.Ys, sm.Cs, !prestaged, mean);
+      stage_tables<true, ADJ>(a, m0, n, st, sm.Xs, sm.Ys, sm.Cs, !prestaged, mean, !pre);
       prestaged = false;
       __syncthreads();
       const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
-      HOT_WITH_ROWS(st.rows, (back_traps<FAST, R>(sm.Xs, sm.Ys, sm.Cs, lo, hi, lane, S)));
+      const float2 *C = pre ? C0 : sm.Cs;
+      HOT_WITH_ROWS(st.rows, (back_traps<FAST, R>(sm.Xs, sm.Ys, C, lo, hi, lane, S)));
     }
     // Sum the 8 warps' superpositions, half of the rows at a time, in warp order.
 #pragma unroll
@@ -541,12 +589,12 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
   if (FWD)  // the buffer the next launch accumulates into
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
   float mean = 0.f;
-  if (BACK && !ADJ && !a.G) {
-    mean = mean_field_amplitude(a);
-    for (int m = blockIdx.x + gridDim.x * threadIdx.x; m < a.M; m += gridDim.x * kThreads)
-      a.w_out[m] = coefficient(a, m, mean).x;
-  }
-  for (int t = t_begin; t < t_end; t++) process_subtile<FAST, BACK, FWD, ADJ>(a, a.sub[t], mean, prestaged, sm);
+  LateWeight lw;
+  const bool gsw = BACK && !ADJ && !a.G;
+  if (gsw) mean = gsw_prologue<false>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw);
+  for (int t = t_begin; t < t_end; t++)
+    process_subtile<FAST, BACK, FWD, ADJ>(a, a.sub[t], mean, prestaged, sm, gsw ? sm.C0 : nullptr);
+  if (gsw) write_weights(a, lw, gridDim.x, mean);
 }
 
 // Batched launch: the sub-tiles of up to kBatchMax holograms (SubTile::pad = hologram index)
@@ -588,17 +636,19 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_batch_kernel(const __grid_con
     }
   int cur = -1;
   float mean = 0.f;
+  LateWeight lw;  // the owner block writes all weights of a hologram, after its sub-tiles
   for (int t = t_begin; t < t_end; t++) {
     const SubTile st = b.sub[t];
     const StepArgs &a = b.holo[st.pad];
     if (BACK && st.pad != cur) {
-      mean = mean_field_amplitude(a);
-      if (b.owner[st.pad] == (int)blockIdx.x)
-        for (int m = threadIdx.x; m < a.M; m += kThreads) a.w_out[m] = coefficient(a, m, mean).x;
+      if (cur >= 0) write_weights(b.holo[cur], lw, 1, mean);
+      const int mc = a.M < a.chunk ? a.M : a.chunk;
+      mean = gsw_prologue<false>(a, mc, sm.C0, b.owner[st.pad] == (int)blockIdx.x ? 0 : a.M, 1, lw);
     }
     cur = st.pad;
-    process_subtile<FAST, BACK, FWD, false>(a, st, mean, prestaged, sm);
+    process_subtile<FAST, BACK, FWD, false>(a, st, mean, prestaged, sm, BACK ? sm.C0 : nullptr);
   }
+  if (BACK && cur >= 0) write_weights(b.holo[cur], lw, 1, mean);
 }
 
 // Start stamp of a batched sequence (%globaltimer, ns).
@@ -619,34 +669,30 @@ __global__ void stamp_kernel(unsigned long long *t) { *t = global_timer_ns(); }
 constexpr int kSepUsFloats = kRowsMax * kTileW * 2;
 
 __host__ __device__ constexpr int sep_smem_bytes(int chunk) {
-  return chunk * (kTileW + kYStride) * 8 + chunk * 8 + kWarps * kHalfRows * kTileW * 8 + kSepUsFloats * 4;
+  return chunk * (kTileW + kYStride) * 8 + 2 * chunk * 8 + kWarps * kHalfRows * kTileW * 8 + kSepUsFloats * 4;
 }
 
 struct SepSmem {
-  float2 *Xs, *Ys, *Cs, *Sp, *Us;
+  float2 *Xs, *Ys, *Cs, *Sp, *Us, *C0;
   __device__ __forceinline__ SepSmem(unsigned char *raw, int chunk) {
     Xs = reinterpret_cast<float2 *>(raw);  // [chunk][kTileW]
     Ys = Xs + chunk * kTileW;              // [chunk][kYStride]
     Cs = Ys + chunk * kYStride;            // [chunk]
     Sp = Cs + chunk;                       // [kWarps][kHalfRows][kTileW]
     Us = Sp + kWarps * kHalfRows * kTileW; // [kRowsMax][kTileW] unit phasors of the sub-tile
+    C0 = Us + kRowsMax * kTileW;           // [chunk] coefficients of the first chunk (prologue)
   }
 };
 
 // Sec. 3 coefficient of trap m in complex form: w_m' V_m/|V_m| with w_m' = w_m <|V|>/|V_m|
 // (R4: |V_m| = 0 keeps w_m and takes the unit field 1).
 __device__ __forceinline__ float2 complex_coefficient(const StepArgs &a, int m, float mean) {
-  const float2 v = field_from_sums(a, m);
-  const float am = sqrtf(v.x * v.x + v.y * v.y);
-  const float w = __ldcg(a.w_in + m);
-  if (am < 1e-30f) return make_float2(w, 0.f);
-  const float s = w * mean / (am * am);
-  return make_float2(s * v.x, s * v.y);
+  return update_from<true>(field_from_sums(a, m), __ldcg(a.w_in + m), mean, 1.f);
 }
 
 template <bool BACK, bool ADJ = false>
 __device__ __forceinline__ void stage_sep(const StepArgs &a, int m0, int n, const SubTile &st, const SepSmem &sm,
-                                          bool xy = true, float mean = 0.f) {
+                                          bool xy = true, float mean = 0.f, bool coef = true) {
   for (int i = threadIdx.x; xy && i < n * kTileW; i += kThreads) {
     const int k = i / kTileW, col = st.x0 + (i % kTileW);
     const bool ok = col < a.W;
@@ -657,17 +703,18 @@ __device__ __forceinline__ void stage_sep(const StepArgs &a, int m0, int n, cons
     const bool ok = r < st.rows;
     cp_async8(sm.Ys + i, a.Yc + (ok ? (size_t)(m0 + k) * a.H + st.y0 + r : 0), ok);
   }
-  if (BACK)
+  if (BACK && coef)
     for (int i = threadIdx.x; i < n; i += kThreads)
       sm.Cs[i] = (ADJ || a.G) ? a.G[m0 + i] : complex_coefficient(a, m0 + i, mean);
   cp_async_wait_all();
 }
 
-// S_r += Yc_m(r) (c_m Xc_m(lane)) for traps [lo, hi) of the staged chunk.
+// S_r += Yc_m(r) (c_m Xc_m(lane)) for traps [lo, hi) of the staged chunk (coefficients C).
 template <int R>
-__device__ __forceinline__ void back_traps_sep(const SepSmem &sm, int lo, int hi, int lane, float2 (&S)[kRowsMax]) {
+__device__ __forceinline__ void back_traps_sep(const SepSmem &sm, const float2 *C, int lo, int hi, int lane,
+                                               float2 (&S)[kRowsMax]) {
   for (int k = lo; k < hi; k++) {
-    const float2 x = sm.Xs[k * kTileW + lane], c = sm.Cs[k];
+    const float2 x = sm.Xs[k * kTileW + lane], c = C[k];
     const float2 b = make_float2(c.x * x.x - c.y * x.y, c.x * x.y + c.y * x.x);
     const float4 *yq = reinterpret_cast<const float4 *>(sm.Ys + k * kYStride);
 #pragma unroll
@@ -729,7 +776,7 @@ __device__ __forceinline__ void forward_traps_sep(const SepSmem &sm, int lo, int
 
 template <bool BACK, bool FWD, bool ADJ>
 __device__ __forceinline__ void process_subtile_sep(const StepArgs &a, const SubTile st, float mean, bool &prestaged,
-                                                    const SepSmem &sm) {
+                                                    const SepSmem &sm, const float2 *C0 = nullptr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int mc = a.M < a.chunk ? a.M : a.chunk;
   const int nchunks = (a.M + mc - 1) / mc;
@@ -742,12 +789,14 @@ __device__ __forceinline__ void process_subtile_sep(const StepArgs &a, const Sub
     for (int r = 0; r < kRowsMax; r++) S[r] = make_float2(0.f, 0.f);
     for (int ch = 0; ch < nchunks; ch++) {
       const int m0 = ch * mc, n = min(mc, a.M - m0);
+      const bool pre = C0 && ch == 0;
       __syncthreads();  // earlier readers of the tables are done
-      stage_sep<true, ADJ>(a, m0, n, st, sm, !prestaged, mean);
+      stage_sep<true, ADJ>(a, m0, n, st, sm, !prestaged, mean, !pre);
       prestaged = false;
       __syncthreads();
       const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
-      HOT_WITH_ROWS(st.rows, (back_traps_sep<R>(sm, lo, hi, lane, S)));
+      const float2 *C = pre ? C0 : sm.Cs;
+      HOT_WITH_ROWS(st.rows, (back_traps_sep<R>(sm, C, lo, hi, lane, S)));
     }
 #pragma unroll
     for (int h = 0; h < 2; h++) {
@@ -829,12 +878,12 @@ __global__ void __launch_bounds__(kThreads, 3) gsw_sep_kernel(StepArgs a) {
   if (FWD)
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
   float mean = 0.f;
-  if (BACK && !ADJ && !a.G) {
-    mean = mean_field_amplitude(a);
-    for (int m = blockIdx.x + gridDim.x * threadIdx.x; m < a.M; m += gridDim.x * kThreads)
-      a.w_out[m] = coefficient(a, m, mean).x;
-  }
-  for (int t = t_begin; t < t_end; t++) process_subtile_sep<BACK, FWD, ADJ>(a, a.sub[t], mean, prestaged, sm);
+  LateWeight lw;
+  const bool gsw = BACK && !ADJ && !a.G;
+  if (gsw) mean = gsw_prologue<true>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw);
+  for (int t = t_begin; t < t_end; t++)
+    process_subtile_sep<BACK, FWD, ADJ>(a, a.sub[t], mean, prestaged, sm, gsw ? sm.C0 : nullptr);
+  if (gsw) write_weights(a, lw, gridDim.x, mean);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -921,27 +970,29 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 3 : 4)
     if (k > 0 && !grid_sync(p.sync, epoch)) return;
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
     float mean = 0.f;
-    if (k > 0) {
-      mean = mean_field_amplitude(a);
-      for (int m = blockIdx.x + gridDim.x * threadIdx.x; m < a.M; m += gridDim.x * kThreads)
-        a.w_out[m] = coefficient(a, m, mean).x;
-    }
-    for (int t = t_begin; t < t_end; t++) {
-      bool prestaged = resident && k > 0;
-      if constexpr (MODE == kModeSeparable) {
-        const SepSmem sm(smem_raw, mc);
+    LateWeight lw;
+    if constexpr (MODE == kModeSeparable) {
+      const SepSmem sm(smem_raw, mc);
+      if (k > 0) mean = gsw_prologue<true>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw);
+      for (int t = t_begin; t < t_end; t++) {
+        bool prestaged = resident && k > 0;
         if (k == 0)
           process_subtile_sep<false, true, false>(a, a.sub[t], 0.f, prestaged, sm);
         else
-          process_subtile_sep<true, true, false>(a, a.sub[t], mean, prestaged, sm);
-      } else {
-        const StepSmem sm(smem_raw);
+          process_subtile_sep<true, true, false>(a, a.sub[t], mean, prestaged, sm, sm.C0);
+      }
+    } else {
+      const StepSmem sm(smem_raw);
+      if (k > 0) mean = gsw_prologue<false>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw);
+      for (int t = t_begin; t < t_end; t++) {
+        bool prestaged = resident && k > 0;
         if (k == 0)
           process_subtile<FAST, false, true, false>(a, a.sub[t], 0.f, prestaged, sm);
         else
-          process_subtile<FAST, true, true, false>(a, a.sub[t], mean, prestaged, sm);
+          process_subtile<FAST, true, true, false>(a, a.sub[t], mean, prestaged, sm, sm.C0);
       }
     }
+    if (k > 0) write_weights(a, lw, gridDim.x, mean);
   }
 }
 
