@@ -106,6 +106,22 @@ int hot_set_precision(hot_ctx *c, int precision);
  * HOT_ESTATE before hot_set_traps; HOT_EINVAL if iters < 0. */
 int hot_gsw(hot_ctx *c, int iters, double *eff_out, double *unif_out);
 
+/* Checkpoint / resume: the GSW state is the phases and the weights (float32, exactly as held),
+ * so hot_set_state on a context with the same optics and traps continues bit for bit where
+ * hot_get_state left off.  phi: HOST float32 [H*W]; w: HOST float32 [M] (finite, > 0).
+ * Both synchronise; HOT_ESTATE before hot_set_traps. */
+int hot_get_state(hot_ctx *c, float *phi, float *w);
+int hot_set_state(hot_ctx *c, const float *phi, const float *w);
+
+/* Convergence trace (no counterpart in the paper): with enable != 0, every following hot_gsw
+ * records e and u (Eq. 4) of the field each iteration starts from; block 0 of each step
+ * computes them from the sums it reads anyway.  hot_get_trace then returns n = iters + 1
+ * values of the last call: F(phi^0), ..., F(phi^(iters-1)) and the final F(phi^iters).
+ * eff, unif: HOST arrays of n doubles.  HOT_ESTATE without a traced call; HOT_EINVAL for
+ * another n.  hot_set_trace synchronises. */
+int hot_set_trace(hot_ctx *c, int enable);
+int hot_get_trace(hot_ctx *c, double *eff, double *unif, int n);
+
 /* enable != 0: hot_gsw runs as one persistent cooperative launch plus the finalize kernel;
  * 0 (the default): one launch per iteration, replayed as a CUDA graph (hot_use_graphs), whose
  * programmatic dependent launches overlap consecutive iterations.  Both forms use the same

@@ -67,6 +67,7 @@ struct StepArgs {
   const float2 *G;                   // [M] or NULL: coefficients of the back-projection
   float *grad;                       // [H*W] out: dL/dphi_j
   float inv_n;                       // 1 / N
+  float *trace;                      // NULL, or out: e, u (Eq. 4) of the field this launch reads
   float fx_scale;           // 2^fx_shift: fixed-point scale of the sums
   float inv_fx_n;           // 1 / (N 2^fx_shift)
   float angle_units;        // 1 (radians) or 1/(2 pi) (turns): units of the tables
@@ -321,10 +322,12 @@ struct LateWeight {
 // that all blocks obtain the same value bit for bit; writes the coefficients of traps
 // [0, mc) into C0 (polar, or complex when COMPLEX); and prefetches into lw the weight of trap
 // own + stride * threadIdx.x, which write_weights stores after the block's work.
+// trace: NULL, or where block 0 writes e and u (Eq. 4) of the fields it read (convergence trace).
 template <bool COMPLEX>
 __device__ __forceinline__ float gsw_prologue(const StepArgs &a, int mc, float2 *C0, int own, int stride,
-                                              LateWeight &lw) {
+                                              LateWeight &lw, float *trace = nullptr) {
   __shared__ ff part[kWarps];
+  __shared__ float ext[2][kWarps];
   const int t = threadIdx.x;
   lw.m = own + stride * t;
   lw.v = make_float2(0.f, 0.f);
@@ -336,10 +339,19 @@ __device__ __forceinline__ float gsw_prologue(const StepArgs &a, int mc, float2 
   const float w0 = t < mc ? __ldcg(a.w_in + t) : 0.f;
   float2 v0 = make_float2(0.f, 0.f);
   ff s = {0.f, 0.f};
+  const bool tr = trace && blockIdx.x == 0;
+  ff si = {0.f, 0.f};
+  float mx = -1.f, mn = 3.0e38f;
   for (int m = t; m < a.M; m += kThreads) {
     const float2 v = field_from_sums(a, m);
     if (m == t) v0 = v;
     s = ff_add(s, {sqrtf(v.x * v.x + v.y * v.y), 0.f});
+    if (tr) {
+      const float I = v.x * v.x + v.y * v.y;
+      si = ff_add(si, {I, 0.f});
+      mx = fmaxf(mx, I);
+      mn = fminf(mn, I);
+    }
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1)
@@ -351,6 +363,32 @@ __device__ __forceinline__ float gsw_prologue(const StepArgs &a, int mc, float2 
 #pragma unroll
   for (int i = 1; i < kWarps; i++) q = ff_add(q, part[i]);
   const float mean = (q.hi + q.lo) / (float)a.M;
+  if (tr) {  // block 0 only: e = sum I_m, u = 1 - (max - min)/(max + min) of the fields read
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      si = ff_add(si, {__shfl_down_sync(0xffffffffu, si.hi, o), __shfl_down_sync(0xffffffffu, si.lo, o)});
+      mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+      mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, o));
+    }
+    __syncthreads();  // every thread has read part[] above
+    if ((t & 31) == 0) {
+      part[t >> 5] = si;
+      ext[0][t >> 5] = mx;
+      ext[1][t >> 5] = mn;
+    }
+    __syncthreads();
+    if (t == 0) {
+      ff e = part[0];
+      float hi = ext[0][0], lo = ext[1][0];
+      for (int i = 1; i < kWarps; i++) {
+        e = ff_add(e, part[i]);
+        hi = fmaxf(hi, ext[0][i]);
+        lo = fminf(lo, ext[1][i]);
+      }
+      trace[0] = e.hi + e.lo;
+      trace[1] = (hi + lo > 0.f) ? 1.f - (hi - lo) / (hi + lo) : 0.f;
+    }
+  }
   if (t < mc) C0[t] = update_from<COMPLEX>(v0, w0, mean, a.angle_units);
   return mean;
 }
@@ -591,7 +629,7 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
   float mean = 0.f;
   LateWeight lw;
   const bool gsw = BACK && !ADJ && !a.G;
-  if (gsw) mean = gsw_prologue<false>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw);
+  if (gsw) mean = gsw_prologue<false>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, a.trace);
   for (int t = t_begin; t < t_end; t++)
     process_subtile<FAST, BACK, FWD, ADJ>(a, a.sub[t], mean, prestaged, sm, gsw ? sm.C0 : nullptr);
   if (gsw) write_weights(a, lw, gridDim.x, mean);
@@ -693,15 +731,19 @@ __device__ __forceinline__ float2 complex_coefficient(const StepArgs &a, int m, 
 template <bool BACK, bool ADJ = false>
 __device__ __forceinline__ void stage_sep(const StepArgs &a, int m0, int n, const SubTile &st, const SepSmem &sm,
                                           bool xy = true, float mean = 0.f, bool coef = true) {
-  for (int i = threadIdx.x; xy && i < n * kTileW; i += kThreads) {
-    const int k = i / kTileW, col = st.x0 + (i % kTileW);
-    const bool ok = col < a.W;
-    cp_async8(sm.Xs + i, a.Xc + (ok ? (size_t)(m0 + k) * a.W + col : 0), ok);
-  }
-  for (int i = threadIdx.x; xy && i < n * kYStride; i += kThreads) {
-    const int k = i / kYStride, r = i % kYStride;
-    const bool ok = r < st.rows;
-    cp_async8(sm.Ys + i, a.Yc + (ok ? (size_t)(m0 + k) * a.H + st.y0 + r : 0), ok);
+  if (xy) {
+    // thread t copies column t % 32 of traps t / 32, t / 32 + 8, ... and row t % 16 of traps
+    // t / 16, t / 16 + 16, ...: fixed column / row, pointers advanced by whole trap strides
+    const int col = threadIdx.x % kTileW, kx = threadIdx.x / kTileW;
+    const bool okx = st.x0 + col < a.W;
+    const float2 *src = a.Xc + (okx ? (size_t)(m0 + kx) * a.W + st.x0 + col : 0);
+    const size_t sx = okx ? (size_t)(kThreads / kTileW) * a.W : 0;
+    for (int k = kx; k < n; k += kThreads / kTileW, src += sx) cp_async8(sm.Xs + k * kTileW + col, src, okx);
+    const int r = threadIdx.x % kYStride, ky = threadIdx.x / kYStride;
+    const bool oky = r < st.rows;
+    const float2 *srcy = a.Yc + (oky ? (size_t)(m0 + ky) * a.H + st.y0 + r : 0);
+    const size_t sy = oky ? (size_t)(kThreads / kYStride) * a.H : 0;
+    for (int k = ky; k < n; k += kThreads / kYStride, srcy += sy) cp_async8(sm.Ys + k * kYStride + r, srcy, oky);
   }
   if (BACK && coef)
     for (int i = threadIdx.x; i < n; i += kThreads)
@@ -880,7 +922,7 @@ __global__ void __launch_bounds__(kThreads, 3) gsw_sep_kernel(StepArgs a) {
   float mean = 0.f;
   LateWeight lw;
   const bool gsw = BACK && !ADJ && !a.G;
-  if (gsw) mean = gsw_prologue<true>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw);
+  if (gsw) mean = gsw_prologue<true>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, a.trace);
   for (int t = t_begin; t < t_end; t++)
     process_subtile_sep<BACK, FWD, ADJ>(a, a.sub[t], mean, prestaged, sm, gsw ? sm.C0 : nullptr);
   if (gsw) write_weights(a, lw, gridDim.x, mean);
@@ -950,6 +992,7 @@ struct PersistArgs {
   StepArgs step[6];
   int iters;
   GridSync sync;
+  float *trace;  // NULL, or [iters][2]: e, u of the field read by iteration k (convergence trace)
 };
 
 constexpr int kModeAccurate = 0, kModeFast = 1, kModeSeparable = 2;
@@ -973,7 +1016,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 3 : 4)
     LateWeight lw;
     if constexpr (MODE == kModeSeparable) {
       const SepSmem sm(smem_raw, mc);
-      if (k > 0) mean = gsw_prologue<true>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw);
+      if (k > 0) mean = gsw_prologue<true>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, p.trace ? p.trace + 2 * (k - 1) : nullptr);
       for (int t = t_begin; t < t_end; t++) {
         bool prestaged = resident && k > 0;
         if (k == 0)
@@ -983,7 +1026,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 3 : 4)
       }
     } else {
       const StepSmem sm(smem_raw);
-      if (k > 0) mean = gsw_prologue<false>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw);
+      if (k > 0) mean = gsw_prologue<false>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, p.trace ? p.trace + 2 * (k - 1) : nullptr);
       for (int t = t_begin; t < t_end; t++) {
         bool prestaged = resident && k > 0;
         if (k == 0)

@@ -103,6 +103,10 @@ struct hot_ctx {
   cudaStream_t cap = nullptr;  // capture stream (capture is not allowed on the legacy stream)
   // persistent form (one cooperative launch per hot_gsw): grid barrier state [count, gen, err]
   bool persistent = false;
+  // convergence trace (hot_set_trace): e, u of the field read by each iteration of hot_gsw
+  bool tracing = false;
+  float *trace = nullptr;  // [trace_cap][2]
+  int trace_cap = 0, trace_iters = -1;
   double wait_limit_s = 2.0;
   unsigned int *sync = nullptr;
   std::vector<Graph> graphs;
@@ -233,6 +237,7 @@ hot::StepArgs make_step_args(const hot_ctx *c, int k, const float *phi, const fl
   a.G = G;
   a.grad = grad;
   a.inv_n = (float)(1.0 / (n_total(c)));
+  a.trace = (c->tracing && c->trace && k >= 1 && k <= c->trace_cap) ? c->trace + 2 * (k - 1) : nullptr;
   return a;
 }
 
@@ -408,6 +413,7 @@ int launch_persistent(hot_ctx *c, int iters) {
     if (c->precision == HOT_PREC_SEPARABLE) p.step[j].chunk = sep_chunk(c);
   }
   p.iters = iters;
+  p.trace = c->tracing ? c->trace : nullptr;
   p.sync.count = c->sync;
   p.sync.err = reinterpret_cast<int *>(c->sync + 2);
   p.sync.limit_ns = (long long)(c->wait_limit_s * 1e9);
@@ -563,6 +569,7 @@ void hot_destroy(hot_ctx *c) {
   dfree(c->metrics);
   dfree(c->u8);
   dfree(c->sync);
+  dfree(c->trace);
   delete c;
 }
 
@@ -674,6 +681,19 @@ int hot_gsw(hot_ctx *c, int iters, double *eff_out, double *unif_out) {
   if (!c) return fail(HOT_EINVAL, "hot_gsw: NULL context");
   if (iters < 0) return fail(HOT_EINVAL, "hot_gsw: iters = %d < 0", iters);
   if (!c->M) return fail(HOT_ESTATE, "hot_gsw: no traps set");
+  if (c->tracing) {
+    if (iters > c->trace_cap) {  // the launches' trace slots change: recapture the graphs
+      HOT_CUDA(cudaStreamSynchronize(c->st));
+      drop_graphs(c);
+      dfree(c->trace);
+      c->trace_cap = 0;
+      const int cap = std::max(iters, 64);
+      const int rc = dalloc(&c->trace, 2 * (size_t)cap);
+      if (rc != HOT_OK) return rc;
+      c->trace_cap = cap;
+    }
+    c->trace_iters = iters;
+  }
   const int rc = (c->use_graphs && !c->profiling && !c->persistent) ? launch_gsw_graph(c, iters) : enqueue_gsw(c, iters);
   if (rc != HOT_OK) return rc;
   c->have_fields = true;
@@ -862,6 +882,59 @@ int hot_sync(hot_ctx *c) {
   if (!c) return fail(HOT_EINVAL, "hot_sync: NULL context");
   HOT_CUDA(cudaStreamSynchronize(c->st));
   return check_wait_error(c, "hot_sync");
+}
+
+int hot_set_trace(hot_ctx *c, int enable) {
+  if (!c) return fail(HOT_EINVAL, "hot_set_trace: NULL context");
+  if ((enable != 0) != c->tracing) {
+    HOT_CUDA(cudaStreamSynchronize(c->st));
+    drop_graphs(c);  // the captured launches carry (or not) trace slots
+  }
+  c->tracing = enable != 0;
+  c->trace_iters = -1;
+  return HOT_OK;
+}
+
+int hot_get_trace(hot_ctx *c, double *eff, double *unif, int n) {
+  if (!c || !eff || !unif) return fail(HOT_EINVAL, "hot_get_trace: NULL argument");
+  if (!c->tracing || c->trace_iters < 0 || !c->have_fields)
+    return fail(HOT_ESTATE, "hot_get_trace: no traced hot_gsw since tracing was enabled");
+  const int K = c->trace_iters;
+  if (n != K + 1) return fail(HOT_EINVAL, "hot_get_trace: n = %d, the last call has %d values", n, K + 1);
+  const int rc = check_wait_error(c, "hot_get_trace");
+  if (rc != HOT_OK) return rc;
+  std::vector<float> t(2 * (size_t)K + 2);
+  if (K) HOT_CUDA(cudaMemcpyAsync(t.data(), c->trace, sizeof(float) * 2 * K, cudaMemcpyDeviceToHost, c->st));
+  HOT_CUDA(cudaMemcpyAsync(t.data() + 2 * K, c->metrics, sizeof(float) * 2, cudaMemcpyDeviceToHost, c->st));
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  for (int k = 0; k <= K; k++) {
+    eff[k] = t[2 * k];
+    unif[k] = t[2 * k + 1];
+  }
+  return HOT_OK;
+}
+
+int hot_get_state(hot_ctx *c, float *phi, float *w) {
+  if (!c || !phi || !w) return fail(HOT_EINVAL, "hot_get_state: NULL argument");
+  if (!c->M) return fail(HOT_ESTATE, "hot_get_state: no traps set");
+  const int rc = check_wait_error(c, "hot_get_state");
+  if (rc != HOT_OK) return rc;
+  HOT_CUDA(cudaMemcpyAsync(phi, c->phi, sizeof(float) * (size_t)c->W * c->H, cudaMemcpyDeviceToHost, c->st));
+  HOT_CUDA(cudaMemcpyAsync(w, c->w, sizeof(float) * c->M, cudaMemcpyDeviceToHost, c->st));
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  return HOT_OK;
+}
+
+int hot_set_state(hot_ctx *c, const float *phi, const float *w) {
+  if (!c || !phi || !w) return fail(HOT_EINVAL, "hot_set_state: NULL argument");
+  if (!c->M) return fail(HOT_ESTATE, "hot_set_state: no traps set");
+  for (int m = 0; m < c->M; m++)
+    if (!(std::isfinite(w[m]) && w[m] > 0.f)) return fail(HOT_EINVAL, "hot_set_state: weight %d not finite and > 0", m);
+  HOT_CUDA(cudaMemcpyAsync(c->phi, phi, sizeof(float) * (size_t)c->W * c->H, cudaMemcpyHostToDevice, c->st));
+  HOT_CUDA(cudaMemcpyAsync(c->w, w, sizeof(float) * c->M, cudaMemcpyHostToDevice, c->st));
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  c->have_fields = false;
+  return HOT_OK;
 }
 
 int hot_use_persistent(hot_ctx *c, int enable) {

@@ -66,6 +66,10 @@ SIGNATURES = {
     "hot_kernel_launches": (ctypes.c_longlong, [_vp]),
     "hot_use_graphs": (_c_int, [_vp, _c_int]),
     "hot_use_persistent": (_c_int, [_vp, _c_int]),
+    "hot_set_trace": (_c_int, [_vp, _c_int]),
+    "hot_get_trace": (_c_int, [_vp, _vp, _vp, _c_int]),
+    "hot_get_state": (_c_int, [_vp, _vp, _vp]),
+    "hot_set_state": (_c_int, [_vp, _vp, _vp]),
     "hot_set_wait_limit": (_c_int, [_vp, _c_double]),
     "hot_profile": (_c_int, [_vp, _c_int]),
     "hot_profile_read": (_c_int, [_vp, _vp, _vp]),
@@ -338,6 +342,28 @@ def hot_use_graphs(ctx: int, enable: bool) -> None:
     _ok(lib.hot_use_graphs(_vp(ctx), int(bool(enable))), "hot_use_graphs")
 
 
+def hot_set_trace(ctx: int, enable: bool) -> None:
+    _ok(lib.hot_set_trace(_vp(ctx), int(bool(enable))), "hot_set_trace")
+
+
+def hot_get_trace(ctx: int, n: int):
+    e, u = np.empty(n), np.empty(n)
+    _ok(lib.hot_get_trace(_vp(ctx), e.ctypes.data_as(_vp), u.ctypes.data_as(_vp), int(n)), "hot_get_trace")
+    return e, u
+
+
+def hot_get_state(ctx: int, N: int, M: int):
+    phi, w = np.empty(N, dtype=np.float32), np.empty(M, dtype=np.float32)
+    _ok(lib.hot_get_state(_vp(ctx), phi.ctypes.data_as(_vp), w.ctypes.data_as(_vp)), "hot_get_state")
+    return phi, w
+
+
+def hot_set_state(ctx: int, phi, w) -> None:
+    phi, pp = _host_ptr(np.asarray(phi).reshape(-1), np.float32)
+    w, wp = _host_ptr(np.asarray(w).reshape(-1), np.float32)
+    _ok(lib.hot_set_state(_vp(ctx), pp, wp), "hot_set_state")
+
+
 def hot_use_persistent(ctx: int, enable: bool) -> None:
     _ok(lib.hot_use_persistent(_vp(ctx), int(bool(enable))), "hot_use_persistent")
 
@@ -457,6 +483,20 @@ class Hologram:
 
     def use_persistent(self, enable: bool = True):
         hot_use_persistent(self.ctx, enable)
+
+    def set_trace(self, enable: bool = True):
+        hot_set_trace(self.ctx, enable)
+
+    def trace(self, iters: int):
+        """(e, u) arrays of the last traced gsw(iters): iters + 1 values, F(phi^0) .. F(phi^iters)."""
+        return hot_get_trace(self.ctx, iters + 1)
+
+    def get_state(self):
+        """(phi, w) float32 host copies: resume elsewhere with set_state, bit for bit."""
+        return hot_get_state(self.ctx, self.N, self.M)
+
+    def set_state(self, phi, w):
+        hot_set_state(self.ctx, phi, w)
 
     def set_wait_limit(self, seconds: float):
         hot_set_wait_limit(self.ctx, seconds)

@@ -309,3 +309,47 @@ def test_barrier_wait_limit_reports_timeout_and_recovers(hot):
         with make(hot, w) as h:
             with pytest.raises(hot.HotError, match="HOT_EINVAL"):
                 h.set_wait_limit(bad)
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_convergence_trace_matches_oracle(hot, persistent):
+    """hot_set_trace: e and u of F(phi^k), k = 0..K, against the oracle's runs of k iterations;
+    the last entry is the call's own result; a longer call regrows the trace."""
+    w = wl.random_case(100, 37, 13, seed=21, precision="fast")
+    with make(hot, w) as h:
+        h.use_persistent(persistent)
+        h.set_trace(True)
+        eK, uK = h.gsw(5)
+        e, u = h.trace(5)
+        assert e[-1] == np.float32(eK) and u[-1] == np.float32(uK)
+        h.set_phase(w.phi0)
+        h.set_weights(np.ones(w.M))
+        h.gsw(70)
+        e70, u70 = h.trace(70)
+        with pytest.raises(hot.HotError, match="HOT_EINVAL"):
+            h.trace(5)
+    for k in range(6):
+        r = oracle.gsw(w.geom, w.xyz, k, w.phi0)
+        assert abs(e[k] - r["e"]) < ABS_EU and abs(u[k] - r["u"]) < ABS_EU, (k, e[k], r["e"], u[k], r["u"])
+    assert np.array_equal(e70[:6], e) and np.array_equal(u70[:6], u)
+    assert len(e70) == 71 and e70[-1] > 0.5
+
+
+def test_checkpoint_resume_across_contexts(hot):
+    """hot_get_state / hot_set_state: 3 iterations, state moved to a fresh context, 2 more
+    iterations equal 5 iterations in one context, bit for bit."""
+    w = wl.random_case(70, 45, 20, seed=22, precision="fast")
+    with make(hot, w) as a:
+        a.gsw(5)
+        ref = (a.phase("f32"), a.fields())
+    with make(hot, w) as b:
+        b.gsw(3)
+        phi, wt = b.get_state()
+    with hot.Hologram(w.W, w.H, w.pitch, w.wavelength, w.focal, precision=w.precision) as c:
+        c.set_traps(w.xyz)
+        c.set_state(phi, wt)
+        c.gsw(2)
+        got = (c.phase("f32"), c.fields())
+        with pytest.raises(hot.HotError, match="HOT_EINVAL"):
+            c.set_state(phi, -wt)
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1][0], got[1][0]) and np.array_equal(ref[1][1], got[1][1])
