@@ -519,8 +519,9 @@ def run_grid_sweep(args):
 
 
 def run_precision_report(args):
-    """Errors of HOT_PREC_ACCURATE and HOT_PREC_FAST against the FP64 oracle, per result, on
-    grid16_256 and rand100_512, with the time per GSW iteration of each mode."""
+    """Errors of HOT_PREC_ACCURATE, HOT_PREC_FAST and HOT_PREC_SEPARABLE against the FP64
+    oracle, per result, on grid16_256 and rand100_512, with the time per GSW iteration of each
+    mode."""
     import torch
     import oracle
     from paper_0907_4027_gb300 import _build
@@ -534,7 +535,7 @@ def run_precision_report(args):
         K = base.iters
         r1 = oracle.gsw(base.geom, base.xyz, 1, base.phi0)
         rK = oracle.gsw(base.geom, base.xyz, K, base.phi0)
-        for prec in ("accurate", "fast"):
+        for prec in ("accurate", "fast", "separable"):
             w = wl.NAMED[name]()
             w.precision = prec
             h = hot.Hologram.from_workload(w, stream.cuda_stream)
