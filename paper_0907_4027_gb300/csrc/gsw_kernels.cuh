@@ -101,6 +101,15 @@ __device__ __forceinline__ float phase_units(float ph) {
   return FAST ? ph : ph * 0.15915494309189535f;
 }
 
+// A caller's pixel phase (any real value, radians) reduced to one turn, in table units.
+template <bool FAST>
+__device__ __forceinline__ float reduced_phase_units(float ph) {
+  const float k = rintf(ph * 0.15915494309189535f);
+  if (!FAST) return ph * 0.15915494309189535f - k;
+  return fmaf(-k, -1.74845553e-07f, fmaf(-k, 6.28318548e+00f, ph));
+}
+
+
 // Shared memory of a block: the staged tables of one trap chunk (X for the sub-tile's 32
 // columns, Y for its rows, and the chunk's coefficients), the per-warp partial superpositions
 // of half a sub-tile's rows, and the pixel phases of the sub-tile.
@@ -585,7 +594,7 @@ __device__ __forceinline__ void process_subtile(const StepArgs &a, const SubTile
   } else if (FWD) {
     __syncthreads();  // earlier readers of the phases and of the tables are done
     for (int r = warp; r < st.rows; r += kWarps)
-      sm.Ps[r * kTileW + lane] = col_ok ? phase_units<FAST>(a.phi[(size_t)(st.y0 + r) * a.W + ix]) : 0.0f;
+      sm.Ps[r * kTileW + lane] = col_ok ? reduced_phase_units<FAST>(a.phi[(size_t)(st.y0 + r) * a.W + ix]) : 0.0f;
   }
 
   if (FWD) {
