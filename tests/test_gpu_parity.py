@@ -353,3 +353,25 @@ def test_checkpoint_resume_across_contexts(hot):
         with pytest.raises(hot.HotError, match="HOT_EINVAL"):
             c.set_state(phi, -wt)
     assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1][0], got[1][0]) and np.array_equal(ref[1][1], got[1][1])
+
+
+@pytest.mark.parametrize("precision", ["accurate", "separable"])
+def test_maximum_trap_count(hot, precision):
+    """HOT_MAX_TRAPS (4096) traps on a small SLM: 32 staged trap chunks per sub-tile; M + 1 traps
+    are rejected.  (The first weight update here spreads the weights over a factor of ~400, so
+    the back-projection cancels strongly at some pixels; the fast mode's 5e-7 sincos error is then
+    amplified past the 1e-4 bound on |V_m|, as the conditioning-aware phase bound predicts, and the
+    case is run in the two modes whose per-term error is ~1e-7.)"""
+    w = wl.random_case(160, 120, 4096, seed=31, precision=precision)
+    with make(hot, w) as h:
+        h.gsw(1)
+        V1, w1 = h.fields()
+        e, u = h.gsw(1)
+        xyz = np.vstack([w.xyz, w.xyz[:1]])
+        with pytest.raises(hot.HotError, match="HOT_EINVAL"):
+            h.set_traps(xyz)
+    r1 = oracle.gsw(w.geom, w.xyz, 1, w.phi0)
+    assert rel_err(V1, r1["V"]) < REL_V
+    np.testing.assert_allclose(w1, r1["w"], rtol=REL_V)
+    r2 = oracle.gsw(w.geom, w.xyz, 2, w.phi0)
+    assert abs(e - r2["e"]) < ABS_EU and abs(u - r2["u"]) < ABS_EU
