@@ -1255,6 +1255,10 @@ struct Tiling {
   bool operator==(const Tiling &o) const { return rows == o.rows && bps == o.bps && chunk == o.chunk; }
 };
 
+// The kernels are launch-bounded to at most 4 resident blocks per SM; a candidate above what
+// the current staging chunk leaves room for is clamped to it by the schedule.
+constexpr int kMaxBlocksPerSm = 4;
+
 // Coordinate search: each parameter in turn takes the fastest of its candidates with the
 // others fixed; a candidate replaces the incumbent only if it is more than 1 % faster; at
 // most two passes.  apply(t) installs a tiling, time(&us) measures it.  Leaves `best` applied.
@@ -1385,7 +1389,7 @@ int hot_autotune(hot_ctx *c, int iters, int *rows, int *blocks_per_sm, int *chun
   Tiling best = {c->tile_rows, c->sched_bps, c->tile_chunk};
   double best_us = 0;
   rc = tune_tiling(
-      c->sched_bps_max, best, best_us,
+      kMaxBlocksPerSm, best, best_us,
       [&](const Tiling &t) { return hot_set_tiling(c, t.rows, t.bps, t.chunk); },
       [&](double *us) {
         return time_runs(c->st, iters, us, [&]() { return restore_state(c, saved, c->st); },
