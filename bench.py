@@ -590,6 +590,9 @@ def run_batch(args):
     from paper_0907_4027_gb300 import hot, workloads as wl
 
     ws = wl.batch64()
+    if args.precision:
+        for w in ws:
+            w.precision = args.precision
     stream = torch.cuda.current_stream()
     holos = [hot.Hologram.from_workload(w, stream.cuda_stream) for w in ws]
     K = ws[0].iters
@@ -643,7 +646,7 @@ def run_batch(args):
         "value": len(ws) / (batch_ms * 1e-3), "unit": "holograms/s", "n_gpus": 1, "steps": reps,
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch64: 64 holograms, sizes from {512^2, 1024^2, 1920x1152}, M ~ U{8..2000}, "
-                               "30 GSW iterations in one CUDA graph, fast sincos", "seed": 0},
+                               f"30 GSW iterations in one CUDA graph, {ws[0].precision} mode", "seed": 0},
         "batch": {"ms": batch_ms, "updates_per_s": pairs / (batch_ms * 1e-3),
                   "latency_ms_p50": float(np.percentile(lat, 50)),
                   "latency_ms_p99": float(np.percentile(lat, 99)),

@@ -243,7 +243,8 @@ int hot_autotune(hot_ctx *c, int iters, int *rows, int *blocks_per_sm, int *chun
  * context's buffers); the iteration is the same as hot_gsw's (Sec. 3). */
 typedef struct hot_batch hot_batch;
 
-/* Groups count >= 1 contexts (same device, traps set, same precision mode) into a batch
+/* Groups count >= 1 contexts (same device, traps set, same precision mode, not row bands)
+ * into a batch
  * queued on cuda_stream (NULL: the legacy stream).  The batch refers to the contexts'
  * buffers: recreate it after hot_set_traps changes a trap count, and destroy it before
  * destroying its contexts.  The contexts must not be used concurrently with the batch. */

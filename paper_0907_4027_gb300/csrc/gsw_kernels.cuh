@@ -36,6 +36,7 @@ constexpr int kRowsMax = 14;    // rows per sub-tile (each lane keeps one field 
 constexpr int kYStride = (kRowsMax + 3) & ~3;  // floats per trap in the staged row table (16-byte rows)
 constexpr int kChunk = 128;     // traps whose tables are staged in shared memory at once
 constexpr float kTwoPi = 6.283185307179586f;
+constexpr int kModeAccurate = 0, kModeFast = 1, kModeSeparable = 2;  // kernel variants
 
 // Work decomposition: the image is cut into 32-pixel-wide column strips; each strip's rows
 // are dealt out as contiguous runs to a fixed number of resident blocks (one wave), so that
@@ -644,60 +645,6 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
   if (gsw) write_weights(a, lw, gridDim.x, mean);
 }
 
-// Batched launch: the sub-tiles of up to kBatchMax holograms (SubTile::pad = hologram index)
-// in one grid.  The holograms' parameters travel in the launch itself (a __grid_constant__
-// argument read through the constant cache, as the single-hologram kernel reads its own).
-// Every block that meets a hologram computes its <|V|> and coefficients itself; the weights
-// of hologram h are written by block owner[h].
-constexpr int kBatchMax = 24;  // keeps the launch argument under 4 KB
-
-struct BatchArgs {
-  StepArgs holo[kBatchMax];
-  int owner[kBatchMax];
-  const SubTile *sub;
-  const int *first;  // [gridDim.x + 1]
-  int count;
-};
-static_assert(sizeof(BatchArgs) <= 4096, "launch argument above 4 KB");
-
-template <bool FAST, bool BACK, bool FWD>
-__global__ void __launch_bounds__(kThreads, 4) gsw_batch_kernel(const __grid_constant__ BatchArgs b) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const StepSmem sm(smem_raw);
-  const int t_begin = b.first[blockIdx.x], t_end = b.first[blockIdx.x + 1];
-
-  allow_dependents();
-  bool prestaged = false;
-  if (BACK && t_begin < t_end) {
-    const SubTile st0 = b.sub[t_begin];
-    const StepArgs &a0 = b.holo[st0.pad];
-    stage_tables<false>(a0, 0, a0.M < a0.chunk ? a0.M : a0.chunk, st0, sm.Xs, sm.Ys, sm.Cs);
-    prestaged = true;
-  }
-  grid_dependency_wait();
-  if (FWD)  // clear the buffers the next launch accumulates into, for every hologram
-    for (int h = 0; h < b.count; h++) {
-      unsigned long long *clr = b.holo[h].acc_clear;
-      const int n2 = 2 * b.holo[h].M;
-      for (int i = blockIdx.x * kThreads + threadIdx.x; i < n2; i += gridDim.x * kThreads) clr[i] = 0ull;
-    }
-  int cur = -1;
-  float mean = 0.f;
-  LateWeight lw;  // the owner block writes all weights of a hologram, after its sub-tiles
-  for (int t = t_begin; t < t_end; t++) {
-    const SubTile st = b.sub[t];
-    const StepArgs &a = b.holo[st.pad];
-    if (BACK && st.pad != cur) {
-      if (cur >= 0) write_weights(b.holo[cur], lw, 1, mean);
-      const int mc = a.M < a.chunk ? a.M : a.chunk;
-      mean = gsw_prologue<false>(a, mc, sm.C0, b.owner[st.pad] == (int)blockIdx.x ? 0 : a.M, 1, lw);
-    }
-    cur = st.pad;
-    process_subtile<FAST, BACK, FWD, false>(a, st, mean, prestaged, sm, BACK ? sm.C0 : nullptr);
-  }
-  if (BACK && cur >= 0) write_weights(b.holo[cur], lw, 1, mean);
-}
-
 // Start stamp of a batched sequence (%globaltimer, ns).
 __global__ void stamp_kernel(unsigned long long *t) { *t = global_timer_ns(); }
 
@@ -939,6 +886,74 @@ __global__ void __launch_bounds__(kThreads, 2) gsw_sep_kernel(StepArgs a) {
   if (gsw) write_weights(a, lw, gridDim.x, mean);
 }
 
+// Batched launch: the sub-tiles of up to kBatchMax holograms (SubTile::pad = hologram index)
+// in one grid.  The holograms' parameters travel in the launch itself (a __grid_constant__
+// argument read through the constant cache, as the single-hologram kernel reads its own).
+// Every block that meets a hologram computes its <|V|> and coefficients itself; the weights
+// of hologram h are written by block owner[h].
+constexpr int kBatchMax = 24;  // keeps the launch argument under 4 KB
+
+struct BatchArgs {
+  StepArgs holo[kBatchMax];
+  int owner[kBatchMax];
+  const SubTile *sub;
+  const int *first;  // [gridDim.x + 1]
+  int count;
+};
+static_assert(sizeof(BatchArgs) <= 4096, "launch argument above 4 KB");
+
+// MODE: kModeAccurate, kModeFast or kModeSeparable (the separable kernel's staging capacity is
+// the batch's chunk, the same for all holograms of a launch).
+template <int MODE, bool BACK, bool FWD>
+__global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)
+    gsw_batch_kernel(const __grid_constant__ BatchArgs b) {
+  constexpr bool FAST = MODE == kModeFast, SEP = MODE == kModeSeparable;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int t_begin = b.first[blockIdx.x], t_end = b.first[blockIdx.x + 1];
+  const int cap = b.holo[0].chunk;
+  float2 *const C0 = SEP ? SepSmem(smem_raw, cap).C0 : StepSmem(smem_raw).C0;
+
+  allow_dependents();
+  bool prestaged = false;
+  if (BACK && t_begin < t_end) {
+    const SubTile st0 = b.sub[t_begin];
+    const StepArgs &a0 = b.holo[st0.pad];
+    const int mc0 = a0.M < a0.chunk ? a0.M : a0.chunk;
+    if constexpr (SEP) {
+      stage_sep<false>(a0, 0, mc0, st0, SepSmem(smem_raw, cap));
+    } else {
+      const StepSmem sm(smem_raw);
+      stage_tables<false>(a0, 0, mc0, st0, sm.Xs, sm.Ys, sm.Cs);
+    }
+    prestaged = true;
+  }
+  grid_dependency_wait();
+  if (FWD)  // clear the buffers the next launch accumulates into, for every hologram
+    for (int h = 0; h < b.count; h++) {
+      unsigned long long *clr = b.holo[h].acc_clear;
+      const int n2 = 2 * b.holo[h].M;
+      for (int i = blockIdx.x * kThreads + threadIdx.x; i < n2; i += gridDim.x * kThreads) clr[i] = 0ull;
+    }
+  int cur = -1;
+  float mean = 0.f;
+  LateWeight lw;  // the owner block writes all weights of a hologram, after its sub-tiles
+  for (int t = t_begin; t < t_end; t++) {
+    const SubTile st = b.sub[t];
+    const StepArgs &a = b.holo[st.pad];
+    if (BACK && st.pad != cur) {
+      if (cur >= 0) write_weights(b.holo[cur], lw, 1, mean);
+      const int mc = a.M < a.chunk ? a.M : a.chunk;
+      mean = gsw_prologue<SEP>(a, mc, C0, b.owner[st.pad] == (int)blockIdx.x ? 0 : a.M, 1, lw);
+    }
+    cur = st.pad;
+    if constexpr (SEP)
+      process_subtile_sep<BACK, FWD, false>(a, st, mean, prestaged, SepSmem(smem_raw, cap), BACK ? C0 : nullptr);
+    else
+      process_subtile<FAST, BACK, FWD, false>(a, st, mean, prestaged, StepSmem(smem_raw), BACK ? C0 : nullptr);
+  }
+  if (BACK && cur >= 0) write_weights(b.holo[cur], lw, 1, mean);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Persistent form: all launches of a hot_gsw call (the forward field of the starting phases and
 // iterations 1..K) in one cooperative launch whose blocks are all resident, separated by a
@@ -1005,8 +1020,6 @@ struct PersistArgs {
   GridSync sync;
   float *trace;  // NULL, or [iters][2]: e, u of the field read by iteration k (convergence trace)
 };
-
-constexpr int kModeAccurate = 0, kModeFast = 1, kModeSeparable = 2;
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)

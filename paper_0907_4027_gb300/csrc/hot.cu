@@ -1025,11 +1025,44 @@ struct hot_batch {
 
 namespace {
 
-template <bool FAST>
+int batch_mode(const hot_batch *b) {
+  return b->precision == HOT_PREC_SEPARABLE ? hot::kModeSeparable
+                                            : b->precision == HOT_PREC_FAST ? hot::kModeFast : hot::kModeAccurate;
+}
+
+// Dynamic shared memory of the batch kernels: the separable one stages `chunk` complex traps.
+int batch_smem(const hot_batch *b) {
+  return b->precision == HOT_PREC_SEPARABLE ? hot::sep_smem_bytes(b->chunk) : hot::step_smem_bytes(0, true);
+}
+
+template <int MODE>
 int batch_set_smem() {
-  const int bytes = hot::step_smem_bytes(0, true);
-  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_batch_kernel<FAST, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_batch_kernel<FAST, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  const int bytes = MODE == hot::kModeSeparable ? hot::sep_smem_bytes(hot::kChunk) : hot::step_smem_bytes(0, true);
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_batch_kernel<MODE, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_batch_kernel<MODE, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  return HOT_OK;
+}
+
+// Resident blocks per SM of the batch's fused kernel at its current staging chunk.
+int batch_occupancy(hot_batch *b) {
+  int per_sm = 0;
+  const int smem = batch_smem(b);
+  cudaError_t e;
+  switch (batch_mode(b)) {
+    case hot::kModeSeparable:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_batch_kernel<hot::kModeSeparable, true, true>,
+                                                        hot::kThreads, smem);
+      break;
+    case hot::kModeFast:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_batch_kernel<hot::kModeFast, true, true>,
+                                                        hot::kThreads, smem);
+      break;
+    default:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_batch_kernel<hot::kModeAccurate, true, true>,
+                                                        hot::kThreads, smem);
+  }
+  if (e != cudaSuccess) return fail(HOT_ECUDA, "batch occupancy query: %s", cudaGetErrorString(e));
+  b->per_sm_max = per_sm < 1 ? 1 : per_sm;
   return HOT_OK;
 }
 
@@ -1064,6 +1097,8 @@ hot::StepArgs step_args(const hot_ctx *c, int k, int chunk) {
   a.chunk = chunk;
   a.X = fast ? c->Xr : c->Xt;
   a.Y = fast ? c->Yr : c->Yt;
+  a.Xc = c->Xc;
+  a.Yc = c->Yc;
   a.phi = c->phi;
   a.acc_in = c->acc + M2 * ((k + 2) % 3);
   a.acc_out = c->acc + M2 * (k % 3);
@@ -1167,6 +1202,8 @@ int build_group(hot_batch *b, hot_batch::Group &g) {
 int batch_schedule(hot_batch *b) {
   HOT_CUDA(cudaStreamSynchronize(b->st));
   batch_drop_graphs(b);
+  const int rc0 = batch_occupancy(b);
+  if (rc0 != HOT_OK) return rc0;
   for (auto &g : b->groups) group_free(g);
   b->groups.clear();
   b->ran = false;
@@ -1201,7 +1238,7 @@ int batch_schedule(hot_batch *b) {
   return HOT_OK;
 }
 
-template <bool FAST, bool BACK>
+template <int MODE, bool BACK>
 int batch_launch(hot_batch *b, const hot_batch::Group &g, int k, bool pdl) {
   hot::BatchArgs a = {};
   const int count = (int)g.members.size();
@@ -1214,7 +1251,7 @@ int batch_launch(hot_batch *b, const hot_batch::Group &g, int k, bool pdl) {
   a.count = count;
   hot_ctx tmp;  // launch() needs a context only for the stream
   tmp.st = b->st;
-  launch(&tmp, hot::gsw_batch_kernel<FAST, BACK, true>, g.grid, hot::kThreads, hot::step_smem_bytes(0, true), pdl, a);
+  launch(&tmp, hot::gsw_batch_kernel<MODE, BACK, true>, g.grid, hot::kThreads, batch_smem(b), pdl, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(HOT_ECUDA, "launch of gsw_batch_kernel: %s", cudaGetErrorString(e));
   return HOT_OK;
@@ -1222,16 +1259,23 @@ int batch_launch(hot_batch *b, const hot_batch::Group &g, int k, bool pdl) {
 
 // A start stamp, then the groups in order: forward field of the starting phases (k = 0),
 // iterations 1..iters, and the per-hologram finalize with its completion stamp.
+template <bool BACK>
+int batch_launch_mode(hot_batch *b, const hot_batch::Group &g, int k, bool pdl) {
+  switch (batch_mode(b)) {
+    case hot::kModeSeparable: return batch_launch<hot::kModeSeparable, BACK>(b, g, k, pdl);
+    case hot::kModeFast: return batch_launch<hot::kModeFast, BACK>(b, g, k, pdl);
+    default: return batch_launch<hot::kModeAccurate, BACK>(b, g, k, pdl);
+  }
+}
+
 int batch_enqueue(hot_batch *b, int iters) {
-  const bool fast = b->precision == HOT_PREC_FAST;
   hot::stamp_kernel<<<1, 1, 0, b->st>>>(b->stamps + b->count);
   cudaError_t e0 = cudaGetLastError();
   if (e0 != cudaSuccess) return fail(HOT_ECUDA, "launch of stamp_kernel: %s", cudaGetErrorString(e0));
   for (size_t gi = 0; gi < b->groups.size(); gi++) {
     const hot_batch::Group &g = b->groups[gi];
-    int rc = fast ? batch_launch<true, false>(b, g, 0, true) : batch_launch<false, false>(b, g, 0, true);
-    for (int k = 1; k <= iters && rc == HOT_OK; k++)
-      rc = fast ? batch_launch<true, true>(b, g, k, true) : batch_launch<false, true>(b, g, k, true);
+    int rc = batch_launch_mode<false>(b, g, 0, true);
+    for (int k = 1; k <= iters && rc == HOT_OK; k++) rc = batch_launch_mode<true>(b, g, k, true);
     if (rc != HOT_OK) return rc;
     hot_ctx tmp;
     tmp.st = b->st;
@@ -1417,8 +1461,8 @@ int hot_batch_create(hot_batch **out, int count, hot_ctx *const *ctxs, void *cud
     if (!ctxs[i]->M) return fail(HOT_ESTATE, "hot_batch_create: context %d has no traps", i);
     if (ctxs[i]->precision != ctxs[0]->precision)
       return fail(HOT_EINVAL, "hot_batch_create: contexts differ in precision mode");
-    if (ctxs[i]->precision == HOT_PREC_SEPARABLE)
-      return fail(HOT_EINVAL, "hot_batch_create: the separable mode is not batched");
+    if (ctxs[i]->H_total != ctxs[i]->H)
+      return fail(HOT_EINVAL, "hot_batch_create: context %d is a row band (its sums need an exchange)", i);
     if (ctxs[i]->dev != ctxs[0]->dev) return fail(HOT_EINVAL, "hot_batch_create: contexts on different devices");
     for (int j = 0; j < i; j++)
       if (ctxs[j] == ctxs[i]) return fail(HOT_EINVAL, "hot_batch_create: context %d given twice", i);
@@ -1430,19 +1474,11 @@ int hot_batch_create(hot_batch **out, int count, hot_ctx *const *ctxs, void *cud
   b->st = static_cast<cudaStream_t>(cuda_stream);
   b->precision = ctxs[0]->precision;
   b->dev = ctxs[0]->dev;
-  const bool fast = b->precision == HOT_PREC_FAST;
-  int rc = fast ? batch_set_smem<true>() : batch_set_smem<false>();
+  int rc = batch_mode(b) == hot::kModeSeparable ? batch_set_smem<hot::kModeSeparable>()
+           : batch_mode(b) == hot::kModeFast    ? batch_set_smem<hot::kModeFast>()
+                                                : batch_set_smem<hot::kModeAccurate>();
   if (rc == HOT_OK && cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev) != cudaSuccess)
     rc = fail(HOT_ECUDA, "hot_batch_create: device query failed");
-  if (rc == HOT_OK) {
-    int per_sm = 0;
-    cudaError_t e = fast ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_batch_kernel<true, true, true>,
-                                                                        hot::kThreads, hot::step_smem_bytes(0, true))
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_batch_kernel<false, true, true>,
-                                                                        hot::kThreads, hot::step_smem_bytes(0, true));
-    if (e != cudaSuccess) rc = fail(HOT_ECUDA, "hot_batch_create: occupancy query: %s", cudaGetErrorString(e));
-    b->per_sm_max = per_sm < 1 ? 1 : per_sm;
-  }
   if (rc == HOT_OK) rc = dalloc(&b->stamps, (size_t)count + 1);
   if (rc == HOT_OK) rc = batch_schedule(b);
   if (rc != HOT_OK) {
@@ -1534,7 +1570,7 @@ int hot_batch_autotune(hot_batch *b, int iters, int *rows, int *blocks_per_sm, i
   double best_us = 0;
   const double gp = b->group_pairs;
   rc = tune_tiling(
-      b->per_sm_max, best, best_us, [&](const Tiling &t) { return hot_batch_set_tiling(b, t.rows, t.bps, t.chunk, gp); },
+      kMaxBlocksPerSm, best, best_us, [&](const Tiling &t) { return hot_batch_set_tiling(b, t.rows, t.bps, t.chunk, gp); },
       [&](double *us) { return time_runs(b->st, iters, us, restore, [&]() { return hot_batch_gsw(b, iters); }); });
   const int rc2 = restore();
   cudaStreamSynchronize(b->st);

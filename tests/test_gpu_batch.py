@@ -66,7 +66,7 @@ def run_batch(hot, ws, configure=None):
     return out, lat, tiling
 
 
-@pytest.mark.parametrize("precision", ["accurate", "fast"])
+@pytest.mark.parametrize("precision", ["accurate", "fast", "separable"])
 def test_batch_matches_single_runs_and_oracle(hot, precision):
     ws = cases(precision)
     got, _, _ = run_batch(hot, ws)
@@ -128,9 +128,10 @@ def test_tiling_matches_oracle(hot, tiling):
     check_against_oracle(w, V1, w1, eu)
 
 
+@pytest.mark.parametrize("precision", ["accurate", "separable"])
 @pytest.mark.parametrize("tiling", [(5, 2, 16), (14, 1, 128)])
-def test_batch_tiling_matches_oracle(hot, tiling):
-    ws = cases("accurate")
+def test_batch_tiling_matches_oracle(hot, tiling, precision):
+    ws = cases(precision)
     got, _, t = run_batch(hot, ws, lambda b: b.set_tiling(*tiling))
     assert (t["rows"], t["chunk"]) == (tiling[0], tiling[2])
     for w, (V, wt, eu, _) in zip(ws, got):
@@ -186,8 +187,10 @@ def test_batch_autotune_keeps_state(hot):
         check_against_oracle(w, V, wt, eu)
 
 
-def test_separable_mode_is_not_batched(hot):
-    w = wl.random_case(64, 32, 5, seed=1, precision="separable")
-    with hot.Hologram.from_workload(w) as h:
+def test_row_bands_are_not_batched(hot):
+    w = wl.random_case(64, 32, 5, seed=1, precision="fast")
+    with hot.Hologram(w.W, 16, w.pitch, w.wavelength, w.focal, precision="fast") as h:
+        h.set_band(32, 16)
+        h.set_traps(w.xyz)
         with pytest.raises(hot.HotError, match="HOT_EINVAL"):
             hot.Batch([h]).close()
