@@ -395,13 +395,15 @@ def run_engine(args):
 def run_adam(args):
     """Differentiable form (diff256_1024): Adam on the phases for the trap-intensity loss
     L = -sum log|V_m|^2 + 10 var|V_m|^2 through the autograd Function (forward field and
-    adjoint kernels), 200 steps, lr 1e-2; compared with plain GSW on the same traps and phi0."""
+    adjoint kernels), 200 steps, lr 1.0; compared with plain GSW on the same traps and phi0."""
     import torch
     from paper_0907_4027_gb300 import _build
     _build.build()
     from paper_0907_4027_gb300 import autograd as ag, hot, workloads as wl
 
     w = wl.NAMED[args.workload]()
+    if args.precision:
+        w.precision = args.precision
     stream = torch.cuda.current_stream()
     h = hot.Hologram(w.W, w.H, w.pitch, w.wavelength, w.focal, stream.cuda_stream, w.precision)
     h.set_traps(w.xyz, w.w0)
@@ -412,7 +414,7 @@ def run_adam(args):
 
     def adam_run(n_steps, timed):
         phi = torch.tensor(w.phi0, dtype=torch.float32, device="cuda", requires_grad=True)
-        opt = torch.optim.Adam([phi], lr=1e-2)
+        opt = torch.optim.Adam([phi], lr=1.0)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record(stream)
         for _ in range(n_steps):
@@ -448,8 +450,8 @@ def run_adam(args):
         "unit": "steps/s", "n_gpus": 1, "steps": w.iters, "warmup": 3, "ms_per_step": ms / w.iters,
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{w.name}: {w.W}x{w.H} px, M={w.M} traps, {w.iters} Adam steps on the phases, "
-                               f"{w.precision} sincos", "W": w.W, "H": w.H, "M": w.M, "steps": w.iters,
-                   "precision": w.precision, "seed": 0, "optimizer": "Adam lr 1e-2 (torch defaults otherwise)"},
+                               f"{w.precision} mode", "W": w.W, "H": w.H, "M": w.M, "steps": w.iters,
+                   "precision": w.precision, "seed": 0, "optimizer": "Adam lr 1.0 (the best of 1e-2, 3e-2, 0.1, 0.3, 1.0 for this loss; torch defaults otherwise)"},
         "final": {"loss": loss, "e": e, "u": u, "ms_total": ms},
         "gsw_same_traps": {str(k): v for k, v in gsw.items()},
     }
