@@ -321,24 +321,26 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
 
 // Weight update a thread writes after its block's work (prefetched in the prologue).
 struct LateWeight {
-  int m;     // first trap (m >= M: none)
+  int own;   // the block's first trap (own + stride * t for thread t); >= M: the block owns none
+  int m;     // this thread's first trap (m >= M: none)
   float2 v;  // its field
   float w;   // its weight before the update
+  ff part;   // this thread's share of sum_m |V_m| (traps t, t + kThreads, ...)
 };
 
 // Start of a GSW step: the previous forward's fields are read once, every load issued before
-// any is used.  Returns <|V|> (mean of |V_m| over the traps, Sec. 3) computed by every block in
-// the same fixed order (thread-strided float-float sums, warp shuffles, warps in order), so
-// that all blocks obtain the same value bit for bit; writes the coefficients of traps
-// [0, mc) into C0 (polar, or complex when COMPLEX); and prefetches into lw the weight of trap
-// own + stride * threadIdx.x, which write_weights stores after the block's work.
+// any is used.  Writes the coefficients of traps [0, mc) into C0 (polar, or complex when
+// COMPLEX) without the factor <|V|> of the weight update: a factor common to all coefficients
+// scales S_j and leaves arg S_j unchanged (the weights' global scale is free, reading R6), so
+// no block-wide reduction stands between the sums and the back-projection.  Keeps in lw the
+// thread's share of sum |V_m| and the prefetched weight of trap own + stride * threadIdx.x,
+// which write_weights completes after the block's work.
 // trace: NULL, or where block 0 writes e and u (Eq. 4) of the fields it read (convergence trace).
 template <bool COMPLEX>
-__device__ __forceinline__ float gsw_prologue(const StepArgs &a, int mc, float2 *C0, int own, int stride,
-                                              LateWeight &lw, float *trace = nullptr) {
-  __shared__ ff part[kWarps];
-  __shared__ float ext[2][kWarps];
+__device__ __forceinline__ void gsw_prologue(const StepArgs &a, int mc, float2 *C0, int own, int stride,
+                                             LateWeight &lw, float *trace = nullptr) {
   const int t = threadIdx.x;
+  lw.own = own;
   lw.m = own + stride * t;
   lw.v = make_float2(0.f, 0.f);
   lw.w = 0.f;
@@ -363,35 +365,28 @@ __device__ __forceinline__ float gsw_prologue(const StepArgs &a, int mc, float2 
       mn = fminf(mn, I);
     }
   }
-#pragma unroll
-  for (int o = 16; o; o >>= 1)
-    s = ff_add(s, {__shfl_down_sync(0xffffffffu, s.hi, o), __shfl_down_sync(0xffffffffu, s.lo, o)});
-  __syncthreads();
-  if ((t & 31) == 0) part[t >> 5] = s;
-  __syncthreads();
-  ff q = part[0];
-#pragma unroll
-  for (int i = 1; i < kWarps; i++) q = ff_add(q, part[i]);
-  const float mean = (q.hi + q.lo) / (float)a.M;
+  lw.part = s;
+  if (t < mc) C0[t] = update_from<COMPLEX>(v0, w0, 1.f, a.angle_units);
   if (tr) {  // block 0 only: e = sum I_m, u = 1 - (max - min)/(max + min) of the fields read
+    __shared__ ff tpart[kWarps];
+    __shared__ float ext[2][kWarps];
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       si = ff_add(si, {__shfl_down_sync(0xffffffffu, si.hi, o), __shfl_down_sync(0xffffffffu, si.lo, o)});
       mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
       mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, o));
     }
-    __syncthreads();  // every thread has read part[] above
     if ((t & 31) == 0) {
-      part[t >> 5] = si;
+      tpart[t >> 5] = si;
       ext[0][t >> 5] = mx;
       ext[1][t >> 5] = mn;
     }
     __syncthreads();
     if (t == 0) {
-      ff e = part[0];
+      ff e = tpart[0];
       float hi = ext[0][0], lo = ext[1][0];
       for (int i = 1; i < kWarps; i++) {
-        e = ff_add(e, part[i]);
+        e = ff_add(e, tpart[i]);
         hi = fmaxf(hi, ext[0][i]);
         lo = fminf(lo, ext[1][i]);
       }
@@ -399,12 +394,26 @@ __device__ __forceinline__ float gsw_prologue(const StepArgs &a, int mc, float2 
       trace[1] = (hi + lo > 0.f) ? 1.f - (hi - lo) / (hi + lo) : 0.f;
     }
   }
-  if (t < mc) C0[t] = update_from<COMPLEX>(v0, w0, mean, a.angle_units);
-  return mean;
 }
 
-// The weight updates prefetched by gsw_prologue (traps lw.m, lw.m + stride * kThreads, ...).
-__device__ __forceinline__ void write_weights(const StepArgs &a, const LateWeight &lw, int stride, float mean) {
+// After the block's work, in blocks that own weights (a block-uniform condition): <|V|> (mean
+// of |V_m| over the traps, Sec. 3) from the threads' shares in one fixed order (warp
+// shuffles, warps in order), so every such block obtains the same bits, and the block's
+// weight updates w_m <- w_m <|V|>/|V_m| (traps lw.m, lw.m + stride * kThreads, ...).
+__device__ __forceinline__ void write_weights(const StepArgs &a, const LateWeight &lw, int stride) {
+  if (lw.own >= a.M) return;
+  __shared__ ff part[kWarps];
+  ff s = lw.part;
+#pragma unroll
+  for (int o = 16; o; o >>= 1)
+    s = ff_add(s, {__shfl_down_sync(0xffffffffu, s.hi, o), __shfl_down_sync(0xffffffffu, s.lo, o)});
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  ff q = part[0];
+#pragma unroll
+  for (int i = 1; i < kWarps; i++) q = ff_add(q, part[i]);
+  const float mean = (q.hi + q.lo) / (float)a.M;
   if (lw.m < a.M) a.w_out[lw.m] = update_from<false>(lw.v, lw.w, mean, 1.f).x;
   for (int m = lw.m + stride * kThreads; m < a.M; m += stride * kThreads)
     a.w_out[m] = update_from<false>(field_from_sums(a, m), __ldcg(a.w_in + m), mean, 1.f).x;
@@ -636,13 +645,12 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
   grid_dependency_wait();
   if (FWD)  // the buffer the next launch accumulates into
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
-  float mean = 0.f;
   LateWeight lw;
   const bool gsw = BACK && !ADJ && !a.G;
-  if (gsw) mean = gsw_prologue<false>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, a.trace);
+  if (gsw) gsw_prologue<false>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, a.trace);
   for (int t = t_begin; t < t_end; t++)
-    process_subtile<FAST, BACK, FWD, ADJ>(a, a.sub[t], mean, prestaged, sm, gsw ? sm.C0 : nullptr);
-  if (gsw) write_weights(a, lw, gridDim.x, mean);
+    process_subtile<FAST, BACK, FWD, ADJ>(a, a.sub[t], 1.f, prestaged, sm, gsw ? sm.C0 : nullptr);
+  if (gsw) write_weights(a, lw, gridDim.x);
 }
 
 // Start stamp of a batched sequence (%globaltimer, ns).
@@ -877,13 +885,12 @@ __global__ void __launch_bounds__(kThreads, 2) gsw_sep_kernel(StepArgs a) {
   grid_dependency_wait();
   if (FWD)
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
-  float mean = 0.f;
   LateWeight lw;
   const bool gsw = BACK && !ADJ && !a.G;
-  if (gsw) mean = gsw_prologue<true>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, a.trace);
+  if (gsw) gsw_prologue<true>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, a.trace);
   for (int t = t_begin; t < t_end; t++)
-    process_subtile_sep<BACK, FWD, ADJ>(a, a.sub[t], mean, prestaged, sm, gsw ? sm.C0 : nullptr);
-  if (gsw) write_weights(a, lw, gridDim.x, mean);
+    process_subtile_sep<BACK, FWD, ADJ>(a, a.sub[t], 1.f, prestaged, sm, gsw ? sm.C0 : nullptr);
+  if (gsw) write_weights(a, lw, gridDim.x);
 }
 
 // Batched launch: the sub-tiles of up to kBatchMax holograms (SubTile::pad = hologram index)
@@ -935,23 +942,22 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)
       for (int i = blockIdx.x * kThreads + threadIdx.x; i < n2; i += gridDim.x * kThreads) clr[i] = 0ull;
     }
   int cur = -1;
-  float mean = 0.f;
   LateWeight lw;  // the owner block writes all weights of a hologram, after its sub-tiles
   for (int t = t_begin; t < t_end; t++) {
     const SubTile st = b.sub[t];
     const StepArgs &a = b.holo[st.pad];
     if (BACK && st.pad != cur) {
-      if (cur >= 0) write_weights(b.holo[cur], lw, 1, mean);
+      if (cur >= 0) write_weights(b.holo[cur], lw, 1);
       const int mc = a.M < a.chunk ? a.M : a.chunk;
-      mean = gsw_prologue<SEP>(a, mc, C0, b.owner[st.pad] == (int)blockIdx.x ? 0 : a.M, 1, lw);
+      gsw_prologue<SEP>(a, mc, C0, b.owner[st.pad] == (int)blockIdx.x ? 0 : a.M, 1, lw);
     }
     cur = st.pad;
     if constexpr (SEP)
-      process_subtile_sep<BACK, FWD, false>(a, st, mean, prestaged, SepSmem(smem_raw, cap), BACK ? C0 : nullptr);
+      process_subtile_sep<BACK, FWD, false>(a, st, 1.f, prestaged, SepSmem(smem_raw, cap), BACK ? C0 : nullptr);
     else
-      process_subtile<FAST, BACK, FWD, false>(a, st, mean, prestaged, StepSmem(smem_raw), BACK ? C0 : nullptr);
+      process_subtile<FAST, BACK, FWD, false>(a, st, 1.f, prestaged, StepSmem(smem_raw), BACK ? C0 : nullptr);
   }
-  if (BACK && cur >= 0) write_weights(b.holo[cur], lw, 1, mean);
+  if (BACK && cur >= 0) write_weights(b.holo[cur], lw, 1);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1036,11 +1042,11 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)
     const StepArgs &a = p.step[k % 6];
     if (k > 0 && !grid_sync(p.sync, epoch)) return;
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
-    float mean = 0.f;
+    const float mean = 1.f;  // coefficients without the common factor <|V|> (see gsw_prologue)
     LateWeight lw;
     if constexpr (MODE == kModeSeparable) {
       const SepSmem sm(smem_raw, mc);
-      if (k > 0) mean = gsw_prologue<true>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, p.trace ? p.trace + 2 * (k - 1) : nullptr);
+      if (k > 0) gsw_prologue<true>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, p.trace ? p.trace + 2 * (k - 1) : nullptr);
       for (int t = t_begin; t < t_end; t++) {
         bool prestaged = resident && k > 0;
         if (k == 0)
@@ -1050,7 +1056,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)
       }
     } else {
       const StepSmem sm(smem_raw);
-      if (k > 0) mean = gsw_prologue<false>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, p.trace ? p.trace + 2 * (k - 1) : nullptr);
+      if (k > 0) gsw_prologue<false>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, p.trace ? p.trace + 2 * (k - 1) : nullptr);
       for (int t = t_begin; t < t_end; t++) {
         bool prestaged = resident && k > 0;
         if (k == 0)
@@ -1059,7 +1065,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)
           process_subtile<FAST, true, true, false>(a, a.sub[t], mean, prestaged, sm, sm.C0);
       }
     }
-    if (k > 0) write_weights(a, lw, gridDim.x, mean);
+    if (k > 0) write_weights(a, lw, gridDim.x);
   }
 }
 
