@@ -192,10 +192,11 @@ int hot_set_band(hot_ctx *c, int total_height, int y0);
 /* The launch sequence of hot_gsw, one launch per call, for a caller that adds the partial
  * sums over the bands between launches (not captured as a graph):
  *   hot_sharded_begin(c)      launch 0: partial sums of V for the current phases;
- *   hot_sharded_sums(c, k, &p) DEVICE pointer to launch k's partial sums: int64 [2][M] (Re
- *                             parts, then Im parts; two's complement), to be replaced in
- *                             place, in stream order on the context's stream, by their sum over
- *                             all bands before the next launch;
+ *   hot_sharded_sums(c, k, &p, &n) DEVICE pointer to launch k's partial sums, n int64 values
+ *                             (copies x [2][M]: Re parts, then Im parts, two's complement; the
+ *                             field is their sum over the copies), to be replaced in place, in
+ *                             stream order on the context's stream, by their elementwise sum
+ *                             over all bands before the next launch;
  *   hot_sharded_step(c, k)    launch k = 1, 2, ...: weight update, back-projection of the band,
  *                             partial sums of the new forward field;
  *   hot_sharded_end(c, K, &e, &u) after launch K: the metrics (Eq. 4) and fields of the summed
@@ -203,7 +204,7 @@ int hot_set_band(hot_ctx *c, int total_height, int y0);
  * Launches are queued on the context's stream.  HOT_ESTATE for a call out of this order. */
 int hot_sharded_begin(hot_ctx *c);
 int hot_sharded_step(hot_ctx *c, int k);
-int hot_sharded_sums(hot_ctx *c, int k, void **sums_dev);
+int hot_sharded_sums(hot_ctx *c, int k, void **sums_dev, int *count);
 int hot_sharded_end(hot_ctx *c, int iters, double *eff_out, double *unif_out);
 
 /* Efficiency e and uniformity u (Eq. 4) of the last forward evaluation (hot_gsw, hot_field or
@@ -234,7 +235,7 @@ int hot_autotune(hot_ctx *c, int iters, int *rows, int *blocks_per_sm, int *chun
 /* ---- batches of holograms ------------------------------------------------------------------
  * A batch runs GSW on several contexts at once -- SLMs of different sizes and trap counts.
  * The holograms are ordered by their work per iteration (N x M pixel-trap pairs, smallest
- * first) and cut into groups of at least `group_pairs` pairs per iteration (and at most 24
+ * first) and cut into groups of at least `group_pairs` pairs per iteration (and at most 22
  * holograms: their parameters travel in the kernel launch); each group runs
  * its iterations with one kernel launch per iteration that covers all of its holograms (their
  * row segments are dealt out to one wave of blocks in equal shares of pairs), and the groups

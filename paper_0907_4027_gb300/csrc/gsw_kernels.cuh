@@ -49,6 +49,9 @@ struct SubTile {
 struct StepArgs {
   int W, H, M;
   int chunk;              // traps staged in shared memory at once (1..kChunk)
+  int copies;             // copies of each fixed-point accumulator buffer (a power of two; more than
+                          // one in the separable mode only): block b adds into copy b % copies,
+                          // spreading the atomics over more addresses
   const SubTile *sub;     // work schedule: sub-tiles
   const int *first;       // [gridDim.x + 1]: block b processes sub-tiles first[b] .. first[b+1]-1
   const float *X;         // [M][W] column phase parts (turns if accurate, radians if fast)
@@ -57,12 +60,12 @@ struct StepArgs {
   const float2 *Yc;       // [M][H] e^{i 2pi Y} (separable variant)
   float *phi;             // [H*W] pixel phases, radians
   // BACK: weight update and coefficients from the previous launch's forward field
-  const unsigned long long *acc_in;  // [2][M] fixed-point sums of the previous forward: Re, Im
+  const unsigned long long *acc_in;  // [copies][2][M] fixed-point sums of the previous forward: Re, Im
   const float *w_in;                 // [M] weights before this iteration's update
   float *w_out;                      // [M] updated weights (trap m written by block m % gridDim.x)
   // FWD: forward field of this launch's phases
-  unsigned long long *acc_out;       // [2][M] zero on entry (cleared by the launch before last)
-  unsigned long long *acc_clear;     // [2][M] cleared here for the next launch
+  unsigned long long *acc_out;       // [copies][2][M] zero on entry (cleared by the launch before last)
+  unsigned long long *acc_clear;     // [copies][2][M] cleared here for the next launch
   // Explicit coefficients G_m (Re, Im) instead of the GSW update (superposition, adjoint),
   // and the gradient output of the adjoint (ADJ)
   const float2 *G;                   // [M] or NULL: coefficients of the back-projection
@@ -143,10 +146,23 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
-// The field V_m of the previous forward, from its fixed-point sums.
+// The field V_m of the previous forward, from its fixed-point sums; MULTI: added over the
+// copies (integer addition, exact in any order).  The direct kernels run with one copy.
+template <bool MULTI = false>
 __device__ __forceinline__ float2 field_from_sums(const StepArgs &a, int m) {
-  const long long sr = (long long)__ldcg(a.acc_in + m), si = (long long)__ldcg(a.acc_in + a.M + m);
+  long long sr = (long long)__ldcg(a.acc_in + m), si = (long long)__ldcg(a.acc_in + a.M + m);
+  if (MULTI)
+#pragma unroll 7
+    for (int c = 1; c < a.copies; c++) {
+      sr += (long long)__ldcg(a.acc_in + (size_t)c * 2 * a.M + m);
+      si += (long long)__ldcg(a.acc_in + (size_t)c * 2 * a.M + a.M + m);
+    }
   return make_float2((float)sr * a.inv_fx_n, (float)si * a.inv_fx_n);
+}
+
+// The accumulator copy this block adds its forward sums into (copies is a power of two).
+__device__ __forceinline__ unsigned long long *block_acc(const StepArgs &a) {
+  return a.acc_out + (size_t)(blockIdx.x & (unsigned)(a.copies - 1)) * 2 * a.M;
 }
 
 // Sec. 3 weight update and back-projection coefficient of a trap with field v and weight w:
@@ -345,7 +361,7 @@ __device__ __forceinline__ void gsw_prologue(const StepArgs &a, int mc, float2 *
   lw.v = make_float2(0.f, 0.f);
   lw.w = 0.f;
   if (lw.m < a.M) {
-    lw.v = field_from_sums(a, lw.m);
+    lw.v = field_from_sums<COMPLEX>(a, lw.m);
     lw.w = __ldcg(a.w_in + lw.m);
   }
   const float w0 = t < mc ? __ldcg(a.w_in + t) : 0.f;
@@ -355,7 +371,7 @@ __device__ __forceinline__ void gsw_prologue(const StepArgs &a, int mc, float2 *
   ff si = {0.f, 0.f};
   float mx = -1.f, mn = 3.0e38f;
   for (int m = t; m < a.M; m += kThreads) {
-    const float2 v = field_from_sums(a, m);
+    const float2 v = field_from_sums<COMPLEX>(a, m);
     if (m == t) v0 = v;
     s = ff_add(s, {sqrtf(v.x * v.x + v.y * v.y), 0.f});
     if (tr) {
@@ -400,6 +416,7 @@ __device__ __forceinline__ void gsw_prologue(const StepArgs &a, int mc, float2 *
 // of |V_m| over the traps, Sec. 3) from the threads' shares in one fixed order (warp
 // shuffles, warps in order), so every such block obtains the same bits, and the block's
 // weight updates w_m <- w_m <|V|>/|V_m| (traps lw.m, lw.m + stride * kThreads, ...).
+template <bool MULTI = false>
 __device__ __forceinline__ void write_weights(const StepArgs &a, const LateWeight &lw, int stride) {
   if (lw.own >= a.M) return;
   __shared__ ff part[kWarps];
@@ -416,13 +433,14 @@ __device__ __forceinline__ void write_weights(const StepArgs &a, const LateWeigh
   const float mean = (q.hi + q.lo) / (float)a.M;
   if (lw.m < a.M) a.w_out[lw.m] = update_from<false>(lw.v, lw.w, mean, 1.f).x;
   for (int m = lw.m + stride * kThreads; m < a.M; m += stride * kThreads)
-    a.w_out[m] = update_from<false>(field_from_sums(a, m), __ldcg(a.w_in + m), mean, 1.f).x;
+    a.w_out[m] = update_from<false>(field_from_sums<MULTI>(a, m), __ldcg(a.w_in + m), mean, 1.f).x;
 }
 
 struct FinalizeArgs {
   int M;
-  const unsigned long long *acc;  // [2][M] sums of the last forward field
-  unsigned long long *acc_all;    // [3][2][M] all accumulators: cleared for the next call
+  int copies;                     // accumulator copies (as StepArgs::copies)
+  const unsigned long long *acc;  // [copies][2][M] sums of the last forward field
+  unsigned long long *acc_all;    // [3][copies][2][M] all accumulators: cleared for the next call
   const float *w_src;             // [M] weights after the last update
   float *w_dst;                   // [M] where the weights live between calls (may equal w_src)
   long long *Vsum;                // [2][M] out: the sums (V_m = Vsum / (N 2^fx_shift))
@@ -451,7 +469,11 @@ __device__ __forceinline__ void finalize_block(const FinalizeArgs &a) {
   __shared__ Part part[kFinalizeThreads / 32];
   Part p = {{0.f, 0.f}, -1.f, 3.0e38f};
   for (int m = threadIdx.x; m < a.M; m += kFinalizeThreads) {
-    const long long sr = (long long)__ldcg(a.acc + m), si = (long long)__ldcg(a.acc + a.M + m);
+    long long sr = 0, si = 0;
+    for (int c = 0; c < a.copies; c++) {
+      sr += (long long)__ldcg(a.acc + (size_t)c * 2 * a.M + m);
+      si += (long long)__ldcg(a.acc + (size_t)c * 2 * a.M + a.M + m);
+    }
     a.Vsum[m] = sr;
     a.Vsum[a.M + m] = si;
     const float vr = (float)sr * a.inv_fx_n, vi = (float)si * a.inv_fx_n;
@@ -469,7 +491,7 @@ __device__ __forceinline__ void finalize_block(const FinalizeArgs &a) {
   }
   if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = p;
   __syncthreads();  // every read of the accumulators is done before they are cleared
-  for (int i = threadIdx.x; i < 6 * a.M; i += kFinalizeThreads) a.acc_all[i] = 0ull;
+  for (int i = threadIdx.x; i < 6 * a.M * a.copies; i += kFinalizeThreads) a.acc_all[i] = 0ull;
   if (threadIdx.x == 0) {
     Part q = part[0];
     for (int i = 1; i < kFinalizeThreads / 32; i++) {
@@ -644,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
   }
   grid_dependency_wait();
   if (FWD)  // the buffer the next launch accumulates into
-    for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M * a.copies; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
   LateWeight lw;
   const bool gsw = BACK && !ADJ && !a.G;
   if (gsw) gsw_prologue<false>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, a.trace);
@@ -689,7 +711,7 @@ struct SepSmem {
 // Sec. 3 coefficient of trap m in complex form: w_m' V_m/|V_m| with w_m' = w_m <|V|>/|V_m|
 // (R4: |V_m| = 0 keeps w_m and takes the unit field 1).
 __device__ __forceinline__ float2 complex_coefficient(const StepArgs &a, int m, float mean) {
-  return update_from<true>(field_from_sums(a, m), __ldcg(a.w_in + m), mean, 1.f);
+  return update_from<true>(field_from_sums<true>(a, m), __ldcg(a.w_in + m), mean, 1.f);
 }
 
 template <bool BACK, bool ADJ = false>
@@ -774,8 +796,9 @@ __device__ __forceinline__ void forward_traps_sep(const SepSmem &sm, int lo, int
     const float2 v = warp_reduce8(acc, lane);
     const int k = g + ((lane >> 2) & 7);
     if ((lane & 3) == 0 && k < hi) {
-      atomicAdd(a.acc_out + m0 + k, (unsigned long long)__float2ll_rn(v.x * a.fx_scale));
-      atomicAdd(a.acc_out + a.M + m0 + k, (unsigned long long)__float2ll_rn(v.y * a.fx_scale));
+      unsigned long long *acc = block_acc(a);
+      atomicAdd(acc + m0 + k, (unsigned long long)__float2ll_rn(v.x * a.fx_scale));
+      atomicAdd(acc + a.M + m0 + k, (unsigned long long)__float2ll_rn(v.y * a.fx_scale));
     }
   }
 }
@@ -884,13 +907,13 @@ __global__ void __launch_bounds__(kThreads, 2) gsw_sep_kernel(StepArgs a) {
   }
   grid_dependency_wait();
   if (FWD)
-    for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M * a.copies; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
   LateWeight lw;
   const bool gsw = BACK && !ADJ && !a.G;
   if (gsw) gsw_prologue<true>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, a.trace);
   for (int t = t_begin; t < t_end; t++)
     process_subtile_sep<BACK, FWD, ADJ>(a, a.sub[t], 1.f, prestaged, sm, gsw ? sm.C0 : nullptr);
-  if (gsw) write_weights(a, lw, gridDim.x);
+  if (gsw) write_weights<true>(a, lw, gridDim.x);
 }
 
 // Batched launch: the sub-tiles of up to kBatchMax holograms (SubTile::pad = hologram index)
@@ -898,7 +921,7 @@ __global__ void __launch_bounds__(kThreads, 2) gsw_sep_kernel(StepArgs a) {
 // argument read through the constant cache, as the single-hologram kernel reads its own).
 // Every block that meets a hologram computes its <|V|> and coefficients itself; the weights
 // of hologram h are written by block owner[h].
-constexpr int kBatchMax = 24;  // keeps the launch argument under 4 KB
+constexpr int kBatchMax = 22;  // keeps the launch argument under 4 KB
 
 struct BatchArgs {
   StepArgs holo[kBatchMax];
@@ -938,7 +961,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)
   if (FWD)  // clear the buffers the next launch accumulates into, for every hologram
     for (int h = 0; h < b.count; h++) {
       unsigned long long *clr = b.holo[h].acc_clear;
-      const int n2 = 2 * b.holo[h].M;
+      const int n2 = 2 * b.holo[h].M * b.holo[h].copies;
       for (int i = blockIdx.x * kThreads + threadIdx.x; i < n2; i += gridDim.x * kThreads) clr[i] = 0ull;
     }
   int cur = -1;
@@ -947,7 +970,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)
     const SubTile st = b.sub[t];
     const StepArgs &a = b.holo[st.pad];
     if (BACK && st.pad != cur) {
-      if (cur >= 0) write_weights(b.holo[cur], lw, 1);
+      if (cur >= 0) write_weights<SEP>(b.holo[cur], lw, 1);
       const int mc = a.M < a.chunk ? a.M : a.chunk;
       gsw_prologue<SEP>(a, mc, C0, b.owner[st.pad] == (int)blockIdx.x ? 0 : a.M, 1, lw);
     }
@@ -957,7 +980,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)
     else
       process_subtile<FAST, BACK, FWD, false>(a, st, 1.f, prestaged, StepSmem(smem_raw), BACK ? C0 : nullptr);
   }
-  if (BACK && cur >= 0) write_weights(b.holo[cur], lw, 1);
+  if (BACK && cur >= 0) write_weights<SEP>(b.holo[cur], lw, 1);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1041,7 +1064,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)
   for (int k = 0; k <= p.iters; k++) {
     const StepArgs &a = p.step[k % 6];
     if (k > 0 && !grid_sync(p.sync, epoch)) return;
-    for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M * a.copies; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
     const float mean = 1.f;  // coefficients without the common factor <|V|> (see gsw_prologue)
     LateWeight lw;
     if constexpr (MODE == kModeSeparable) {
@@ -1065,7 +1088,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)
           process_subtile<FAST, true, true, false>(a, a.sub[t], mean, prestaged, sm, sm.C0);
       }
     }
-    if (k > 0) write_weights(a, lw, gridDim.x);
+    if (k > 0) write_weights<MODE == kModeSeparable>(a, lw, gridDim.x);
   }
 }
 

@@ -78,7 +78,7 @@ struct hot_ctx {
   float *Xt = nullptr, *Yt = nullptr, *Xr = nullptr, *Yr = nullptr;  // tables
   float2 *Xc = nullptr, *Yc = nullptr;                               // complex tables (separable)
   float *w = nullptr;                                          // [2][M] weights (home: w[0])
-  unsigned long long *acc = nullptr;                           // [3][2][M] fixed-point field sums
+  unsigned long long *acc = nullptr;                           // [3][copies][2][M] fixed-point field sums
   long long *Vsum = nullptr;                                   // [2][M] sums of the last forward
   float *metrics = nullptr;                                    // [2]
   int fx_shift = 0;                                            // fixed-point scale 2^fx_shift
@@ -115,6 +115,13 @@ struct hot_ctx {
 namespace {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
+
+// Copies of each fixed-point accumulator buffer (StepArgs::copies).  With few traps all blocks
+// add into the same 2M addresses at nearly the same moment; 8 copies (block b adds into copy
+// b % 8) spread those atomics.  The separable kernel reads the copies; the direct kernels,
+// whose registers are fully used, keep one.  Storage is sized for the largest count.
+int acc_copies(const hot_ctx *c) { return (c->precision == HOT_PREC_SEPARABLE && c->M <= 512) ? 8 : 1; }
+size_t acc_elems(int M) { return 6 * (size_t)M * (M <= 512 ? 8 : 1); }
 
 // Pixels of the whole hologram (all row bands): the normalisation 1/N of Eq. 1.
 double n_total(const hot_ctx *c) { return (double)c->W * (double)c->H_total; }
@@ -224,7 +231,8 @@ hot::StepArgs make_step_args(const hot_ctx *c, int k, const float *phi, const fl
   a.Xc = c->Xc;
   a.Yc = c->Yc;
   a.phi = c->phi;
-  const size_t M2 = 2 * (size_t)c->M;
+  const size_t M2 = 2 * (size_t)c->M * acc_copies(c);
+  a.copies = acc_copies(c);
   a.acc_in = c->acc + M2 * ((k + 2) % 3);
   a.acc_out = c->acc + M2 * (k % 3);
   a.acc_clear = c->acc + M2 * ((k + 1) % 3);
@@ -376,8 +384,9 @@ int launch_step(hot_ctx *c, bool back, bool fwd, bool pdl, int k) {
 // After the last launch (k = iters): Eq. 4 metrics, field sums, weights home, accumulators cleared.
 int launch_finalize(hot_ctx *c, bool pdl, int iters) {
   hot::FinalizeArgs f;
-  const size_t M2 = 2 * (size_t)c->M;
+  const size_t M2 = 2 * (size_t)c->M * acc_copies(c);
   f.M = c->M;
+  f.copies = acc_copies(c);
   f.acc = c->acc + M2 * (iters % 3);
   f.acc_all = c->acc;
   f.w_src = c->w + (size_t)c->M * (iters & 1);
@@ -449,7 +458,7 @@ int check_wait_error(hot_ctx *c, const char *who) {
   HOT_CUDA(cudaStreamSynchronize(c->st));
   if (!st[2]) return HOT_OK;
   HOT_CUDA(cudaMemsetAsync(c->sync, 0, sizeof st, c->st));
-  if (c->M) HOT_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * 6 * c->M, c->st));
+  if (c->M) HOT_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * acc_elems(c->M), c->st));
   HOT_CUDA(cudaStreamSynchronize(c->st));
   c->have_fields = false;
   return fail(HOT_ETIMEOUT, "%s: a grid barrier wait of the persistent kernel ran out (limit %.3g s)", who,
@@ -618,9 +627,9 @@ int hot_set_traps(hot_ctx *c, int M, const double *xyz_m, const double *w0) {
     if (rc == HOT_OK) rc = dalloc(&c->Xc, (size_t)M * c->W);
     if (rc == HOT_OK) rc = dalloc(&c->Yc, (size_t)M * c->H);
     if (rc == HOT_OK) rc = dalloc(&c->w, 2 * (size_t)M);
-    if (rc == HOT_OK) rc = dalloc(&c->acc, 6 * (size_t)M);
+    if (rc == HOT_OK) rc = dalloc(&c->acc, acc_elems(M));
     if (rc == HOT_OK) rc = dalloc(&c->Vsum, 2 * (size_t)M);
-    if (rc == HOT_OK && cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * 6 * M, c->st) != cudaSuccess)
+    if (rc == HOT_OK && cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * acc_elems(M), c->st) != cudaSuccess)
       rc = fail(HOT_ECUDA, "hot_set_traps: clearing the field accumulators failed");
     if (rc != HOT_OK) {
       free_traps(c);
@@ -839,11 +848,13 @@ int hot_sharded_step(hot_ctx *c, int k) {
   return rc;
 }
 
-int hot_sharded_sums(hot_ctx *c, int k, void **sums_dev) {
-  if (!c || !sums_dev) return fail(HOT_EINVAL, "hot_sharded_sums: NULL argument");
+int hot_sharded_sums(hot_ctx *c, int k, void **sums_dev, int *count) {
+  if (!c || !sums_dev || !count) return fail(HOT_EINVAL, "hot_sharded_sums: NULL argument");
   if (c->shard_k < 0 || k != c->shard_k)
     return fail(HOT_ESTATE, "hot_sharded_sums: launch %d is not the last one (%d)", k, c->shard_k);
-  *sums_dev = c->acc + 2 * (size_t)c->M * (k % 3);
+  const size_t n = 2 * (size_t)c->M * acc_copies(c);
+  *sums_dev = c->acc + n * (k % 3);
+  *count = (int)n;
   return HOT_OK;
 }
 
@@ -1090,11 +1101,12 @@ void batch_free(hot_batch *b) {
 hot::StepArgs step_args(const hot_ctx *c, int k, int chunk) {
   hot::StepArgs a = {};
   const bool fast = c->precision == HOT_PREC_FAST;
-  const size_t M2 = 2 * (size_t)c->M;
+  const size_t M2 = 2 * (size_t)c->M * acc_copies(c);
   a.W = c->W;
   a.H = c->H;
   a.M = c->M;
   a.chunk = chunk;
+  a.copies = acc_copies(c);
   a.X = fast ? c->Xr : c->Xt;
   a.Y = fast ? c->Yr : c->Yt;
   a.Xc = c->Xc;
@@ -1177,7 +1189,8 @@ int build_group(hot_batch *b, hot_batch::Group &g) {
       const hot_ctx *c = b->ctx[g.members[i]];
       hot::FinalizeArgs &f = fs[i];
       f.M = c->M;
-      f.acc = c->acc + 2 * (size_t)c->M * (r6 % 3);  // the last launch accumulated into acc[iters % 3]
+      f.copies = acc_copies(c);
+      f.acc = c->acc + 2 * (size_t)c->M * acc_copies(c) * (r6 % 3);  // the last launch accumulated into acc[iters % 3]
       f.acc_all = c->acc;
       f.w_src = c->w + (size_t)c->M * (r6 & 1);       // and left the weights in w[iters & 1]
       f.w_dst = c->w;
@@ -1847,6 +1860,7 @@ extern "C" int hot_field_noalloc(int width, int height, double pitch_m, double w
   a.H = height;
   a.M = M;
   a.chunk = hot::kChunk;
+  a.copies = 1;
   a.sub = d_sub;
   a.first = d_first;
   a.X = fast ? Xr : Xt;
@@ -1866,6 +1880,7 @@ extern "C" int hot_field_noalloc(int width, int height, double pitch_m, double w
   HOT_CUDA(cudaGetLastError());
   hot::FinalizeArgs f;
   f.M = M;
+  f.copies = 1;
   f.acc = acc;
   f.acc_all = acc;
   f.w_src = w;

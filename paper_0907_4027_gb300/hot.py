@@ -56,7 +56,7 @@ SIGNATURES = {
     "hot_set_band": (_c_int, [_vp, _c_int, _c_int]),
     "hot_sharded_begin": (_c_int, [_vp]),
     "hot_sharded_step": (_c_int, [_vp, _c_int]),
-    "hot_sharded_sums": (_c_int, [_vp, _c_int, ctypes.POINTER(_vp)]),
+    "hot_sharded_sums": (_c_int, [_vp, _c_int, ctypes.POINTER(_vp), _ip]),
     "hot_sharded_end": (_c_int, [_vp, _c_int, _dp, _dp]),
     "hot_get_tiling": (_c_int, [_vp, _ip, _ip, _ip]),
     "hot_autotune": (_c_int, [_vp, _c_int, _ip, _ip, _ip, _dp]),
@@ -230,11 +230,11 @@ def hot_sharded_step(ctx: int, k: int) -> None:
     _ok(lib.hot_sharded_step(_vp(ctx), int(k)), "hot_sharded_step")
 
 
-def hot_sharded_sums(ctx: int, k: int) -> int:
-    """Device address of launch k's partial sums, int64 [2][M]."""
-    p = _vp()
-    _ok(lib.hot_sharded_sums(_vp(ctx), int(k), ctypes.byref(p)), "hot_sharded_sums")
-    return p.value
+def hot_sharded_sums(ctx: int, k: int):
+    """(device address, count) of launch k's partial sums: count int64 values."""
+    p, n = _vp(), _c_int()
+    _ok(lib.hot_sharded_sums(_vp(ctx), int(k), ctypes.byref(p), ctypes.byref(n)), "hot_sharded_sums")
+    return p.value, n.value
 
 
 def hot_sharded_end(ctx: int, iters: int):
@@ -513,9 +513,10 @@ class Hologram:
         hot_sharded_step(self.ctx, k)
 
     def sharded_sums(self, k: int):
-        """Launch k's partial sums as a zero-copy torch int64 tensor [2*M] on the device."""
+        """Launch k's partial sums as a zero-copy torch int64 tensor on the device."""
         import torch
-        return torch.as_tensor(_DeviceArray(hot_sharded_sums(self.ctx, k), 2 * self.M, "<i8"), device="cuda")
+        ptr, n = hot_sharded_sums(self.ctx, k)
+        return torch.as_tensor(_DeviceArray(ptr, n, "<i8"), device="cuda")
 
     def sharded_end(self, iters: int):
         return hot_sharded_end(self.ctx, iters)
