@@ -49,9 +49,14 @@ typedef enum {
 typedef enum {
   HOT_PREC_ACCURATE = 0, /* sincospif on the exactly reduced phase (FP32, ~1 ulp) */
   HOT_PREC_FAST = 1,     /* sin.approx / cos.approx (SFU) on the reduced phase */
-  HOT_PREC_SEPARABLE = 2 /* Eq. 2 factorised: e^{i Delta} = e^{i X_m(ix)} e^{i Y_m(iy)} from FP32
-                            complex tables (FP64 cos/sin once per entry); per pair one complex
-                            multiply-add in each step, no transcendental function */
+  HOT_PREC_SEPARABLE = 2, /* Eq. 2 factorised: e^{i Delta} = e^{i X_m(ix)} e^{i Y_m(iy)} from FP32
+                             complex tables (FP64 cos/sin once per entry); per pair one complex
+                             multiply-add in each step, no transcendental function */
+  HOT_PREC_TENSOR = 3      /* the separable form on the tensor cores: each step of a GSW iteration
+                             is a complex matrix product (S = P X, T = U X^H) run as tcgen05 TF32
+                             MMAs with every operand split in two TF32 parts (three MMAs per
+                             product, FP32 accumulation); the GSW loop only (hot_gsw), other
+                             calls run the separable kernels */
 } hot_precision;
 
 typedef enum {
@@ -83,9 +88,14 @@ int hot_set_weights(hot_ctx *c, const double *w);
  * host memory (on_device = 0) or device memory (on_device = 1). */
 int hot_set_phase(hot_ctx *c, const float *phi, int on_device);
 
-/* Selects HOT_PREC_ACCURATE, HOT_PREC_FAST or HOT_PREC_SEPARABLE for the following calls
- * (switching to or from HOT_PREC_SEPARABLE synchronises and rebuilds the work schedule).
- * HOT_EINVAL for another value. */
+/* Selects HOT_PREC_ACCURATE, HOT_PREC_FAST, HOT_PREC_SEPARABLE or HOT_PREC_TENSOR for the
+ * following calls (switching between the direct and the separable kernels synchronises and
+ * rebuilds the work schedule).  HOT_EINVAL for another value.  In HOT_PREC_TENSOR mode hot_gsw
+ * runs three kernels per iteration (weight update and operand P, back-projection GEMM with the
+ * phases in its epilogue, forward GEMM with the field sums in its epilogue); its operands
+ * (about 8 (2W + 2M)(2M + 2W) + 16 H (W + M) bytes) are built on the first hot_gsw after the
+ * traps are set.  HOT_PREC_TENSOR rejects the persistent form (hot_use_persistent), row-band
+ * steps (hot_sharded_begin), batches (hot_batch_create) and hot_autotune with HOT_EINVAL. */
 int hot_set_precision(hot_ctx *c, int precision);
 
 /* Runs `iters` GSW iterations (Sec. 3, Fig. 2) from the current phases and weights:
@@ -316,6 +326,15 @@ void hot_destroy(hot_ctx *c);
  * *per_clk_per_sm receives the rate and *sms (nullable) the SM count.  Synchronises the
  * device; takes a few milliseconds. */
 int hot_sfu_rate(int op, double *per_clk_per_sm, int *sms);
+
+/* The matrix product of HOT_PREC_TENSOR on its own (no counterpart in the paper):
+ * C = A B^T for DEVICE float32 arrays A [rows][K], B [cols][K] (row-major) into C [rows][cols],
+ * on the tcgen05 tensor cores with every operand split into two TF32 parts (a b ~ a_hi b_hi +
+ * a_hi b_lo + a_lo b_hi, FP32 accumulation), tiles of 128 x tile_n (64 or 128).  rows, cols,
+ * K >= 1.  Allocates its split operands, synchronises cuda_stream (a cudaStream_t or NULL) and
+ * frees them before returning.  HOT_ETIMEOUT if a bounded device-side wait ran out. */
+int hot_tf32x3_gemm(int rows, int cols, int K, const float *A, const float *B, float *C, int tile_n,
+                    void *cuda_stream);
 
 /* Text of the last error on the calling thread ("" if none). */
 const char *hot_last_error(void);

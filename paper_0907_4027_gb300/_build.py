@@ -9,8 +9,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libhot.so")
-SOURCES = [os.path.join(CSRC, "hot.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "gsw_kernels.cuh"), os.path.join(ROOT, "include", "hot.h")]
+SOURCES = [os.path.join(CSRC, "hot.cu"), os.path.join(CSRC, "tc.cu")]
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("gsw_kernels.cuh", "tc_kernels.cuh", "tc.h")] + \
+    [os.path.join(ROOT, "include", "hot.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -33,15 +34,28 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-cudart", "static", "-I", os.path.join(ROOT, "include"), *SOURCES, "-o", tmp]
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
+        flags.insert(0, "-Xptxas=-v")
+    # the translation units compile in parallel, then link into one shared library
+    objs = [f"{tmp}.{i}.o" for i in range(len(SOURCES))]
+    procs = [subprocess.Popen([nvcc(), *flags, "-c", src, "-o", obj], stdout=subprocess.PIPE,
+                              stderr=subprocess.STDOUT, text=True) for src, obj in zip(SOURCES, objs)]
+    outs = [p.communicate()[0] for p in procs]
+    try:
+        for p, src, out in zip(procs, SOURCES, outs):
+            if p.returncode != 0:
+                raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{out}")
+        link = [nvcc(), *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp]
+        r = subprocess.run(link, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc link failed:\n" + " ".join(link) + "\n" + r.stdout + r.stderr)
+    finally:
+        for obj in objs:
+            if os.path.exists(obj):
+                os.remove(obj)
     if verbose:
-        print(r.stdout + r.stderr)
+        print("".join(outs))
     os.replace(tmp, LIB)
     return LIB
 

@@ -12,6 +12,7 @@
 
 #include "../../include/hot.h"
 #include "gsw_kernels.cuh"
+#include "tc.h"
 
 namespace {
 
@@ -110,6 +111,8 @@ struct hot_ctx {
   double wait_limit_s = 2.0;
   unsigned int *sync = nullptr;
   std::vector<Graph> graphs;
+  // HOT_PREC_TENSOR: operands and launch shapes of the tensor-core iteration (built on first use)
+  hot_tc::Plan *tc = nullptr;
 };
 
 namespace {
@@ -121,6 +124,12 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
 // b % 8) spread those atomics.  The separable kernel reads the copies; the direct kernels,
 // whose registers are fully used, keep one.  Storage is sized for the largest count.
 int acc_copies(const hot_ctx *c) { return (c->precision == HOT_PREC_SEPARABLE && c->M <= 512) ? 8 : 1; }
+
+// Modes whose step kernels are the separable ones: HOT_PREC_SEPARABLE, and HOT_PREC_TENSOR for
+// every launch outside the GSW loop (forward field and adjoint of given phases, superposition).
+bool separable_kernels(const hot_ctx *c) {
+  return c->precision == HOT_PREC_SEPARABLE || c->precision == HOT_PREC_TENSOR;
+}
 size_t acc_elems(int M) { return 6 * (size_t)M * (M <= 512 ? 8 : 1); }
 
 // Pixels of the whole hologram (all row bands): the normalisation 1/N of Eq. 1.
@@ -140,6 +149,8 @@ void drop_graphs(hot_ctx *c) {
 
 void free_traps(hot_ctx *c) {
   drop_graphs(c);
+  hot_tc::plan_destroy(c->tc);
+  c->tc = nullptr;
   dfree(c->abc);
   dfree(c->Xt);
   dfree(c->Yt);
@@ -276,7 +287,7 @@ int launch_sep(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const fl
 template <bool BACK, bool FWD, bool ADJ = false>
 int launch_mode(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const float2 *G = nullptr,
                 float *grad = nullptr) {
-  if (c->precision == HOT_PREC_SEPARABLE) return launch_sep<BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
+  if (separable_kernels(c)) return launch_sep<BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
   if (c->precision == HOT_PREC_FAST) return launch_tile<true, BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
   return launch_tile<false, BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
 }
@@ -315,7 +326,7 @@ int build_schedule(hot_ctx *c) {
   // the per-iteration and the persistent kernels share the schedule (so that they compute the
   // same bits): as many blocks per SM as both can keep resident
   int per_sm_p = 0;
-  if (c->precision == HOT_PREC_SEPARABLE) {
+  if (separable_kernels(c)) {
     const int smem = hot::sep_smem_bytes(sep_chunk(c));
     HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_sep_kernel<true, true>, hot::kThreads, smem));
     HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_p, hot::gsw_persistent_kernel<hot::kModeSeparable>,
@@ -410,7 +421,54 @@ int launch_build_tables(hot_ctx *c) {
   Probe p(c, HOT_KERNEL_OTHER);
   hot::build_tables_kernel<<<blocks, 256, 0, c->st>>>(c->W, c->H, c->H_total, c->y_off, c->M, c->abc, c->Xt, c->Yt,
                                                       c->Xr, c->Yr, c->Xc, c->Yc);
-  return check_launch(c, "build_tables_kernel");
+  int rc = check_launch(c, "build_tables_kernel");
+  if (rc == HOT_OK && c->tc) {  // the tensor-core operands derive from the tables
+    cudaError_t e = hot_tc::plan_refresh(c->tc, c->st);
+    if (e != cudaSuccess) rc = fail(HOT_ECUDA, "rebuilding the tensor-core operands: %s", cudaGetErrorString(e));
+    c->launches++;
+  }
+  return rc;
+}
+
+// The tensor-core plan of the context's traps (HOT_PREC_TENSOR), built on first use.
+int ensure_tc_plan(hot_ctx *c) {
+  if (c->tc) return HOT_OK;
+  const char *what = "";
+  cudaError_t e = hot_tc::plan_create(&c->tc, c->W, c->H, c->M, c->Xc, c->Yc, c->st, &what);
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorMemoryAllocation ? HOT_ENOMEM : HOT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  c->launches++;
+  return HOT_OK;
+}
+
+hot_tc::Step tc_step(hot_ctx *c, int k) {
+  const hot::StepArgs a = make_step_args(c, k, nullptr, nullptr, nullptr);
+  hot_tc::Step s;
+  s.M = c->M;
+  s.acc_in = a.acc_in;
+  s.acc_out = a.acc_out;
+  s.acc_clear = a.acc_clear;
+  s.w_in = a.w_in;
+  s.w_out = a.w_out;
+  s.phi = c->phi;
+  s.trace = a.trace;
+  s.fx_scale = a.fx_scale;
+  s.inv_fx_n = a.inv_fx_n;
+  s.err = reinterpret_cast<int *>(c->sync + 2);
+  s.limit_ns = (long long)(c->wait_limit_s * 1e9);
+  return s;
+}
+
+// Launch k of the tensor-core sequence: k = 0 the forward field of the phases, k >= 1 iteration k.
+int launch_tc(hot_ctx *c, bool pdl, int k) {
+  Probe p(c, k ? HOT_KERNEL_STEP : HOT_KERNEL_FORWARD);
+  int kernels = 0;
+  const bool chain = !c->profiling;
+  const cudaError_t e = k ? hot_tc::launch_iteration(c->tc, tc_step(c, k), c->st, pdl, chain, &kernels)
+                          : hot_tc::launch_forward(c->tc, tc_step(c, k), c->st, pdl, chain, &kernels);
+  c->launches += kernels;
+  if (e != cudaSuccess) return fail(HOT_ECUDA, "tensor-core launch %d: %s", k, cudaGetErrorString(e));
+  return HOT_OK;
 }
 
 // The whole sequence of enqueue_gsw's step launches as one cooperative launch (all blocks
@@ -453,7 +511,7 @@ int launch_persistent(hot_ctx *c, int iters) {
 // Reads the barrier's error flag (synchronises): after a wait ran out, the accumulators and the
 // barrier are reset and HOT_ETIMEOUT is returned; the phases are then undefined.
 int check_wait_error(hot_ctx *c, const char *who) {
-  unsigned int st[3] = {0, 0, 0};
+  unsigned int st[3] = {0, 0, 0};  // [2]: error flag of the bounded waits
   HOT_CUDA(cudaMemcpyAsync(st, c->sync, sizeof st, cudaMemcpyDeviceToHost, c->st));
   HOT_CUDA(cudaStreamSynchronize(c->st));
   if (!st[2]) return HOT_OK;
@@ -461,8 +519,7 @@ int check_wait_error(hot_ctx *c, const char *who) {
   if (c->M) HOT_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * acc_elems(c->M), c->st));
   HOT_CUDA(cudaStreamSynchronize(c->st));
   c->have_fields = false;
-  return fail(HOT_ETIMEOUT, "%s: a grid barrier wait of the persistent kernel ran out (limit %.3g s)", who,
-              c->wait_limit_s);
+  return fail(HOT_ETIMEOUT, "%s: a bounded device-side wait ran out (limit %.3g s)", who, c->wait_limit_s);
 }
 
 int enqueue_gsw(hot_ctx *c, int iters) {
@@ -472,6 +529,12 @@ int enqueue_gsw(hot_ctx *c, int iters) {
     return rc;
   }
   const bool pdl = !c->profiling;
+  if (c->precision == HOT_PREC_TENSOR) {
+    int rc = launch_tc(c, false, 0);
+    for (int k = 1; k <= iters && rc == HOT_OK; k++) rc = launch_tc(c, pdl, k);
+    if (rc == HOT_OK) rc = launch_finalize(c, pdl, iters);
+    return rc;
+  }
   int rc = launch_step(c, false, true, false, 0);       // V^1 = F(phi^0)
   for (int k = 1; k <= iters && rc == HOT_OK; k++)
     rc = launch_step(c, true, true, pdl, k);            // w^k, c^k from V^k; phi^k; V^{k+1} = F(phi^k)
@@ -677,10 +740,14 @@ int hot_set_phase(hot_ctx *c, const float *phi, int on_device) {
 
 int hot_set_precision(hot_ctx *c, int precision) {
   if (!c) return fail(HOT_EINVAL, "hot_set_precision: NULL context");
-  if (precision != HOT_PREC_ACCURATE && precision != HOT_PREC_FAST && precision != HOT_PREC_SEPARABLE)
+  if (precision != HOT_PREC_ACCURATE && precision != HOT_PREC_FAST && precision != HOT_PREC_SEPARABLE &&
+      precision != HOT_PREC_TENSOR)
     return fail(HOT_EINVAL, "hot_set_precision: unknown mode %d", precision);
-  const bool resched = (precision == HOT_PREC_SEPARABLE) != (c->precision == HOT_PREC_SEPARABLE);
-  if (resched) HOT_CUDA(cudaStreamSynchronize(c->st));
+  const bool was_sep = separable_kernels(c);
+  const bool copies_change = (precision == HOT_PREC_SEPARABLE) != (c->precision == HOT_PREC_SEPARABLE);
+  if (was_sep != (precision == HOT_PREC_SEPARABLE || precision == HOT_PREC_TENSOR) || copies_change)
+    HOT_CUDA(cudaStreamSynchronize(c->st));
+  const bool resched = was_sep != (precision == HOT_PREC_SEPARABLE || precision == HOT_PREC_TENSOR);
   c->precision = precision;
   if (resched && c->M) return build_schedule(c);  // the two kernels' occupancies differ
   return HOT_OK;
@@ -690,6 +757,11 @@ int hot_gsw(hot_ctx *c, int iters, double *eff_out, double *unif_out) {
   if (!c) return fail(HOT_EINVAL, "hot_gsw: NULL context");
   if (iters < 0) return fail(HOT_EINVAL, "hot_gsw: iters = %d < 0", iters);
   if (!c->M) return fail(HOT_ESTATE, "hot_gsw: no traps set");
+  if (c->precision == HOT_PREC_TENSOR) {
+    if (c->persistent) return fail(HOT_EINVAL, "hot_gsw: the persistent form has no tensor-core variant");
+    const int rc = ensure_tc_plan(c);
+    if (rc != HOT_OK) return rc;
+  }
   if (c->tracing) {
     if (iters > c->trace_cap) {  // the launches' trace slots change: recapture the graphs
       HOT_CUDA(cudaStreamSynchronize(c->st));
@@ -707,7 +779,7 @@ int hot_gsw(hot_ctx *c, int iters, double *eff_out, double *unif_out) {
   if (rc != HOT_OK) return rc;
   c->have_fields = true;
   if (eff_out || unif_out) {
-    if (c->persistent) {
+    if (c->persistent || c->precision == HOT_PREC_TENSOR) {
       const int rc2 = check_wait_error(c, "hot_gsw");
       if (rc2 != HOT_OK) return rc2;
     }
@@ -832,6 +904,8 @@ int hot_set_band(hot_ctx *c, int total_height, int y0) {
 int hot_sharded_begin(hot_ctx *c) {
   if (!c) return fail(HOT_EINVAL, "hot_sharded_begin: NULL context");
   if (!c->M) return fail(HOT_ESTATE, "hot_sharded_begin: no traps set");
+  if (c->precision == HOT_PREC_TENSOR)
+    return fail(HOT_EINVAL, "hot_sharded_begin: row bands run the direct or separable kernels, not HOT_PREC_TENSOR");
   c->shard_k = -1;
   c->have_fields = false;
   const int rc = launch_step(c, false, true, false, 0);
@@ -1438,6 +1512,8 @@ int hot_autotune(hot_ctx *c, int iters, int *rows, int *blocks_per_sm, int *chun
   if (!c) return fail(HOT_EINVAL, "hot_autotune: NULL context");
   if (!c->M) return fail(HOT_ESTATE, "hot_autotune: no traps set");
   if (iters < 1) return fail(HOT_EINVAL, "hot_autotune: iters = %d < 1", iters);
+  if (c->precision == HOT_PREC_TENSOR)
+    return fail(HOT_EINVAL, "hot_autotune: HOT_PREC_TENSOR has no tiling parameters (its tiles are fixed)");
   Saved saved;
   int rc = save_state(c, saved, c->st);
   if (rc != HOT_OK) return rc;
@@ -1474,6 +1550,8 @@ int hot_batch_create(hot_batch **out, int count, hot_ctx *const *ctxs, void *cud
     if (!ctxs[i]->M) return fail(HOT_ESTATE, "hot_batch_create: context %d has no traps", i);
     if (ctxs[i]->precision != ctxs[0]->precision)
       return fail(HOT_EINVAL, "hot_batch_create: contexts differ in precision mode");
+    if (ctxs[i]->precision == HOT_PREC_TENSOR)
+      return fail(HOT_EINVAL, "hot_batch_create: batches run the direct or separable kernels, not HOT_PREC_TENSOR");
     if (ctxs[i]->H_total != ctxs[i]->H)
       return fail(HOT_EINVAL, "hot_batch_create: context %d is a row band (its sums need an exchange)", i);
     if (ctxs[i]->dev != ctxs[0]->dev) return fail(HOT_EINVAL, "hot_batch_create: contexts on different devices");
@@ -1659,6 +1737,24 @@ __global__ void __launch_bounds__(1024) sfu_rate_kernel(float *out, long long *c
 }
 
 }  // namespace
+
+extern "C" int hot_tf32x3_gemm(int rows, int cols, int K, const float *A, const float *B, float *C, int tile_n,
+                               void *cuda_stream) {
+  if (rows < 1 || cols < 1 || K < 1) return fail(HOT_EINVAL, "hot_tf32x3_gemm: sizes %d x %d x %d", rows, cols, K);
+  if (!A || !B || !C) return fail(HOT_EINVAL, "hot_tf32x3_gemm: NULL argument");
+  if (tile_n != 64 && tile_n != 128) return fail(HOT_EINVAL, "hot_tf32x3_gemm: tile_n = %d not 64 or 128", tile_n);
+  if ((long long)rows * K >= (1LL << 31) || (long long)cols * K >= (1LL << 31) || (long long)rows * cols >= (1LL << 31))
+    return fail(HOT_EINVAL, "hot_tf32x3_gemm: operands of 2^31 elements or more");
+  int timed_out = 0;
+  const char *what = "";
+  const cudaError_t e = hot_tc::gemm(rows, cols, K, A, B, C, tile_n, static_cast<cudaStream_t>(cuda_stream),
+                                     &timed_out, &what);
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorMemoryAllocation ? HOT_ENOMEM : HOT_ECUDA, "hot_tf32x3_gemm: %s: %s", what,
+                cudaGetErrorString(e));
+  if (timed_out) return fail(HOT_ETIMEOUT, "hot_tf32x3_gemm: a bounded device-side wait ran out");
+  return HOT_OK;
+}
 
 extern "C" int hot_sfu_rate(int op, double *per_clk_per_sm, int *sms) {
   if (!per_clk_per_sm || op < 0 || op > 3) return fail(HOT_EINVAL, "hot_sfu_rate: invalid argument");

@@ -22,8 +22,9 @@ if not os.path.exists(_LIB_PATH):
 lib = ctypes.CDLL(_LIB_PATH)
 
 HOT_OK, HOT_EINVAL, HOT_ENOMEM, HOT_ECUDA, HOT_ETIMEOUT, HOT_ESTATE = 0, -1, -2, -3, -4, -5
-HOT_PREC_ACCURATE, HOT_PREC_FAST, HOT_PREC_SEPARABLE = 0, 1, 2
-PRECISIONS = {"accurate": HOT_PREC_ACCURATE, "fast": HOT_PREC_FAST, "separable": HOT_PREC_SEPARABLE}
+HOT_PREC_ACCURATE, HOT_PREC_FAST, HOT_PREC_SEPARABLE, HOT_PREC_TENSOR = 0, 1, 2, 3
+PRECISIONS = {"accurate": HOT_PREC_ACCURATE, "fast": HOT_PREC_FAST, "separable": HOT_PREC_SEPARABLE,
+              "tensor": HOT_PREC_TENSOR}
 HOT_FMT_F32, HOT_FMT_U8 = 0, 1
 HOT_MAX_TRAPS = 4096
 _STATUS = {0: "HOT_OK", -1: "HOT_EINVAL", -2: "HOT_ENOMEM", -3: "HOT_ECUDA", -4: "HOT_ETIMEOUT",
@@ -76,6 +77,7 @@ SIGNATURES = {
     "hot_destroy": (None, [_vp]),
     "hot_last_error": (ctypes.c_char_p, []),
     "hot_sfu_rate": (_c_int, [_c_int, _dp, ctypes.POINTER(_c_int)]),
+    "hot_tf32x3_gemm": (_c_int, [_c_int, _c_int, _c_int, _vp, _vp, _vp, _c_int, _vp]),
     "hot_field_noalloc": (_c_int, [_c_int, _c_int, _c_double, _c_double, _c_double, _c_int, _vp, _vp, _c_int,
                                    _vp, _vp, _vp]),
 }
@@ -394,6 +396,17 @@ def hot_sfu_rate(op: int = 0):
     r, n = ctypes.c_double(), _c_int()
     _ok(lib.hot_sfu_rate(int(op), ctypes.byref(r), ctypes.byref(n)), "hot_sfu_rate")
     return r.value, n.value
+
+
+def hot_tf32x3_gemm(A, B, C, tile_n: int = 64, cuda_stream: int | None = None) -> None:
+    """C = A B^T on the tensor cores (3xTF32): A (rows, K), B (cols, K), C (rows, cols) are
+    contiguous float32 CUDA tensors.  Synchronises."""
+    rows, K = A.shape
+    cols = B.shape[0]
+    if B.shape[1] != K or tuple(C.shape) != (rows, cols):
+        raise ValueError("hot_tf32x3_gemm: shapes do not match")
+    _ok(lib.hot_tf32x3_gemm(int(rows), int(cols), int(K), _vp(A.data_ptr()), _vp(B.data_ptr()), _vp(C.data_ptr()),
+                            int(tile_n), _vp(cuda_stream or 0)), "hot_tf32x3_gemm")
 
 
 HOT_NOALLOC_SCRATCH_BYTES = 16 << 20
