@@ -36,6 +36,8 @@ SFU_LANES_PER_SM = 16          # sin.approx / cos.approx results per clock per S
 SFU_OPS_PER_UPDATE = 4         # one sin + one cos in the forward field, one each in back-projection
 FMA_LANES_PER_SM = 128         # FP32 FMA results per clock per SM (sm_103a)
 FMA_OPS_PER_UPDATE = 8         # separable mode: one complex multiply-add (4 FMA) in each step
+TF32_FLOPS_PER_UPDATE = 48     # tensor mode: 2 complex MACs (16 flops) x 3 TF32 MMAs per product (hi/lo split)
+TF32_PER_BF16 = 1.1 / 2.25     # nominal dense TF32 / BF16 tensor rate (GB300)
 L2_FLUSH_BYTES = 256 << 20     # > 129 MB L2
 
 
@@ -46,8 +48,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--workload", default="rand100_512")
-    ap.add_argument("--precision", default=None, choices=["accurate", "fast", "separable"],
-                    help="override the workload's mode (separable: its own FP32-FMA roofline)")
+    ap.add_argument("--precision", default=None, choices=["accurate", "fast", "separable", "tensor"],
+                    help="override the workload's mode (separable: its own FP32-FMA roofline; "
+                         "tensor: the TF32 tensor-core roofline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision-report", action="store_true",
                     help="errors of both precision modes against the FP64 oracle, per result")
@@ -218,6 +221,7 @@ def run_engine(args):
     if args.precision:
         w.precision = args.precision
     sep = w.precision == "separable"
+    tensor = w.precision == "tensor"
     stream = torch.cuda.current_stream()
     h = hot.Hologram(w.W, w.H, w.pitch, w.wavelength, w.focal, stream.cuda_stream, w.precision)
     h.set_traps(w.xyz, w.w0)
@@ -234,7 +238,10 @@ def run_engine(args):
     # tiling picked by the autotuner (untimed setup; phases and weights are kept)
     h.set_phase(phi0)
     t_tune = time.perf_counter()
-    tuned = h.autotune(w.iters)
+    if tensor:  # fixed tiles: nothing to tune
+        tuned = {"rows": None, "blocks_per_sm": None, "chunk": None, "us_per_iter": None}
+    else:
+        tuned = h.autotune(w.iters)
     tuned["seconds"] = time.perf_counter() - t_tune
 
     for _ in range(args.warmup):
@@ -308,13 +315,13 @@ def run_engine(args):
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks_path):
         sm_max_mhz = float(json.load(open(peaks_path)).get("sm_max_mhz", sm_max_mhz))
-    if sep:
+    if sep or tensor:
         lanes, ops, pipe = FMA_LANES_PER_SM, FMA_OPS_PER_UPDATE, "FP32 FMA"
     else:
         lanes, ops, pipe = SFU_LANES_PER_SM, SFU_OPS_PER_UPDATE, "SFU"
     peak = dev.multi_processor_count * lanes * sm_max_mhz * 1e6 / ops
-    lanes_measured = hot.hot_sfu_rate(3 if sep else 0)[0]
-    traffic = profiled_traffic(args.workload, "sep" if sep else "step")
+    lanes_measured = hot.hot_sfu_rate(3 if sep or tensor else 0)[0]
+    traffic = profiled_traffic(args.workload, "tc" if tensor else "sep" if sep else "step")
     kernel_share = {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4)
                     for k, v in prof.items()}
 
@@ -347,11 +354,43 @@ def run_engine(args):
     h2d = w.N * 4 + w.M * 3 * 8 + w.M * 8
     d2h = w.N * (1 if w.quantize else 4) + 16
 
+    launch_timing = (f"marginal iteration time of graph-replayed hot_gsw({w.iters}) vs hot_gsw({k_small}), "
+                     f"CUDA events, median of {n_roof}")
+    if tensor:
+        # three launches per iteration (operand P, back-projection GEMM, forward GEMM); the
+        # GEMMs' algorithmic TF32 work is 48 flops per pair (no padding counted)
+        bf16 = float(json.load(open(peaks_path))["bf16_tflops"]) if os.path.exists(peaks_path) else 1900.0
+        tf_peak = bf16 * TF32_PER_BF16
+        tf_achieved = TF32_FLOPS_PER_UPDATE * w.N * w.M / avg_launch_s / 1e12
+        roofline = {"bound": "tensor", "achieved": tf_achieved, "peak": tf_peak, "unit": "TFLOP/s",
+                    "frac": tf_achieved / tf_peak, "traffic": traffic,
+                    "kernel": "tc_prep_kernel + tc_gemm_kernel<back> + tc_gemm_kernel<fwd> (one GSW iteration)",
+                    "peak_basis": f"measured bf16 burst {bf16:.1f} TFLOP/s (MEASURED_PEAKS.json) x nominal "
+                                  f"TF32/BF16 {TF32_PER_BF16:.3f}",
+                    "flops_per_update": TF32_FLOPS_PER_UPDATE, "avg_iteration_us": avg_launch_s * 1e6,
+                    "updates_per_s": achieved,
+                    "fp32_fma_roofline_updates_per_s": peak, "launch_timing": launch_timing,
+                    "avg_iteration_us_unpipelined": step_kernel_ms * 1e3 / max(step_kernel_n, 1)}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "updates/s",
+                    "frac": achieved / peak, "traffic": traffic,
+                    "kernel": ("gsw_sep_kernel<back, fwd>" if sep else
+                               f"gsw_step_kernel<{w.precision}, back, fwd>") + " (one GSW iteration per launch)",
+                    "peak_basis": f"{dev.multi_processor_count} SMs x {lanes} {pipe} "
+                                  f"lanes/clk x {sm_max_mhz:.0f} MHz / {ops} "
+                                  f"{pipe} ops per update",
+                    "lanes_per_clk_per_sm_measured": round(lanes_measured, 2),
+                    "avg_launch_us": avg_launch_s * 1e6,
+                    "units_per_launch": units_per_launch,
+                    "launch_timing": launch_timing,
+                    "avg_launch_us_unpipelined": step_kernel_ms * 1e3 / max(step_kernel_n, 1)}
     if rank == 0:
+        metric = METRIC if args.workload == "rand100_512" else \
+            f"GSW pixel-trap updates/s ({w.W}x{w.H} px, M={w.M}, {w.iters} iterations)"
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3" if tensor else "f32", "data": "synthetic",
             "config": workload_config(w, {
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                 "l2": "flushed between steps (256 MB write outside the step events)",
@@ -362,19 +401,7 @@ def run_engine(args):
                           "one CUDA graph per call; roofline kernel times from a second pass of "
                           "the same steps with per-launch events"}),
             "holograms_per_s": world * args.steps / (total_ms * 1e-3),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "updates/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": ("gsw_sep_kernel<back, fwd>" if sep else
-                                    f"gsw_step_kernel<{w.precision}, back, fwd>") + " (one GSW iteration per launch)",
-                         "peak_basis": f"{dev.multi_processor_count} SMs x {lanes} {pipe} "
-                                       f"lanes/clk x {sm_max_mhz:.0f} MHz / {ops} "
-                                       f"{pipe} ops per update",
-                         "lanes_per_clk_per_sm_measured": round(lanes_measured, 2),
-                         "avg_launch_us": avg_launch_s * 1e6,
-                         "units_per_launch": units_per_launch,
-                         "launch_timing": f"marginal iteration time of graph-replayed hot_gsw({w.iters}) "
-                                          f"vs hot_gsw({k_small}), CUDA events, median of {n_roof}",
-                         "avg_launch_us_unpipelined": step_kernel_ms * 1e3 / max(step_kernel_n, 1)},
+            "roofline": roofline,
             "kernel_time_share": kernel_share,
             "kernel_time_ms": {k: round(v[0] / n_prof, 4) for k, v in prof.items()},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -521,9 +548,9 @@ def run_grid_sweep(args):
 
 
 def run_precision_report(args):
-    """Errors of HOT_PREC_ACCURATE, HOT_PREC_FAST and HOT_PREC_SEPARABLE against the FP64
-    oracle, per result, on grid16_256 and rand100_512, with the time per GSW iteration of each
-    mode."""
+    """Errors of HOT_PREC_ACCURATE, HOT_PREC_FAST, HOT_PREC_SEPARABLE and HOT_PREC_TENSOR against
+    the FP64 oracle, per result, on grid16_256 and rand100_512, with the time per GSW iteration of
+    each mode."""
     import torch
     import oracle
     from paper_0907_4027_gb300 import _build
@@ -537,7 +564,7 @@ def run_precision_report(args):
         K = base.iters
         r1 = oracle.gsw(base.geom, base.xyz, 1, base.phi0)
         rK = oracle.gsw(base.geom, base.xyz, K, base.phi0)
-        for prec in ("accurate", "fast", "separable"):
+        for prec in ("accurate", "fast", "separable", "tensor"):
             w = wl.NAMED[name]()
             w.precision = prec
             h = hot.Hologram.from_workload(w, stream.cuda_stream)

@@ -330,7 +330,7 @@ int hot_sfu_rate(int op, double *per_clk_per_sm, int *sms);
 /* The matrix product of HOT_PREC_TENSOR on its own (no counterpart in the paper):
  * C = A B^T for DEVICE float32 arrays A [rows][K], B [cols][K] (row-major) into C [rows][cols],
  * on the tcgen05 tensor cores with every operand split into two TF32 parts (a b ~ a_hi b_hi +
- * a_hi b_lo + a_lo b_hi, FP32 accumulation), tiles of 128 x tile_n (64 or 128).  rows, cols,
+ * a_hi b_lo + a_lo b_hi, FP32 accumulation), tiles of 128 x tile_n (32, 64, 128 or 256).  rows, cols,
  * K >= 1.  Allocates its split operands, synchronises cuda_stream (a cudaStream_t or NULL) and
  * frees them before returning.  HOT_ETIMEOUT if a bounded device-side wait ran out. */
 int hot_tf32x3_gemm(int rows, int cols, int K, const float *A, const float *B, float *C, int tile_n,

@@ -1742,7 +1742,8 @@ extern "C" int hot_tf32x3_gemm(int rows, int cols, int K, const float *A, const 
                                void *cuda_stream) {
   if (rows < 1 || cols < 1 || K < 1) return fail(HOT_EINVAL, "hot_tf32x3_gemm: sizes %d x %d x %d", rows, cols, K);
   if (!A || !B || !C) return fail(HOT_EINVAL, "hot_tf32x3_gemm: NULL argument");
-  if (tile_n != 64 && tile_n != 128) return fail(HOT_EINVAL, "hot_tf32x3_gemm: tile_n = %d not 64 or 128", tile_n);
+  if (tile_n != 32 && tile_n != 64 && tile_n != 128 && tile_n != 256)
+    return fail(HOT_EINVAL, "hot_tf32x3_gemm: tile_n = %d not 32, 64, 128 or 256", tile_n);
   if ((long long)rows * K >= (1LL << 31) || (long long)cols * K >= (1LL << 31) || (long long)rows * cols >= (1LL << 31))
     return fail(HOT_EINVAL, "hot_tf32x3_gemm: operands of 2^31 elements or more");
   int timed_out = 0;

@@ -13,7 +13,7 @@ struct Plan {
   int W = 0, H = 0, M = 0;
   int Kb = 0, Kf = 0;               // K of the back GEMM (2M padded to 32) and forward GEMM (2W padded)
   int rows_h = 0;                   // H padded to the tile height (rows of P and U)
-  int bn_back = 64;                 // tile width of the back GEMM
+  int bn_back = 64, bn_fwd = 64;    // tile widths of the back and forward GEMMs
   int rows_b = 0, rows_f = 0;       // rows of Bb (2W) and Bf (2M), padded to the tile width
   int fwd_splits = 1, fwd_cps = 1;  // K splits of the forward GEMM, K slices per split
   int sms = 0;
@@ -87,7 +87,30 @@ cudaError_t alloc(T **p, size_t count) {
 
 template <int BN, int EPI>
 cudaError_t launch_gemm(const tc::Maps &maps, const tc::GemmArgs &g, dim3 grid, cudaStream_t st, bool pdl) {
-  return launch(tc::tc_gemm_kernel<BN, EPI>, grid, tc::kThreads, tc::Cfg<BN>::kSmem, st, pdl, maps, g);
+  return launch(tc::tc_gemm_kernel<BN, EPI>, grid, tc::Cfg<BN>::kThreads, tc::Cfg<BN>::kSmem, st, pdl, maps, g);
+}
+
+template <int EPI>
+cudaError_t launch_gemm_bn(int bn, const tc::Maps &maps, const tc::GemmArgs &g, dim3 grid, cudaStream_t st, bool pdl) {
+  return bn == 256 ? launch_gemm<256, EPI>(maps, g, grid, st, pdl)
+         : bn == 128 ? launch_gemm<128, EPI>(maps, g, grid, st, pdl)
+         : bn == 64  ? launch_gemm<64, EPI>(maps, g, grid, st, pdl)
+                     : launch_gemm<32, EPI>(maps, g, grid, st, pdl);
+}
+
+// Tile width of a GEMM with `rows` x `cols` outputs: the widest whose tiles still occupy most
+// SMs and add little padding (wider tiles load fewer operand bytes per MMA; L2 bandwidth bounds
+// the narrow ones).
+// split_k: the K range may be split over CTAs (the forward GEMM) when it has >= 4 slices each.
+int pick_width(int rows, int cols, int k_chunks, int sms, bool split_k) {
+  for (int bn : {256, 128, 64}) {
+    if (8 * round_up(cols, bn) > 9 * round_up(cols, 32)) continue;  // > 12.5% more padding than 32
+    const long long tiles = (long long)((rows + tc::kBM - 1) / tc::kBM) * ((cols + bn - 1) / bn);
+    const long long ctas = split_k ? tiles * std::max(1, std::min(k_chunks / 4, sms / (int)std::max(1LL, tiles)))
+                                   : tiles;
+    if (ctas * 5 >= 4LL * sms) return bn;
+  }
+  return 32;
 }
 
 }  // namespace
@@ -136,15 +159,14 @@ cudaError_t plan_create(Plan **out, int W, int H, int M, const float2 *Xc, const
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev);
-  // back GEMM: wide tiles when they still give every SM a tile
-  const int tiles128 = (p->rows_h / tc::kBM) * ((2 * W + 127) / 128);
-  p->bn_back = tiles128 >= p->sms ? 128 : 64;
+  p->bn_back = pick_width(H, 2 * W, p->Kb / tc::kBK, p->sms, false);
+  p->bn_fwd = pick_width(H, 2 * M, p->Kf / tc::kBK, p->sms, true);
   p->rows_b = round_up(2 * W, p->bn_back);
-  p->rows_f = round_up(2 * M, 64);
-  // forward GEMM: K split over CTAs until the tiles fill the SMs once
-  const int tiles_f = (p->rows_h / tc::kBM) * (p->rows_f / 64);
+  p->rows_f = round_up(2 * M, p->bn_fwd);
+  // forward GEMM: the K range split over CTAs so that the tiles fill the SMs about once
+  const int tiles_f = (p->rows_h / tc::kBM) * (p->rows_f / p->bn_fwd);
   const int kcf = p->Kf / tc::kBK;
-  int splits = std::max(1, std::min(kcf, (p->sms + tiles_f - 1) / std::max(tiles_f, 1)));
+  const int splits = std::max(1, std::min(kcf, p->sms / std::max(tiles_f, 1)));
   p->fwd_cps = (kcf + splits - 1) / splits;
   p->fwd_splits = (kcf + p->fwd_cps - 1) / p->fwd_cps;  // every split has >= 1 slice
   *what = "allocating the tensor-core operands";
@@ -176,14 +198,19 @@ cudaError_t plan_create(Plan **out, int W, int H, int M, const float2 *Xc, const
     if (e == cudaSuccess) e = encode(&p->back.b_lo, p->bb_lo, p->Kb, p->rows_b, p->bn_back);
     if (e == cudaSuccess) e = encode(&p->fwd.a_hi, p->u_hi, p->Kf, p->rows_h, tc::kBM);
     if (e == cudaSuccess) e = encode(&p->fwd.a_lo, p->u_lo, p->Kf, p->rows_h, tc::kBM);
-    if (e == cudaSuccess) e = encode(&p->fwd.b_hi, p->bf_hi, p->Kf, p->rows_f, 64);
-    if (e == cudaSuccess) e = encode(&p->fwd.b_lo, p->bf_lo, p->Kf, p->rows_f, 64);
+    if (e == cudaSuccess) e = encode(&p->fwd.b_hi, p->bf_hi, p->Kf, p->rows_f, p->bn_fwd);
+    if (e == cudaSuccess) e = encode(&p->fwd.b_lo, p->bf_lo, p->Kf, p->rows_f, p->bn_fwd);
   }
   if (e == cudaSuccess) {
     *what = "setting the tensor-core kernels' shared memory";
-    e = set_smem<64, tc::kEpiBack>();
+    e = set_smem<32, tc::kEpiBack>();
+    if (e == cudaSuccess) e = set_smem<64, tc::kEpiBack>();
     if (e == cudaSuccess) e = set_smem<128, tc::kEpiBack>();
+    if (e == cudaSuccess) e = set_smem<256, tc::kEpiBack>();
+    if (e == cudaSuccess) e = set_smem<32, tc::kEpiFwd>();
     if (e == cudaSuccess) e = set_smem<64, tc::kEpiFwd>();
+    if (e == cudaSuccess) e = set_smem<128, tc::kEpiFwd>();
+    if (e == cudaSuccess) e = set_smem<256, tc::kEpiFwd>();
   }
   if (e != cudaSuccess) {
     cudaStreamSynchronize(st);
@@ -216,8 +243,8 @@ cudaError_t launch_forward(Plan *p, const Step &s, cudaStream_t st, bool pdl, bo
   g.Yc = p->Yc;
   g.acc_out = s.acc_out;
   g.fx_scale = s.fx_scale;
-  const dim3 grid(p->rows_f / 64, p->rows_h / tc::kBM, p->fwd_splits);
-  e = launch_gemm<64, tc::kEpiFwd>(p->fwd, g, grid, st, chain);
+  const dim3 grid(p->rows_f / p->bn_fwd, p->rows_h / tc::kBM, p->fwd_splits);
+  e = launch_gemm_bn<tc::kEpiFwd>(p->bn_fwd, p->fwd, g, grid, st, chain);
   if (e == cudaSuccess) ++*kernels;
   return e;
 }
@@ -237,8 +264,10 @@ cudaError_t launch_iteration(Plan *p, const Step &s, cudaStream_t st, bool pdl, 
   pa.p_lo = p->p_lo;
   pa.inv_fx_n = s.inv_fx_n;
   pa.trace = s.trace;
+  // blocks take even shares of the rows (each block also forms all M coefficients)
   const long long pairs = (long long)p->H * (p->Kb / 2);
-  const int prep_blocks = (int)std::max<long long>(1, std::min<long long>((pairs + 1023) / 1024, 2LL * p->sms));
+  const int prep_blocks =
+      (int)std::max<long long>(1, std::min<long long>({(pairs + 255) / 256, 2LL * p->sms, (long long)p->H}));
   cudaError_t e = launch(tc::tc_prep_kernel, dim3(prep_blocks), tc::kPrepThreads, (int)(sizeof(float2) * p->M), st,
                          pdl, pa);
   if (e != cudaSuccess) return e;
@@ -257,8 +286,7 @@ cudaError_t launch_iteration(Plan *p, const Step &s, cudaStream_t st, bool pdl, 
   g.u_hi = p->u_hi;
   g.u_lo = p->u_lo;
   const dim3 grid_b(p->rows_b / p->bn_back, p->rows_h / tc::kBM, 1);
-  e = p->bn_back == 128 ? launch_gemm<128, tc::kEpiBack>(p->back, g, grid_b, st, chain)
-                        : launch_gemm<64, tc::kEpiBack>(p->back, g, grid_b, st, chain);
+  e = launch_gemm_bn<tc::kEpiBack>(p->bn_back, p->back, g, grid_b, st, chain);
   if (e != cudaSuccess) return e;
   ++*kernels;
   g = {};
@@ -275,8 +303,8 @@ cudaError_t launch_iteration(Plan *p, const Step &s, cudaStream_t st, bool pdl, 
   g.Yc = p->Yc;
   g.acc_out = s.acc_out;
   g.fx_scale = s.fx_scale;
-  const dim3 grid_f(p->rows_f / 64, p->rows_h / tc::kBM, p->fwd_splits);
-  e = launch_gemm<64, tc::kEpiFwd>(p->fwd, g, grid_f, st, chain);
+  const dim3 grid_f(p->rows_f / p->bn_fwd, p->rows_h / tc::kBM, p->fwd_splits);
+  e = launch_gemm_bn<tc::kEpiFwd>(p->bn_fwd, p->fwd, g, grid_f, st, chain);
   if (e == cudaSuccess) ++*kernels;
   return e;
 }
@@ -320,7 +348,13 @@ cudaError_t gemm(int rows, int cols, int K, const float *A, const float *B, floa
     g.err = err;
     g.C = C;
     const dim3 grid(rb / tile_n, ra / tc::kBM, 1);
-    if (tile_n == 128) {
+    if (tile_n == 32) {
+      e = set_smem<32, tc::kEpiPlain>();
+      if (e == cudaSuccess) e = launch_gemm<32, tc::kEpiPlain>(maps, g, grid, st, false);
+    } else if (tile_n == 256) {
+      e = set_smem<256, tc::kEpiPlain>();
+      if (e == cudaSuccess) e = launch_gemm<256, tc::kEpiPlain>(maps, g, grid, st, false);
+    } else if (tile_n == 128) {
       e = set_smem<128, tc::kEpiPlain>();
       if (e == cudaSuccess) e = launch_gemm<128, tc::kEpiPlain>(maps, g, grid, st, false);
     } else {

@@ -38,7 +38,7 @@ cudaError_t launch_forward(Plan *p, const Step &s, cudaStream_t st, bool pdl, bo
 cudaError_t launch_iteration(Plan *p, const Step &s, cudaStream_t st, bool pdl, bool chain, int *kernels);
 
 // C[rows][cols] = A[rows][K] B[cols][K]^T (device pointers, FP32) with the 3xTF32 tensor-core
-// GEMM of the iteration, tile width tile_n (64 or 128); synchronous, allocates its operands.
+// GEMM of the iteration, tile width tile_n (32, 64, 128 or 256); synchronous, allocates its operands.
 cudaError_t gemm(int rows, int cols, int K, const float *A, const float *B, float *C, int tile_n, cudaStream_t st,
                  int *timed_out, const char **what);
 

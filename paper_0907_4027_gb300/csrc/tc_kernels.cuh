@@ -18,14 +18,14 @@
 // A CTA computes one 128 x BN tile of a GEMM over a range of K, warp-specialised: one thread of
 // warp 0 issues TMA loads of 32-element K slices (128-byte rows, 128-byte swizzle) of A_hi, A_lo,
 // B_hi, B_lo into a ring of shared-memory stages; one thread of warp 1 issues the 12 MMAs of a
-// slice into one of two tensor-memory accumulators and returns the stage to the loader with
-// tcgen05.commit; warps 2-5 (TMEM lane quadrant = warp % 4, i.e. 32 rows each) drain every
-// slice's accumulator into FP32 registers while the MMAs of the next slice run in the other
-// accumulator.  The tensor core's own accumulation into TMEM is not round-to-nearest (measured:
+// slice into one of 2-4 tensor-memory accumulators and returns the stage to the loader with
+// tcgen05.commit; the drain warps (TMEM lane quadrant = warp % 4, i.e. 32 rows each, and a group
+// of <= 128 columns) add every slice's accumulator into FP32 registers while the MMAs of the next
+// slices run in the other accumulators.  The tensor core's own accumulation into TMEM is not round-to-nearest (measured:
 // a magnitude bias growing with the MMAs accumulated, ~1e-4 relative on small |V_m| after 190),
 // so each accumulator holds the 12 MMAs of one slice only and the K sum runs in the registers
 // (round-to-nearest, fixed order).  Then the epilogue:
-//   back:    phi = arg S (atan2), u = e^{i phi}, written as phases and as the split U operand;
+//   back:    phi = arg S (atan2f), u = e^{i phi}, written as phases and as the split U operand;
 //   forward: the tile's rows weighted by conj(Y_m(iy)) and summed, added into the 64-bit
 //            fixed-point field accumulators (integer atomics: exact and order-independent, so
 //            the K range may be split over CTAs);
@@ -43,19 +43,28 @@ namespace tc {
 constexpr int kBM = 128;     // rows of a tile: the 128 lanes of tensor memory
 constexpr int kBK = 32;      // K elements per stage (32 x 4 B = one 128-byte swizzle row)
 constexpr int kUmmaK = 8;    // K of one kind::tf32 MMA
-constexpr int kEpiWarps = 4;                      // warps that drain the accumulator (one TMEM lane quadrant each)
-constexpr int kThreads = 32 * (2 + kEpiWarps);   // warp 0: TMA loads, warp 1: MMAs, warps 2-5: epilogue
+
 constexpr int kEpiPlain = 0, kEpiBack = 1, kEpiFwd = 2;
 
+// Tile width BN (32, 64, 128 or 256 columns): shared-memory stages as fit in 192 KB; the accumulator
+// is drained by 4 warps per group of at most 128 columns (a thread keeps its row's columns of
+// the group in registers), so BN = 256 has two column groups and 8 drain warps.
 template <int BN>
 struct Cfg {
-  static_assert(BN == 64 || BN == 128, "tile width");
-  static constexpr int kStages = BN == 128 ? 3 : 4;
+  static_assert(BN == 32 || BN == 64 || BN == 128 || BN == 256, "tile width");
+  static constexpr int kStages = BN == 256 ? 2 : BN == 128 ? 3 : 4;
   static constexpr int kABytes = kBM * kBK * 4;  // 16 KB
   static constexpr int kBBytes = BN * kBK * 4;
   static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
   static constexpr int kSmem = kStages * kStageBytes + 1024;  // + slack to align the ring to 1 KB
+  static constexpr int kGroups = BN == 256 ? 2 : 1;           // column groups of the drain
+  static constexpr int kCols = BN / kGroups;                  // columns per drain warp
+  static constexpr int kEpiWarps = 4 * kGroups;               // one per TMEM lane quadrant and group
+  static constexpr int kThreads = 32 * (2 + kEpiWarps);       // warp 0: TMA, warp 1: MMA, then drain
+  static constexpr int kBufs = BN == 256 ? 2 : 4;             // accumulators in the 512 TMEM columns
+  static constexpr int kTmemCols = kBufs * BN;                // a power of two >= 32
 };
+struct BackStage;
 
 // The four operand maps of one GEMM (2-D, FP32, box 32 x rows, 128-byte swizzle).
 struct Maps {
@@ -182,6 +191,17 @@ __device__ __forceinline__ float2 split_tf32(float x) {
   return make_float2(hi, x - hi);
 }
 
+// u = e^{i phi} of a phase in any range: reduced to [-pi, pi] (Cody-Waite with 2 pi split in
+// two floats; a no-op for the back-projection's own phases in (-pi, pi]), then the SFU's
+// sin/cos approximations (|error| ~ 4e-7 on that interval).  The forward operand of the phases
+// a call starts from and of the phases an iteration writes come from this one function, so a
+// resumed run repeats the bits of an uninterrupted one.
+__device__ __forceinline__ void unit_phasor(float ph, float &sn, float &cs) {
+  const float k = rintf(ph * 0.15915494309189535f);
+  const float x = fmaf(-k, -1.74845553e-07f, fmaf(-k, 6.28318548e+00f, ph));
+  __sincosf(x, &sn, &cs);
+}
+
 // Stores a complex value split into the hi and lo operand arrays at float offset i (even).
 __device__ __forceinline__ void store_split(float *hi, float *lo, size_t i, float re, float im) {
   const float2 r = split_tf32(re), m = split_tf32(im);
@@ -189,42 +209,71 @@ __device__ __forceinline__ void store_split(float *hi, float *lo, size_t i, floa
   *reinterpret_cast<float2 *>(lo + i) = make_float2(r.y, m.y);
 }
 
-// 32 accumulator columns n0 .. n0+31 of one row: plain C, or (back) columns 2 ix, 2 ix + 1 =
-// Re S, Im S of pixel (ix, row) -> phi = arg S (Sec. 4; atan2(0, 0) = 0) and u = e^{i phi}.
-template <int EPI>
-__device__ __forceinline__ void epilogue_chunk(const GemmArgs &a, const float *v, int row, int n0) {
-  if (EPI == kEpiPlain) {
-    if (row < a.rows)
+// 32 accumulator columns n0 .. n0+31 of one row of the plain GEMM: C.
+__device__ __forceinline__ void epilogue_plain(const GemmArgs &a, const float *v, int row, int n0) {
+  if (row < a.rows)
 #pragma unroll
-      for (int c = 0; c < 32; c++)
-        if (n0 + c < a.cols) a.C[(size_t)row * a.cols + n0 + c] = v[c];
-  } else if (row < a.H) {
-    const int x0 = n0 >> 1;
-#pragma unroll
-    for (int p = 0; p < 16; p++) {
-      const int ix = x0 + p;
-      if (ix < a.W) {
-        const float ph = atan2f(v[2 * p + 1], v[2 * p]);
-        float sn, cs;
-        sincosf(ph, &sn, &cs);
-        a.phi[(size_t)row * a.W + ix] = ph;
-        store_split(a.u_hi, a.u_lo, (size_t)row * a.Kf + 2 * ix, cs, sn);
-      }
-    }
-  }
+    for (int c = 0; c < 32; c++)
+      if (n0 + c < a.cols) a.C[(size_t)row * a.cols + n0 + c] = v[c];
 }
 
-// Forward: columns 2 p, 2 p + 1 of the 64 hold Re, Im of T[row][m], m = n0/2 + p.  The terms
-// T conj(Y_m(row)) are summed over the tile's 128 rows (in each warp a transposed shuffle
-// reduction after which lane L holds trap L; then the four warps in order) and added into the
-// fixed-point sums with one atomic per trap and component.
-// q: the warp's TMEM lane quadrant; ok: its accumulator is complete; failed: the CTA's flag,
-// read after the epilogue warps' barrier (an incomplete tile adds nothing).
-__device__ __forceinline__ void epilogue_fwd(const GemmArgs &a, float *z, int row, int n0, float (*red)[64], int q,
-                                             bool ok, const int *failed) {
-  const int mt0 = n0 >> 1;
+// Back-projection: 32 accumulator columns n0 .. n0+31, columns 2 p, 2 p + 1 = Re S, Im S of pixel
+// ix = n0/2 + p of this thread's row -> phi = arg S (Sec. 4; atan2(0, 0) = 0) and u = e^{i phi}.
+// A thread holds one row, so the 16 pixels are first written to the warp's staging area in
+// shared memory (rows padded against bank conflicts) and then stored row segment by row segment:
+// each store instruction of the warp writes whole 32-byte sectors of one or two rows instead
+// of one word in each of 32 rows.
+struct BackStage {
+  float ph[32][17];  // phases of 16 pixels of 32 rows
+  float uh[32][33];  // (cos, sin) interleaved, TF32 high parts
+  float ul[32][33];  // and low parts
+};
+__device__ __forceinline__ void epilogue_back(const GemmArgs &a, const float *v, int row0, int n0, BackStage &st) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int p = 0; p < 32; p++) {
+  for (int p = 0; p < 16; p++) {
+    const float ph = atan2f(v[2 * p + 1], v[2 * p]);
+    float sn, cs;
+    unit_phasor(ph, sn, cs);
+    const float2 c2 = split_tf32(cs), s2 = split_tf32(sn);
+    st.ph[lane][p] = ph;
+    st.uh[lane][2 * p] = c2.x;
+    st.uh[lane][2 * p + 1] = s2.x;
+    st.ul[lane][2 * p] = c2.y;
+    st.ul[lane][2 * p + 1] = s2.y;
+  }
+  __syncwarp();
+  const int x0 = n0 >> 1;
+#pragma unroll 4
+  for (int i = 0; i < 16; i++) {  // phases: two rows of 16 pixels per instruction
+    const int r = 2 * i + (lane >> 4), p = lane & 15, iy = row0 + r, ix = x0 + p;
+    if (iy < a.H && ix < a.W) a.phi[(size_t)iy * a.W + ix] = st.ph[r][p];
+  }
+#pragma unroll 4
+  for (int r = 0; r < 32; r++) {  // operand: one row of 16 pixels (128 bytes) per instruction
+    const int iy = row0 + r, ix = x0 + (lane >> 1);
+    if (iy < a.H && ix < a.W) {
+      const size_t o = (size_t)iy * a.Kf + 2 * x0 + lane;
+      a.u_hi[o] = st.uh[r][lane];
+      a.u_lo[o] = st.ul[r][lane];
+    }
+  }
+  __syncwarp();
+}
+
+// Forward: the warp's COLS columns c0 .. c0+COLS-1 of the tile (2 p, 2 p + 1 = Re, Im of T[row][m],
+// m = (n0 + c0)/2 + p).  The terms T conj(Y_m(row)) are summed over the tile's 128 rows (in each
+// warp a transposed shuffle reduction after which lane L holds columns COLS/32 L ..; then the four
+// lane quadrants in order) and added into the fixed-point sums, one atomic per trap and component.
+// q: the warp's TMEM lane quadrant, g its column group; ok: its accumulator is complete; failed:
+// the CTA's flag, read after the drain warps' barrier (an incomplete tile adds nothing).
+template <int BN>
+__device__ __forceinline__ void epilogue_fwd(const GemmArgs &a, float *z, int row, int n0, float *red, int q, int g,
+                                             bool ok, const int *failed) {
+  constexpr int COLS = Cfg<BN>::kCols, PER = COLS / 32;
+  const int mt0 = (n0 + g * COLS) >> 1;
+#pragma unroll
+  for (int p = 0; p < COLS / 2; p++) {
     const int m = mt0 + p;
     const float tr = z[2 * p], ti = z[2 * p + 1];
     float zr = 0.f, zi = 0.f;
@@ -238,7 +287,7 @@ __device__ __forceinline__ void epilogue_fwd(const GemmArgs &a, float *z, int ro
   }
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int o = 16, n = 64; o >= 1; o >>= 1, n >>= 1) {
+  for (int o = 16, n = COLS; o >= 1; o >>= 1, n >>= 1) {
     const bool upper = (lane & o) != 0;
 #pragma unroll
     for (int i = 0; i < n / 2; i++) {
@@ -247,14 +296,16 @@ __device__ __forceinline__ void epilogue_fwd(const GemmArgs &a, float *z, int ro
       z[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
-  red[q][2 * lane] = z[0];
-  red[q][2 * lane + 1] = z[1];
-  asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");  // the epilogue warps only
-  const int t = q * 32 + lane;
-  if (t < 64 && !*(const volatile int *)failed) {
-    const int m = mt0 + (t >> 1);
+#pragma unroll
+  for (int i = 0; i < PER; i++) red[(g * 4 + q) * COLS + PER * lane + i] = z[i];
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * Cfg<BN>::kEpiWarps) : "memory");  // the drain warps only
+  const int t = threadIdx.x - 64;  // index among the drain threads
+  if (t < BN && !*(const volatile int *)failed) {
+    const int gg = t / COLS, j = t % COLS;
+    const int m = (n0 + t) >> 1;
     if (m < a.M) {
-      const float s = ((red[0][t] + red[1][t]) + red[2][t]) + red[3][t];
+      const float *r = red + gg * 4 * COLS + j;
+      const float s = ((r[0] + r[COLS]) + r[2 * COLS]) + r[3 * COLS];
       // |s| <= N, so s * 2^fx_shift rounds to an integer below 2^61
       atomicAdd(a.acc_out + (size_t)(t & 1) * a.M + m, (unsigned long long)__float2ll_rn(s * a.fx_scale));
     }
@@ -262,17 +313,16 @@ __device__ __forceinline__ void epilogue_fwd(const GemmArgs &a, float *z, int ro
 }
 
 // One 128 x BN output tile over a K range: TMA loader (warp 0, one lane), MMA issuer (warp 1,
-// one lane), accumulator drain and epilogue (warps 2-5).  grid = (N tiles, M tiles, K splits).
+// one lane), accumulator drain and epilogue (the other warps).  grid = (N tiles, M tiles, K splits).
 template <int BN, int EPI>
-__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ Maps maps,
-                                                               const __grid_constant__ GemmArgs a) {
+__global__ void __launch_bounds__(Cfg<BN>::kThreads, 1) tc_gemm_kernel(const __grid_constant__ Maps maps,
+                                                                       const __grid_constant__ GemmArgs a) {
   using C = Cfg<BN>;
-  static_assert(EPI != kEpiFwd || BN == 64, "the forward epilogue reduces 64 columns");
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[C::kStages], empty[C::kStages], tfull[2], tempty[2];
+  __shared__ __align__(8) uint64_t full[C::kStages], empty[C::kStages], tfull[C::kBufs], tempty[C::kBufs];
   __shared__ uint32_t tmem_slot;
   __shared__ int issued, consumed, failed;
-  __shared__ float red[kEpiWarps][64];
+  __shared__ float red[EPI == kEpiFwd ? 4 * BN : 1];
   // the ring starts on a 1 KB boundary of the shared window (the 128-byte swizzle pattern repeats
   // every 8 rows of 128 bytes and the descriptors assume aligned tiles)
   unsigned char *ring = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -285,18 +335,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; b++) {
+    for (int b = 0; b < C::kBufs; b++) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], kEpiWarps);
+      mbar_init(&tempty[b], C::kEpiWarps);
     }
     issued = consumed = failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a_hi)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b_hi)) : "memory");
   }
-  if (warp == 0) {  // the whole warp allocates two FP32 accumulators of BN columns
+  if (warp == 0) {  // the whole warp allocates kBufs FP32 accumulators of BN columns
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(2 * BN)
+                 "r"(C::kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -332,9 +382,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     if (lane == 0) {
       constexpr uint32_t idesc = instr_desc_tf32(kBM, BN);
       for (int i = 0; i < nk; i++) {
-        const int b = i & 1;
-        // accumulator b is free once the epilogue warps have drained its previous slice
-        if (i >= 2 && !mbar_wait(&tempty[b], (uint32_t)((i >> 1) - 1) & 1u, a.limit_ns)) {
+        const int b = i % C::kBufs;
+        // accumulator b is free once the drain warps have emptied its previous slice
+        if (i >= C::kBufs && !mbar_wait(&tempty[b], (uint32_t)(i / C::kBufs - 1) & 1u, a.limit_ns)) {
           failed = 1;
           break;
         }
@@ -364,21 +414,23 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     }
     __syncwarp();
   } else {
-    // drain: slice i's partial product (accumulator i & 1) added into registers in slice order
-    const int q = warp & 3;  // TMEM lane quadrant of this warp: rows 32q .. 32q+31
-    const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
-    float acc[BN];
+    // drain: slice i's partial product (accumulator i % kBufs) added into registers in slice order
+    constexpr int COLS = C::kCols;
+    const int q = warp & 3;          // TMEM lane quadrant of this warp: rows 32q .. 32q+31
+    const int g = (warp - 2) >> 2;   // its column group: columns g COLS .. (g+1) COLS - 1
+    const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * COLS);
+    float acc[COLS];
 #pragma unroll
-    for (int c = 0; c < BN; c++) acc[c] = 0.f;
+    for (int c = 0; c < COLS; c++) acc[c] = 0.f;
     bool ok = true;
     for (int i = 0; i < nk; i++) {
-      const int b = i & 1;
-      ok = mbar_wait(&tfull[b], (uint32_t)(i >> 1) & 1u, a.limit_ns);
+      const int b = i % C::kBufs;
+      ok = mbar_wait(&tfull[b], (uint32_t)(i / C::kBufs) & 1u, a.limit_ns);
       ok = __all_sync(0xffffffffu, ok) && !*(volatile int *)&failed;
       if (!ok) break;
       tc_fence_after();
 #pragma unroll
-      for (int c = 0; c < BN; c += 32) {
+      for (int c = 0; c < COLS; c += 32) {
         float v[32];
         tmem_load32(tq + (uint32_t)(b * BN + c), v);
 #pragma unroll
@@ -394,10 +446,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     }
     const int row = m0 + q * 32 + lane;
     if (EPI == kEpiFwd) {
-      epilogue_fwd(a, acc, row, n0, red, q, ok, &failed);
+      epilogue_fwd<BN>(a, acc, row, n0, red, q, g, ok, &failed);
+    } else if (EPI == kEpiBack && ok) {
+      static_assert(sizeof(BackStage) * C::kEpiWarps <= C::kStages * C::kStageBytes, "staging fits the ring");
+      // the ring is free: every MMA that read it has completed (the last slice was drained)
+      BackStage &st = reinterpret_cast<BackStage *>(ring)[warp - 2];
+#pragma unroll
+      for (int c = 0; c < COLS; c += 32) epilogue_back(a, acc + c, m0 + q * 32, n0 + g * COLS + c, st);
     } else if (ok) {
 #pragma unroll
-      for (int c = 0; c < BN; c += 32) epilogue_chunk<EPI>(a, acc + c, row, n0 + c);
+      for (int c = 0; c < COLS; c += 32) epilogue_plain(a, acc + c, row, n0 + g * COLS + c);
     }
   }
   __syncthreads();
@@ -410,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kTmemCols) : "memory");
   }
 }
 
@@ -465,7 +523,7 @@ __global__ void tc_tables_kernel(TableArgs a) {
   }
 }
 
-// The forward operand of given phases: u = e^{i phi} (sincosf), split; and one accumulator
+// The forward operand of given phases: u = e^{i phi} (unit_phasor), split; and one accumulator
 // buffer cleared for the launch after next.
 __global__ void tc_phase_kernel(int W, int H, int Kf, const float *phi, float *u_hi, float *u_lo,
                                 unsigned long long *acc_clear, int n_clear) {
@@ -474,7 +532,7 @@ __global__ void tc_phase_kernel(int W, int H, int Kf, const float *phi, float *u
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N; j += stride) {
     const int iy = (int)(j / W), ix = (int)(j % W);
     float sn, cs;
-    sincosf(phi[j], &sn, &cs);
+    unit_phasor(phi[j], sn, cs);
     store_split(u_hi, u_lo, (size_t)iy * Kf + 2 * ix, cs, sn);
   }
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_clear; i += stride) acc_clear[i] = 0ull;
@@ -576,13 +634,17 @@ __global__ void __launch_bounds__(kPrepThreads) tc_prep_kernel(PrepArgs a) {
   const long long stride = (long long)gridDim.x * kPrepThreads;
   for (long long i = blockIdx.x * (long long)kPrepThreads + t; i < 2LL * a.M; i += stride) a.acc_clear[i] = 0ull;
   __syncthreads();
+  // this block's rows: an even share of the H rows, all Kb/2 (padded) traps of each
   const int half = a.Kb / 2;
-  const long long total = (long long)a.H * half;
-  for (long long j = blockIdx.x * (long long)kPrepThreads + t; j < total; j += stride) {
-    const int m = (int)(j % half);
+  const int r0 = (int)((long long)a.H * blockIdx.x / gridDim.x);
+  const int r1 = (int)((long long)a.H * (blockIdx.x + 1) / gridDim.x);
+  const int n = (r1 - r0) * half;
+  for (int i = t; i < n; i += kPrepThreads) {
+    const int iy = r0 + i / half, m = i - (i / half) * half;
     const float2 c = m < a.M ? cs[m] : make_float2(0.f, 0.f);
+    const size_t j = (size_t)iy * half + m;
     const float2 y = __ldg(a.YT + j);
-    store_split(a.p_hi, a.p_lo, 2 * (size_t)j, c.x * y.x - c.y * y.y, c.x * y.y + c.y * y.x);
+    store_split(a.p_hi, a.p_lo, 2 * j, c.x * y.x - c.y * y.y, c.x * y.y + c.y * y.x);
   }
   grid_release();
 }

@@ -43,8 +43,8 @@ def gemm(hot, A, B, tile_n):
     return c.cpu().numpy()
 
 
-@pytest.mark.parametrize("tile_n", [64, 128])
-@pytest.mark.parametrize("rows,cols,K", [(128, 64, 32), (200, 130, 75), (1, 1, 1), (257, 300, 96)])
+@pytest.mark.parametrize("tile_n", [32, 64, 128, 256])
+@pytest.mark.parametrize("rows,cols,K", [(128, 64, 32), (200, 130, 75), (1, 1, 1), (257, 300, 96), (300, 520, 200)])
 def test_gemm_exact_on_small_integers(hot, rows, cols, K, tile_n):
     rng = np.random.default_rng(rows * 7 + cols + K)
     A = rng.integers(-8, 9, size=(rows, K)).astype(np.float32)
@@ -53,7 +53,7 @@ def test_gemm_exact_on_small_integers(hot, rows, cols, K, tile_n):
     assert np.array_equal(C, (A.astype(np.int64) @ B.astype(np.int64).T).astype(np.float32))
 
 
-@pytest.mark.parametrize("tile_n", [64, 128])
+@pytest.mark.parametrize("tile_n", [32, 64, 128, 256])
 @pytest.mark.parametrize("rows,cols,K", [(300, 200, 1000), (130, 70, 33)])
 def test_gemm_within_3xtf32_bound(hot, rows, cols, K, tile_n):
     rng = np.random.default_rng(rows + cols + K)
@@ -78,10 +78,12 @@ def check_phase_step(gpu_phi, w, coef):
 
 
 @pytest.mark.parametrize("W,H,M", [(100, 37, 13), (64, 16, 1), (33, 9, 7), (40, 24, 300), (1, 1, 5),
-                                   (257, 3, 9), (5, 70, 129), (300, 260, 70), (2048, 1280, 64)])
+                                   (257, 3, 9), (5, 70, 129), (300, 260, 70), (2048, 1280, 64),
+                                   (1600, 1300, 128)])
 def test_one_iteration_matches_oracle(hot, W, H, M):
-    """Ragged tiles in both directions, one and several K splits, both back-GEMM tile widths
-    (2048 x 1280 takes the 128-wide tiles)."""
+    """Ragged tiles in both directions, one and several K splits, the tile widths (2048 x 1280
+    takes 256-wide back-projection tiles and 128-wide forward tiles, 1600 x 1300 with 128 traps
+    256-wide tiles in both, the small cases 32-wide tiles)."""
     w = wl.random_case(W, H, M, seed=W + H + M, precision="tensor")
     with hot.Hologram.from_workload(w) as h:
         e0, u0 = h.gsw(0)
