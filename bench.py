@@ -11,6 +11,8 @@ reported beside it.  --gpus N > 1 runs N independent replicas (one per rank; the
 no exchange step), timed between barriers, max over ranks.
 
 --impl reference times the FP64 CPU oracle on the host cores instead (bounded sample).
+--single K runs hot_gsw(K) once on the workload (no timing): the program that the ncu
+summaries under profiles/ capture.
 """
 from __future__ import annotations
 
@@ -56,6 +58,8 @@ def parse():
                     help="errors of both precision modes against the FP64 oracle, per result")
     ap.add_argument("--grid-sweep", action="store_true",
                     help="efficiency and uniformity vs trap count on n x n grids (n = 2..9, 768^2 SLM)")
+    ap.add_argument("--single", type=int, default=0, metavar="K",
+                    help="run hot_gsw(K) once on the workload and print e, u (no timing; for profilers)")
     ap.add_argument("--cpu-sample-iters", type=int, default=0,
                     help="GSW iterations of the CPU-baseline sample (0: the workload's own count)")
     return ap.parse_args()
@@ -183,21 +187,23 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- engine (GPU)
 
-def kernel_source_hash() -> str:
-    src = os.path.join(ROOT, "paper_0907_4027_gb300", "csrc", "gsw_kernels.cuh")
+def kernel_source_hash(kernel: str = "step") -> str:
+    name = "tc_kernels.cuh" if kernel == "tc" else "gsw_kernels.cuh"
+    src = os.path.join(ROOT, "paper_0907_4027_gb300", "csrc", name)
     return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
 
 def profiled_traffic(workload: str, kernel: str = "step"):
-    """DRAM bytes per launch of the fused step kernel (gsw_step / gsw_sep) from the committed
-    ncu summary, if the summary was taken on the current kernel source (else None)."""
+    """DRAM bytes per launch of the fused step kernel (gsw_step / gsw_sep), or per iteration of
+    the tensor mode's three kernels (gsw_tc), from the committed ncu summary, if the summary was
+    taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", f"gsw_{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not h or not b or h.group(1) != kernel_source_hash():
+    if not h or not b or h.group(1) != kernel_source_hash(kernel):
         return None
     return float(b.group(1))
 
@@ -692,10 +698,28 @@ def run_batch(args):
     return 0
 
 
+def run_single(args):
+    """One hot_gsw(K) call on the workload (trap tables, starting phases, K iterations, e and u)."""
+    import torch
+    from paper_0907_4027_gb300 import _build
+    _build.build()
+    from paper_0907_4027_gb300 import hot, workloads as wl
+    w = wl.NAMED[args.workload]()
+    if args.precision:
+        w.precision = args.precision
+    with hot.Hologram.from_workload(w, torch.cuda.current_stream().cuda_stream) as h:
+        e, u = h.gsw(args.single)
+        print(json.dumps({"workload": w.name, "precision": w.precision, "iters": args.single, "e": e, "u": u,
+                          "kernels": h.launches}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.single:
+        return run_single(args)
     if args.workload == "batch64":
         return run_batch(args)
     if args.grid_sweep:
