@@ -53,8 +53,8 @@ typedef enum {
                              complex tables (FP64 cos/sin once per entry); per pair one complex
                              multiply-add in each step, no transcendental function */
   HOT_PREC_TENSOR = 3      /* the separable form on the tensor cores: each step of a GSW iteration
-                             is a complex matrix product (S = P X, T = U X^H) run as tcgen05 TF32
-                             MMAs with every operand split in two TF32 parts (three MMAs per
+                             is a complex matrix product (S = P X, T = U X^H) run as tcgen05 FP16
+                             MMAs with every operand split in two FP16 parts (three MMAs per
                              product, FP32 accumulation); the GSW loop only (hot_gsw), other
                              calls run the separable kernels */
 } hot_precision;
@@ -93,7 +93,7 @@ int hot_set_phase(hot_ctx *c, const float *phi, int on_device);
  * rebuilds the work schedule).  HOT_EINVAL for another value.  In HOT_PREC_TENSOR mode hot_gsw
  * runs three kernels per iteration (weight update and operand P, back-projection GEMM with the
  * phases in its epilogue, forward GEMM with the field sums in its epilogue); its operands
- * (about 8 (2W + 2M)(2M + 2W) + 16 H (W + M) bytes) are built on the first hot_gsw after the
+ * (about 4 (2W + 2M)(2M + 2W) + 8 H (W + M) + 8 H M bytes) are built on the first hot_gsw after the
  * traps are set.  HOT_PREC_TENSOR rejects the persistent form (hot_use_persistent), row-band
  * steps (hot_sharded_begin), batches (hot_batch_create) and hot_autotune with HOT_EINVAL. */
 int hot_set_precision(hot_ctx *c, int precision);
@@ -329,12 +329,18 @@ int hot_sfu_rate(int op, double *per_clk_per_sm, int *sms);
 
 /* The matrix product of HOT_PREC_TENSOR on its own (no counterpart in the paper):
  * C = A B^T for DEVICE float32 arrays A [rows][K], B [cols][K] (row-major) into C [rows][cols],
- * on the tcgen05 tensor cores with every operand split into two TF32 parts (a b ~ a_hi b_hi +
- * a_hi b_lo + a_lo b_hi, FP32 accumulation), tiles of 128 x tile_n (32, 64, 128 or 256).  rows, cols,
- * K >= 1.  Allocates its split operands, synchronises cuda_stream (a cudaStream_t or NULL) and
- * frees them before returning.  HOT_ETIMEOUT if a bounded device-side wait ran out. */
-int hot_tf32x3_gemm(int rows, int cols, int K, const float *A, const float *B, float *C, int tile_n,
-                    void *cuda_stream);
+ * on the tcgen05 tensor cores with every operand split into two parts (a b ~ a_hi b_hi +
+ * a_hi b_lo + a_lo b_hi, FP32 accumulation, each K slice's partial product added in FP32
+ * registers), tiles of 128 x tile_n (32, 64, 128 or 256).  operands: HOT_TC_TF32 (two TF32
+ * parts, kind::tf32; the FP32 exponent range) or HOT_TC_FP16 (two FP16 parts, kind::f16 at twice
+ * the rate; the FP16 range: |x| < 65504, and precision drops for |x| below ~0.25, where the low
+ * part is subnormal -- the mode uses it on operands of magnitude ~1).  rows, cols, K >= 1.
+ * Allocates its split operands, synchronises cuda_stream (a cudaStream_t or NULL) and frees
+ * them before returning.  HOT_ETIMEOUT if a bounded device-side wait ran out. */
+#define HOT_TC_TF32 0
+#define HOT_TC_FP16 1
+int hot_tc_gemm(int rows, int cols, int K, const float *A, const float *B, float *C, int tile_n, int operands,
+                void *cuda_stream);
 
 /* Text of the last error on the calling thread ("" if none). */
 const char *hot_last_error(void);

@@ -1738,22 +1738,24 @@ __global__ void __launch_bounds__(1024) sfu_rate_kernel(float *out, long long *c
 
 }  // namespace
 
-extern "C" int hot_tf32x3_gemm(int rows, int cols, int K, const float *A, const float *B, float *C, int tile_n,
-                               void *cuda_stream) {
-  if (rows < 1 || cols < 1 || K < 1) return fail(HOT_EINVAL, "hot_tf32x3_gemm: sizes %d x %d x %d", rows, cols, K);
-  if (!A || !B || !C) return fail(HOT_EINVAL, "hot_tf32x3_gemm: NULL argument");
+extern "C" int hot_tc_gemm(int rows, int cols, int K, const float *A, const float *B, float *C, int tile_n,
+                           int operands, void *cuda_stream) {
+  if (rows < 1 || cols < 1 || K < 1) return fail(HOT_EINVAL, "hot_tc_gemm: sizes %d x %d x %d", rows, cols, K);
+  if (!A || !B || !C) return fail(HOT_EINVAL, "hot_tc_gemm: NULL argument");
   if (tile_n != 32 && tile_n != 64 && tile_n != 128 && tile_n != 256)
-    return fail(HOT_EINVAL, "hot_tf32x3_gemm: tile_n = %d not 32, 64, 128 or 256", tile_n);
+    return fail(HOT_EINVAL, "hot_tc_gemm: tile_n = %d not 32, 64, 128 or 256", tile_n);
+  if (operands != HOT_TC_TF32 && operands != HOT_TC_FP16)
+    return fail(HOT_EINVAL, "hot_tc_gemm: operands = %d not HOT_TC_TF32 or HOT_TC_FP16", operands);
   if ((long long)rows * K >= (1LL << 31) || (long long)cols * K >= (1LL << 31) || (long long)rows * cols >= (1LL << 31))
-    return fail(HOT_EINVAL, "hot_tf32x3_gemm: operands of 2^31 elements or more");
+    return fail(HOT_EINVAL, "hot_tc_gemm: operands of 2^31 elements or more");
   int timed_out = 0;
   const char *what = "";
-  const cudaError_t e = hot_tc::gemm(rows, cols, K, A, B, C, tile_n, static_cast<cudaStream_t>(cuda_stream),
-                                     &timed_out, &what);
+  const cudaError_t e = hot_tc::gemm(rows, cols, K, A, B, C, tile_n, operands == HOT_TC_FP16 ? 1 : 0,
+                                     static_cast<cudaStream_t>(cuda_stream), &timed_out, &what);
   if (e != cudaSuccess)
-    return fail(e == cudaErrorMemoryAllocation ? HOT_ENOMEM : HOT_ECUDA, "hot_tf32x3_gemm: %s: %s", what,
+    return fail(e == cudaErrorMemoryAllocation ? HOT_ENOMEM : HOT_ECUDA, "hot_tc_gemm: %s: %s", what,
                 cudaGetErrorString(e));
-  if (timed_out) return fail(HOT_ETIMEOUT, "hot_tf32x3_gemm: a bounded device-side wait ran out");
+  if (timed_out) return fail(HOT_ETIMEOUT, "hot_tc_gemm: a bounded device-side wait ran out");
   return HOT_OK;
 }
 

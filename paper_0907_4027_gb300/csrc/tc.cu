@@ -9,16 +9,22 @@
 
 namespace hot_tc {
 
+// Operand type of the GSW iteration's GEMMs: FP16 halves (kind::f16, twice the TF32 rate; the
+// operands are unit phasors and coefficients normalised to max |c_m| = 1).
+constexpr int kPlanOp = tc::kOpF16;
+constexpr int kSliceK = tc::slice_k<kPlanOp>();
+constexpr size_t kElem = tc::Op<kPlanOp>::kBytes;
+
 struct Plan {
   int W = 0, H = 0, M = 0;
-  int Kb = 0, Kf = 0;               // K of the back GEMM (2M padded to 32) and forward GEMM (2W padded)
+  int Kb = 0, Kf = 0;               // K of the back GEMM (2M) and forward GEMM (2W), padded to a K slice
   int rows_h = 0;                   // H padded to the tile height (rows of P and U)
   int bn_back = 64, bn_fwd = 64;    // tile widths of the back and forward GEMMs
   int rows_b = 0, rows_f = 0;       // rows of Bb (2W) and Bf (2M), padded to the tile width
   int fwd_splits = 1, fwd_cps = 1;  // K splits of the forward GEMM, K slices per split
   int sms = 0;
-  float *bb_hi = nullptr, *bb_lo = nullptr, *bf_hi = nullptr, *bf_lo = nullptr;
-  float *p_hi = nullptr, *p_lo = nullptr, *u_hi = nullptr, *u_lo = nullptr;
+  void *bb_hi = nullptr, *bb_lo = nullptr, *bf_hi = nullptr, *bf_lo = nullptr;  // operand elements
+  void *p_hi = nullptr, *p_lo = nullptr, *u_hi = nullptr, *u_lo = nullptr;
   float2 *YT = nullptr;
   const float2 *Xc = nullptr, *Yc = nullptr;  // the context's complex tables [M][W], [M][H]
   tc::Maps back{}, fwd{};
@@ -41,17 +47,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// A row-major FP32 matrix [rows][inner] (inner a multiple of 32, base 16-byte aligned) read in
-// boxes of 32 x box_rows with 128-byte swizzle; rows is a multiple of box_rows, so no box leaves
-// the matrix.
-cudaError_t encode(CUtensorMap *map, const float *base, int inner, int rows, int box_rows) {
+// A row-major operand matrix [rows][inner] of OP elements (inner a multiple of one K slice, base
+// 16-byte aligned) read in boxes of one 128-byte K slice x box_rows with 128-byte swizzle; rows
+// is a multiple of box_rows, so no box leaves the matrix.
+template <int OP>
+cudaError_t encode(CUtensorMap *map, const void *base, int inner, int rows, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)inner * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)tc::kBK, (cuuint32_t)box_rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)inner * tc::Op<OP>::kBytes};
+  const cuuint32_t box[2] = {(cuuint32_t)tc::slice_k<OP>(), (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+  const CUtensorMapDataType dt = OP == tc::kOpF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUresult r = fn(map, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -74,9 +82,9 @@ cudaError_t launch(void (*kernel)(KArgs...), dim3 grid, int block, int smem, cud
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-template <int BN, int EPI>
+template <int BN, int EPI, int OP = kPlanOp>
 cudaError_t set_smem() {
-  return cudaFuncSetAttribute(tc::tc_gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(tc::tc_gemm_kernel<BN, EPI, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               tc::Cfg<BN>::kSmem);
 }
 
@@ -84,10 +92,11 @@ template <typename T>
 cudaError_t alloc(T **p, size_t count) {
   return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
 }
+cudaError_t alloc_bytes(void **p, size_t bytes) { return cudaMalloc(p, bytes); }
 
-template <int BN, int EPI>
+template <int BN, int EPI, int OP = kPlanOp>
 cudaError_t launch_gemm(const tc::Maps &maps, const tc::GemmArgs &g, dim3 grid, cudaStream_t st, bool pdl) {
-  return launch(tc::tc_gemm_kernel<BN, EPI>, grid, tc::Cfg<BN>::kThreads, tc::Cfg<BN>::kSmem, st, pdl, maps, g);
+  return launch(tc::tc_gemm_kernel<BN, EPI, OP>, grid, tc::Cfg<BN>::kThreads, tc::Cfg<BN>::kSmem, st, pdl, maps, g);
 }
 
 template <int EPI>
@@ -117,7 +126,7 @@ int pick_width(int rows, int cols, int k_chunks, int sms, bool split_k) {
 
 void plan_destroy(Plan *p) {
   if (!p) return;
-  for (float *b : {p->bb_hi, p->bb_lo, p->bf_hi, p->bf_lo, p->p_hi, p->p_lo, p->u_hi, p->u_lo})
+  for (void *b : {p->bb_hi, p->bb_lo, p->bf_hi, p->bf_lo, p->p_hi, p->p_lo, p->u_hi, p->u_lo})
     if (b) cudaFree(b);
   if (p->YT) cudaFree(p->YT);
   delete p;
@@ -141,7 +150,7 @@ cudaError_t plan_refresh(Plan *p, cudaStream_t st) {
   t.YT = p->YT;
   const long long total = (long long)p->rows_b * p->Kb + (long long)p->rows_f * p->Kf + (long long)p->H * (p->Kb / 2);
   const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * p->sms);
-  return launch(tc::tc_tables_kernel, dim3(blocks), 256, 0, st, false, t);
+  return launch(tc::tc_tables_kernel<kPlanOp>, dim3(blocks), 256, 0, st, false, t);
 }
 
 cudaError_t plan_create(Plan **out, int W, int H, int M, const float2 *Xc, const float2 *Yc, cudaStream_t st,
@@ -153,53 +162,53 @@ cudaError_t plan_create(Plan **out, int W, int H, int M, const float2 *Xc, const
   p->M = M;
   p->Xc = Xc;
   p->Yc = Yc;
-  p->Kb = round_up(2 * M, tc::kBK);
-  p->Kf = round_up(2 * W, tc::kBK);
+  p->Kb = round_up(2 * M, kSliceK);
+  p->Kf = round_up(2 * W, kSliceK);
   p->rows_h = round_up(H, tc::kBM);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev);
-  p->bn_back = pick_width(H, 2 * W, p->Kb / tc::kBK, p->sms, false);
-  p->bn_fwd = pick_width(H, 2 * M, p->Kf / tc::kBK, p->sms, true);
+  p->bn_back = pick_width(H, 2 * W, p->Kb / kSliceK, p->sms, false);
+  p->bn_fwd = pick_width(H, 2 * M, p->Kf / kSliceK, p->sms, true);
   p->rows_b = round_up(2 * W, p->bn_back);
   p->rows_f = round_up(2 * M, p->bn_fwd);
   // forward GEMM: the K range split over CTAs so that the tiles fill the SMs about once
   const int tiles_f = (p->rows_h / tc::kBM) * (p->rows_f / p->bn_fwd);
-  const int kcf = p->Kf / tc::kBK;
+  const int kcf = p->Kf / kSliceK;
   const int splits = std::max(1, std::min(kcf, p->sms / std::max(tiles_f, 1)));
   p->fwd_cps = (kcf + splits - 1) / splits;
   p->fwd_splits = (kcf + p->fwd_cps - 1) / p->fwd_cps;  // every split has >= 1 slice
   *what = "allocating the tensor-core operands";
   const size_t nb = (size_t)p->rows_b * p->Kb, nf = (size_t)p->rows_f * p->Kf;
   const size_t np = (size_t)p->rows_h * p->Kb, nu = (size_t)p->rows_h * p->Kf;
-  if (e == cudaSuccess) e = alloc(&p->bb_hi, nb);
-  if (e == cudaSuccess) e = alloc(&p->bb_lo, nb);
-  if (e == cudaSuccess) e = alloc(&p->bf_hi, nf);
-  if (e == cudaSuccess) e = alloc(&p->bf_lo, nf);
-  if (e == cudaSuccess) e = alloc(&p->p_hi, np);
-  if (e == cudaSuccess) e = alloc(&p->p_lo, np);
-  if (e == cudaSuccess) e = alloc(&p->u_hi, nu);
-  if (e == cudaSuccess) e = alloc(&p->u_lo, nu);
+  if (e == cudaSuccess) e = alloc_bytes(&p->bb_hi, nb * kElem);
+  if (e == cudaSuccess) e = alloc_bytes(&p->bb_lo, nb * kElem);
+  if (e == cudaSuccess) e = alloc_bytes(&p->bf_hi, nf * kElem);
+  if (e == cudaSuccess) e = alloc_bytes(&p->bf_lo, nf * kElem);
+  if (e == cudaSuccess) e = alloc_bytes(&p->p_hi, np * kElem);
+  if (e == cudaSuccess) e = alloc_bytes(&p->p_lo, np * kElem);
+  if (e == cudaSuccess) e = alloc_bytes(&p->u_hi, nu * kElem);
+  if (e == cudaSuccess) e = alloc_bytes(&p->u_lo, nu * kElem);
   if (e == cudaSuccess) e = alloc(&p->YT, (size_t)H * (p->Kb / 2));
   // padding rows and columns of P and U stay zero (the kernels write only the image)
-  if (e == cudaSuccess) e = cudaMemsetAsync(p->p_hi, 0, np * sizeof(float), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(p->p_lo, 0, np * sizeof(float), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(p->u_hi, 0, nu * sizeof(float), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(p->u_lo, 0, nu * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->p_hi, 0, np * kElem, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->p_lo, 0, np * kElem, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->u_hi, 0, nu * kElem, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->u_lo, 0, nu * kElem, st);
   if (e == cudaSuccess) {
     *what = "building the tensor-core operand tables";
     e = plan_refresh(p, st);
   }
   if (e == cudaSuccess) {
     *what = "encoding the tensor maps";
-    e = encode(&p->back.a_hi, p->p_hi, p->Kb, p->rows_h, tc::kBM);
-    if (e == cudaSuccess) e = encode(&p->back.a_lo, p->p_lo, p->Kb, p->rows_h, tc::kBM);
-    if (e == cudaSuccess) e = encode(&p->back.b_hi, p->bb_hi, p->Kb, p->rows_b, p->bn_back);
-    if (e == cudaSuccess) e = encode(&p->back.b_lo, p->bb_lo, p->Kb, p->rows_b, p->bn_back);
-    if (e == cudaSuccess) e = encode(&p->fwd.a_hi, p->u_hi, p->Kf, p->rows_h, tc::kBM);
-    if (e == cudaSuccess) e = encode(&p->fwd.a_lo, p->u_lo, p->Kf, p->rows_h, tc::kBM);
-    if (e == cudaSuccess) e = encode(&p->fwd.b_hi, p->bf_hi, p->Kf, p->rows_f, p->bn_fwd);
-    if (e == cudaSuccess) e = encode(&p->fwd.b_lo, p->bf_lo, p->Kf, p->rows_f, p->bn_fwd);
+    e = encode<kPlanOp>(&p->back.a_hi, p->p_hi, p->Kb, p->rows_h, tc::kBM);
+    if (e == cudaSuccess) e = encode<kPlanOp>(&p->back.a_lo, p->p_lo, p->Kb, p->rows_h, tc::kBM);
+    if (e == cudaSuccess) e = encode<kPlanOp>(&p->back.b_hi, p->bb_hi, p->Kb, p->rows_b, p->bn_back);
+    if (e == cudaSuccess) e = encode<kPlanOp>(&p->back.b_lo, p->bb_lo, p->Kb, p->rows_b, p->bn_back);
+    if (e == cudaSuccess) e = encode<kPlanOp>(&p->fwd.a_hi, p->u_hi, p->Kf, p->rows_h, tc::kBM);
+    if (e == cudaSuccess) e = encode<kPlanOp>(&p->fwd.a_lo, p->u_lo, p->Kf, p->rows_h, tc::kBM);
+    if (e == cudaSuccess) e = encode<kPlanOp>(&p->fwd.b_hi, p->bf_hi, p->Kf, p->rows_f, p->bn_fwd);
+    if (e == cudaSuccess) e = encode<kPlanOp>(&p->fwd.b_lo, p->bf_lo, p->Kf, p->rows_f, p->bn_fwd);
   }
   if (e == cudaSuccess) {
     *what = "setting the tensor-core kernels' shared memory";
@@ -225,14 +234,14 @@ cudaError_t launch_forward(Plan *p, const Step &s, cudaStream_t st, bool pdl, bo
   *kernels = 0;
   const long long N = (long long)p->W * p->H;
   const int blocks = (int)std::min<long long>((N + 255) / 256, 8LL * p->sms);
-  cudaError_t e = launch(tc::tc_phase_kernel, dim3(blocks), 256, 0, st, pdl, p->W, p->H, p->Kf, (const float *)s.phi,
-                         p->u_hi, p->u_lo, s.acc_clear, 2 * s.M);
+  cudaError_t e = launch(tc::tc_phase_kernel<kPlanOp>, dim3(blocks), 256, 0, st, pdl, p->W, p->H, p->Kf,
+                         (const float *)s.phi, p->u_hi, p->u_lo, s.acc_clear, 2 * s.M);
   if (e != cudaSuccess) return e;
   ++*kernels;
   tc::GemmArgs g = {};
   g.rows = p->H;
   g.cols = 2 * p->M;
-  g.k_chunks = p->Kf / tc::kBK;
+  g.k_chunks = p->Kf / kSliceK;
   g.chunks_per_split = p->fwd_cps;
   g.limit_ns = s.limit_ns;
   g.err = s.err;
@@ -268,14 +277,14 @@ cudaError_t launch_iteration(Plan *p, const Step &s, cudaStream_t st, bool pdl, 
   const long long pairs = (long long)p->H * (p->Kb / 2);
   const int prep_blocks =
       (int)std::max<long long>(1, std::min<long long>({(pairs + 255) / 256, 2LL * p->sms, (long long)p->H}));
-  cudaError_t e = launch(tc::tc_prep_kernel, dim3(prep_blocks), tc::kPrepThreads, (int)(sizeof(float2) * p->M), st,
-                         pdl, pa);
+  cudaError_t e = launch(tc::tc_prep_kernel<kPlanOp>, dim3(prep_blocks), tc::kPrepThreads,
+                         (int)(sizeof(float2) * p->M), st, pdl, pa);
   if (e != cudaSuccess) return e;
   ++*kernels;
   tc::GemmArgs g = {};
   g.rows = p->H;
   g.cols = 2 * p->W;
-  g.k_chunks = p->Kb / tc::kBK;
+  g.k_chunks = p->Kb / kSliceK;
   g.chunks_per_split = g.k_chunks;
   g.limit_ns = s.limit_ns;
   g.err = s.err;
@@ -292,7 +301,7 @@ cudaError_t launch_iteration(Plan *p, const Step &s, cudaStream_t st, bool pdl, 
   g = {};
   g.rows = p->H;
   g.cols = 2 * p->M;
-  g.k_chunks = p->Kf / tc::kBK;
+  g.k_chunks = p->Kf / kSliceK;
   g.chunks_per_split = p->fwd_cps;
   g.limit_ns = s.limit_ns;
   g.err = s.err;
@@ -309,57 +318,62 @@ cudaError_t launch_iteration(Plan *p, const Step &s, cudaStream_t st, bool pdl, 
   return e;
 }
 
-cudaError_t gemm(int rows, int cols, int K, const float *A, const float *B, float *C, int tile_n, cudaStream_t st,
-                 int *timed_out, const char **what) {
+namespace {
+
+template <int OP>
+cudaError_t gemm_op(int rows, int cols, int K, const float *A, const float *B, float *C, int tile_n, cudaStream_t st,
+                    int *timed_out, const char **what) {
   *timed_out = 0;
-  const int Kp = round_up(K, tc::kBK), ra = round_up(rows, tc::kBM), rb = round_up(cols, tile_n);
-  float *buf[4] = {nullptr, nullptr, nullptr, nullptr};
+  constexpr int sk = tc::slice_k<OP>();
+  const int Kp = round_up(K, sk), ra = round_up(rows, tc::kBM), rb = round_up(cols, tile_n);
+  void *buf[4] = {nullptr, nullptr, nullptr, nullptr};
   int *err = nullptr;
   *what = "allocating the GEMM operands";
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 4 && e == cudaSuccess; i++) e = alloc(&buf[i], (size_t)(i < 2 ? ra : rb) * Kp);
+  for (int i = 0; i < 4 && e == cudaSuccess; i++)
+    e = alloc_bytes(&buf[i], (size_t)(i < 2 ? ra : rb) * Kp * tc::Op<OP>::kBytes);
   if (e == cudaSuccess) e = alloc(&err, 1);
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
   if (e == cudaSuccess) {
     *what = "splitting the GEMM operands";
     const long long ta = (long long)ra * Kp, tb = (long long)rb * Kp;
-    e = launch(tc::tc_split_kernel, dim3((int)std::min<long long>((ta + 255) / 256, 4096)), 256, 0, st, false, A, rows,
-               K, Kp, ta, buf[0], buf[1]);
+    e = launch(tc::tc_split_kernel<OP>, dim3((int)std::min<long long>((ta + 255) / 256, 4096)), 256, 0, st, false, A,
+               rows, K, Kp, ta, buf[0], buf[1]);
     if (e == cudaSuccess)
-      e = launch(tc::tc_split_kernel, dim3((int)std::min<long long>((tb + 255) / 256, 4096)), 256, 0, st, false, B,
+      e = launch(tc::tc_split_kernel<OP>, dim3((int)std::min<long long>((tb + 255) / 256, 4096)), 256, 0, st, false, B,
                  cols, K, Kp, tb, buf[2], buf[3]);
   }
   tc::Maps maps{};
   if (e == cudaSuccess) {
     *what = "encoding the GEMM tensor maps";
-    e = encode(&maps.a_hi, buf[0], Kp, ra, tc::kBM);
-    if (e == cudaSuccess) e = encode(&maps.a_lo, buf[1], Kp, ra, tc::kBM);
-    if (e == cudaSuccess) e = encode(&maps.b_hi, buf[2], Kp, rb, tile_n);
-    if (e == cudaSuccess) e = encode(&maps.b_lo, buf[3], Kp, rb, tile_n);
+    e = encode<OP>(&maps.a_hi, buf[0], Kp, ra, tc::kBM);
+    if (e == cudaSuccess) e = encode<OP>(&maps.a_lo, buf[1], Kp, ra, tc::kBM);
+    if (e == cudaSuccess) e = encode<OP>(&maps.b_hi, buf[2], Kp, rb, tile_n);
+    if (e == cudaSuccess) e = encode<OP>(&maps.b_lo, buf[3], Kp, rb, tile_n);
   }
   if (e == cudaSuccess) {
     *what = "running the GEMM";
     tc::GemmArgs g = {};
     g.rows = rows;
     g.cols = cols;
-    g.k_chunks = Kp / tc::kBK;
+    g.k_chunks = Kp / sk;
     g.chunks_per_split = g.k_chunks;
     g.limit_ns = 2000000000LL;
     g.err = err;
     g.C = C;
     const dim3 grid(rb / tile_n, ra / tc::kBM, 1);
     if (tile_n == 32) {
-      e = set_smem<32, tc::kEpiPlain>();
-      if (e == cudaSuccess) e = launch_gemm<32, tc::kEpiPlain>(maps, g, grid, st, false);
+      e = set_smem<32, tc::kEpiPlain, OP>();
+      if (e == cudaSuccess) e = launch_gemm<32, tc::kEpiPlain, OP>(maps, g, grid, st, false);
     } else if (tile_n == 256) {
-      e = set_smem<256, tc::kEpiPlain>();
-      if (e == cudaSuccess) e = launch_gemm<256, tc::kEpiPlain>(maps, g, grid, st, false);
+      e = set_smem<256, tc::kEpiPlain, OP>();
+      if (e == cudaSuccess) e = launch_gemm<256, tc::kEpiPlain, OP>(maps, g, grid, st, false);
     } else if (tile_n == 128) {
-      e = set_smem<128, tc::kEpiPlain>();
-      if (e == cudaSuccess) e = launch_gemm<128, tc::kEpiPlain>(maps, g, grid, st, false);
+      e = set_smem<128, tc::kEpiPlain, OP>();
+      if (e == cudaSuccess) e = launch_gemm<128, tc::kEpiPlain, OP>(maps, g, grid, st, false);
     } else {
-      e = set_smem<64, tc::kEpiPlain>();
-      if (e == cudaSuccess) e = launch_gemm<64, tc::kEpiPlain>(maps, g, grid, st, false);
+      e = set_smem<64, tc::kEpiPlain, OP>();
+      if (e == cudaSuccess) e = launch_gemm<64, tc::kEpiPlain, OP>(maps, g, grid, st, false);
     }
   }
   int flag = 0;
@@ -367,10 +381,18 @@ cudaError_t gemm(int rows, int cols, int K, const float *A, const float *B, floa
   cudaError_t e2 = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = e2;
   *timed_out = flag;
-  for (float *b : buf)
+  for (void *b : buf)
     if (b) cudaFree(b);
   if (err) cudaFree(err);
   return e;
+}
+
+}  // namespace
+
+cudaError_t gemm(int rows, int cols, int K, const float *A, const float *B, float *C, int tile_n, int operands,
+                 cudaStream_t st, int *timed_out, const char **what) {
+  return operands == 1 ? gemm_op<tc::kOpF16>(rows, cols, K, A, B, C, tile_n, st, timed_out, what)
+                       : gemm_op<tc::kOpTF32>(rows, cols, K, A, B, C, tile_n, st, timed_out, what);
 }
 
 }  // namespace hot_tc

@@ -37,9 +37,10 @@ cudaError_t launch_forward(Plan *p, const Step &s, cudaStream_t st, bool pdl, bo
 // Launch k >= 1: weight update and coefficients, back-projection -> s.phi, forward field (3 kernels).
 cudaError_t launch_iteration(Plan *p, const Step &s, cudaStream_t st, bool pdl, bool chain, int *kernels);
 
-// C[rows][cols] = A[rows][K] B[cols][K]^T (device pointers, FP32) with the 3xTF32 tensor-core
-// GEMM of the iteration, tile width tile_n (32, 64, 128 or 256); synchronous, allocates its operands.
-cudaError_t gemm(int rows, int cols, int K, const float *A, const float *B, float *C, int tile_n, cudaStream_t st,
-                 int *timed_out, const char **what);
+// C[rows][cols] = A[rows][K] B[cols][K]^T (device pointers, FP32) with the tensor-core GEMM of
+// the iteration, operands split in two TF32 (operands = 0) or FP16 (operands = 1) parts, tile
+// width tile_n (32, 64, 128 or 256); synchronous, allocates its operands.
+cudaError_t gemm(int rows, int cols, int K, const float *A, const float *B, float *C, int tile_n, int operands,
+                 cudaStream_t st, int *timed_out, const char **what);
 
 }  // namespace hot_tc

@@ -35,14 +35,39 @@
 // and returns.
 #pragma once
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace tc {
 
-constexpr int kBM = 128;     // rows of a tile: the 128 lanes of tensor memory
-constexpr int kBK = 32;      // K elements per stage (32 x 4 B = one 128-byte swizzle row)
-constexpr int kUmmaK = 8;    // K of one kind::tf32 MMA
+constexpr int kBM = 128;         // rows of a tile: the 128 lanes of tensor memory
+constexpr int kSliceBytes = 128; // one K slice per stage: one 128-byte swizzle row of every operand row
+constexpr int kMmaKBytes = 32;   // K of one MMA: 8 TF32 or 16 FP16 elements
+
+// Operand types.  TF32: FP32 storage, kind::tf32 (the MMA reads the top 19 bits).  FP16: halves,
+// kind::f16 at twice the TF32 rate; its 11-bit significand equals TF32's, so the split keeps the
+// same precision for operands of magnitude ~1 (the GSW operands are unit phasors and normalised
+// coefficients), while subnormals limit it below ~2^-2 (the low part) and ~2^-14 (the high part).
+constexpr int kOpTF32 = 0, kOpF16 = 1;
+template <int OP>
+struct Op;
+template <>
+struct Op<kOpTF32> {
+  using T = float;
+  static constexpr int kBytes = 4;
+  static constexpr uint32_t kFmt = 2;  // instruction-descriptor operand format TF32
+};
+template <>
+struct Op<kOpF16> {
+  using T = __half;
+  static constexpr int kBytes = 2;
+  static constexpr uint32_t kFmt = 0;  // F16
+};
+template <int OP>
+__host__ __device__ constexpr int slice_k() {  // K elements per slice: 32 (TF32) or 64 (FP16)
+  return kSliceBytes / Op<OP>::kBytes;
+}
 
 constexpr int kEpiPlain = 0, kEpiBack = 1, kEpiFwd = 2;
 
@@ -53,8 +78,8 @@ template <int BN>
 struct Cfg {
   static_assert(BN == 32 || BN == 64 || BN == 128 || BN == 256, "tile width");
   static constexpr int kStages = BN == 256 ? 2 : BN == 128 ? 3 : 4;
-  static constexpr int kABytes = kBM * kBK * 4;  // 16 KB
-  static constexpr int kBBytes = BN * kBK * 4;
+  static constexpr int kABytes = kBM * kSliceBytes;  // 16 KB
+  static constexpr int kBBytes = BN * kSliceBytes;
   static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
   static constexpr int kSmem = kStages * kStageBytes + 1024;  // + slack to align the ring to 1 KB
   static constexpr int kGroups = BN == 256 ? 2 : 1;           // column groups of the drain
@@ -66,23 +91,23 @@ struct Cfg {
 };
 struct BackStage;
 
-// The four operand maps of one GEMM (2-D, FP32, box 32 x rows, 128-byte swizzle).
+// The four operand maps of one GEMM (2-D, box of one 128-byte K slice x rows, 128-byte swizzle).
 struct Maps {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
 };
 
 struct GemmArgs {
   int rows, cols;        // GEMM M and N: outputs outside are not written
-  int k_chunks;          // K / 32
+  int k_chunks;          // K slices (K / slice_k)
   int chunks_per_split;  // K slices per CTA: CTA z takes slices z*cps .. min(k_chunks, (z+1)*cps)-1
   long long limit_ns;    // bound of every wait
   int *err;              // set to 1 when a wait runs out
   // plain
   float *C;              // [rows][cols]
   // back: S -> phi, U
-  int W, H, Kf;          // pixels; row stride of U (floats)
+  int W, H, Kf;          // pixels; row stride of U (elements)
   float *phi;            // [H][W]
-  float *u_hi, *u_lo;    // [..][Kf]: (cos phi, sin phi) interleaved, split for the forward GEMM
+  void *u_hi, *u_lo;     // [..][Kf] operand elements: (cos phi, sin phi) interleaved, split
   // forward: T -> fixed-point field sums
   int M;
   const float2 *Yc;              // [M][H] Y_m(iy)
@@ -146,17 +171,27 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// Instruction descriptor of kind::tf32: FP32 accumulator (bits 4-5 = 1), A and B TF32 (bits 7-9
-// and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t instr_desc_tf32(int m, int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+// Instruction descriptor of kind::tf32 / kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
+// format at bits 7-9 and 10-12 (TF32 = 2, F16 = 0), both K-major (bits 15, 16 = 0), N >> 3 at
+// bit 17, M >> 4 at bit 24.
+template <int OP>
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
+  return (1u << 4) | (Op<OP>::kFmt << 7) | (Op<OP>::kFmt << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
+template <int OP>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  if (OP == kOpF16)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 // The barrier receives one arrival when every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -185,10 +220,34 @@ __device__ __forceinline__ void tmem_load32(uint32_t taddr, float *v) {
 __device__ __forceinline__ void grid_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void grid_release() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
-// x = hi + lo: hi is x with the 13 low mantissa bits cleared (a TF32 value), lo the exact rest.
-__device__ __forceinline__ float2 split_tf32(float x) {
+// x ~ hi + lo, both exactly representable in the operand type (returned as floats).  TF32: hi is
+// x with the 13 low mantissa bits cleared, lo the exact FP32 rest (the MMA reads its TF32 part).
+// FP16: hi = x rounded to half, lo = the rest rounded to half.
+template <int OP>
+__device__ __forceinline__ float2 split2(float x) {
+  if (OP == kOpF16) {
+    const float hi = __half2float(__float2half_rn(x));
+    return make_float2(hi, __half2float(__float2half_rn(x - hi)));
+  }
   const float hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
   return make_float2(hi, x - hi);
+}
+
+// Element i of an operand array (a value split2 produced, so the conversion is exact).
+template <int OP>
+__device__ __forceinline__ void store1(void *base, size_t i, float v) {
+  if (OP == kOpF16)
+    static_cast<__half *>(base)[i] = __float2half_rn(v);
+  else
+    static_cast<float *>(base)[i] = v;
+}
+// Elements i, i + 1 (i even).
+template <int OP>
+__device__ __forceinline__ void store2(void *base, size_t i, float a, float b) {
+  if (OP == kOpF16)
+    *reinterpret_cast<__half2 *>(static_cast<__half *>(base) + i) = __floats2half2_rn(a, b);
+  else
+    *reinterpret_cast<float2 *>(static_cast<float *>(base) + i) = make_float2(a, b);
 }
 
 // u = e^{i phi} of a phase in any range: reduced to [-pi, pi] (Cody-Waite with 2 pi split in
@@ -202,11 +261,12 @@ __device__ __forceinline__ void unit_phasor(float ph, float &sn, float &cs) {
   __sincosf(x, &sn, &cs);
 }
 
-// Stores a complex value split into the hi and lo operand arrays at float offset i (even).
-__device__ __forceinline__ void store_split(float *hi, float *lo, size_t i, float re, float im) {
-  const float2 r = split_tf32(re), m = split_tf32(im);
-  *reinterpret_cast<float2 *>(hi + i) = make_float2(r.x, m.x);
-  *reinterpret_cast<float2 *>(lo + i) = make_float2(r.y, m.y);
+// Stores a complex value split into the hi and lo operand arrays at element i (even).
+template <int OP>
+__device__ __forceinline__ void store_split(void *hi, void *lo, size_t i, float re, float im) {
+  const float2 r = split2<OP>(re), m = split2<OP>(im);
+  store2<OP>(hi, i, r.x, m.x);
+  store2<OP>(lo, i, r.y, m.y);
 }
 
 // 32 accumulator columns n0 .. n0+31 of one row of the plain GEMM: C.
@@ -225,9 +285,10 @@ __device__ __forceinline__ void epilogue_plain(const GemmArgs &a, const float *v
 // of one word in each of 32 rows.
 struct BackStage {
   float ph[32][17];  // phases of 16 pixels of 32 rows
-  float uh[32][33];  // (cos, sin) interleaved, TF32 high parts
+  float uh[32][33];  // (cos, sin) interleaved, high parts
   float ul[32][33];  // and low parts
 };
+template <int OP>
 __device__ __forceinline__ void epilogue_back(const GemmArgs &a, const float *v, int row0, int n0, BackStage &st) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -235,7 +296,7 @@ __device__ __forceinline__ void epilogue_back(const GemmArgs &a, const float *v,
     const float ph = atan2f(v[2 * p + 1], v[2 * p]);
     float sn, cs;
     unit_phasor(ph, sn, cs);
-    const float2 c2 = split_tf32(cs), s2 = split_tf32(sn);
+    const float2 c2 = split2<OP>(cs), s2 = split2<OP>(sn);
     st.ph[lane][p] = ph;
     st.uh[lane][2 * p] = c2.x;
     st.uh[lane][2 * p + 1] = s2.x;
@@ -254,8 +315,8 @@ __device__ __forceinline__ void epilogue_back(const GemmArgs &a, const float *v,
     const int iy = row0 + r, ix = x0 + (lane >> 1);
     if (iy < a.H && ix < a.W) {
       const size_t o = (size_t)iy * a.Kf + 2 * x0 + lane;
-      a.u_hi[o] = st.uh[r][lane];
-      a.u_lo[o] = st.ul[r][lane];
+      store1<OP>(a.u_hi, o, st.uh[r][lane]);
+      store1<OP>(a.u_lo, o, st.ul[r][lane]);
     }
   }
   __syncwarp();
@@ -314,7 +375,7 @@ __device__ __forceinline__ void epilogue_fwd(const GemmArgs &a, float *z, int ro
 
 // One 128 x BN output tile over a K range: TMA loader (warp 0, one lane), MMA issuer (warp 1,
 // one lane), accumulator drain and epilogue (the other warps).  grid = (N tiles, M tiles, K splits).
-template <int BN, int EPI>
+template <int BN, int EPI, int OP>
 __global__ void __launch_bounds__(Cfg<BN>::kThreads, 1) tc_gemm_kernel(const __grid_constant__ Maps maps,
                                                                        const __grid_constant__ GemmArgs a) {
   using C = Cfg<BN>;
@@ -369,7 +430,7 @@ __global__ void __launch_bounds__(Cfg<BN>::kThreads, 1) tc_gemm_kernel(const __g
         if (*(volatile int *)&failed) break;
         unsigned char *st = ring + s * C::kStageBytes;
         mbar_expect_tx(&full[s], C::kStageBytes);
-        const int kx = (kc0 + i) * kBK;
+        const int kx = (kc0 + i) * slice_k<OP>();
         tma_load_2d(st, &maps.a_hi, kx, m0, &full[s]);
         tma_load_2d(st + C::kABytes, &maps.a_lo, kx, m0, &full[s]);
         tma_load_2d(st + 2 * C::kABytes, &maps.b_hi, kx, n0, &full[s]);
@@ -380,7 +441,7 @@ __global__ void __launch_bounds__(Cfg<BN>::kThreads, 1) tc_gemm_kernel(const __g
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = instr_desc_tf32(kBM, BN);
+      constexpr uint32_t idesc = instr_desc<OP>(kBM, BN);
       for (int i = 0; i < nk; i++) {
         const int b = i % C::kBufs;
         // accumulator b is free once the drain warps have emptied its previous slice
@@ -398,14 +459,14 @@ __global__ void __launch_bounds__(Cfg<BN>::kThreads, 1) tc_gemm_kernel(const __g
         const uint32_t sa = smem_u32(ring + s * C::kStageBytes);
         const uint32_t d = tmem + (uint32_t)(b * BN);
 #pragma unroll
-        for (int kk = 0; kk < kBK / kUmmaK; kk++) {
-          const uint32_t off = kk * kUmmaK * 4;  // 32 bytes per MMA step along K
+        for (int kk = 0; kk < kSliceBytes / kMmaKBytes; kk++) {
+          const uint32_t off = kk * kMmaKBytes;  // 32 bytes per MMA step along K
           const uint64_t ahi = smem_desc(sa + off), alo = smem_desc(sa + C::kABytes + off);
           const uint64_t bhi = smem_desc(sa + 2 * C::kABytes + off);
           const uint64_t blo = smem_desc(sa + 2 * C::kABytes + C::kBBytes + off);
-          mma_tf32(d, ahi, bhi, idesc, kk != 0);
-          mma_tf32(d, ahi, blo, idesc, 1u);
-          mma_tf32(d, alo, bhi, idesc, 1u);
+          mma<OP>(d, ahi, bhi, idesc, kk != 0);
+          mma<OP>(d, ahi, blo, idesc, 1u);
+          mma<OP>(d, alo, bhi, idesc, 1u);
         }
         mma_commit(&empty[s]);  // the stage returns to the loader when these MMAs have read it
         mma_commit(&tfull[b]);  // and the accumulator goes to the epilogue warps
@@ -452,7 +513,7 @@ __global__ void __launch_bounds__(Cfg<BN>::kThreads, 1) tc_gemm_kernel(const __g
       // the ring is free: every MMA that read it has completed (the last slice was drained)
       BackStage &st = reinterpret_cast<BackStage *>(ring)[warp - 2];
 #pragma unroll
-      for (int c = 0; c < COLS; c += 32) epilogue_back(a, acc + c, m0 + q * 32, n0 + g * COLS + c, st);
+      for (int c = 0; c < COLS; c += 32) epilogue_back<OP>(a, acc + c, m0 + q * 32, n0 + g * COLS + c, st);
     } else if (ok) {
 #pragma unroll
       for (int c = 0; c < COLS; c += 32) epilogue_plain(a, acc + c, row, n0 + g * COLS + c);
@@ -479,14 +540,15 @@ __global__ void __launch_bounds__(Cfg<BN>::kThreads, 1) tc_gemm_kernel(const __g
 //   back    Bb[n][k], n = 2 ix + r, k = 2 m + s: [[xr, -xi], [xi, xr]][r][s]    (2W x Kb)
 //   forward Bf[n][k], n = 2 m + r,  k = 2 ix + s: [[xr, xi], [-xi, xr]][r][s]   (2M x Kf)
 // and the row table transposed, YT[iy][m] = Y_m(iy) (m < Kb/2, zero beyond M).  Padding rows and
-// columns are zero.  Rows of Bb and Bf are padded to the tile width, Kb and Kf to 32.
+// columns are zero.  Rows of Bb and Bf are padded to the tile width, Kb and Kf to a K slice.
 struct TableArgs {
   int W, H, M, Kb, Kf, rows_b, rows_f;
   const float2 *Xc, *Yc;
-  float *bb_hi, *bb_lo, *bf_hi, *bf_lo;
+  void *bb_hi, *bb_lo, *bf_hi, *bf_lo;  // operand elements
   float2 *YT;
 };
 
+template <int OP>
 __global__ void tc_tables_kernel(TableArgs a) {
   const long long nb = (long long)a.rows_b * a.Kb, nf = (long long)a.rows_f * a.Kf;
   const long long ny = (long long)a.H * (a.Kb / 2);
@@ -500,9 +562,9 @@ __global__ void tc_tables_kernel(TableArgs a) {
         const float2 x = a.Xc[(size_t)m * a.W + ix];
         val = (r == s) ? x.x : (r == 0 ? -x.y : x.y);
       }
-      const float2 h = split_tf32(val);
-      a.bb_hi[i] = h.x;
-      a.bb_lo[i] = h.y;
+      const float2 h = split2<OP>(val);
+      store1<OP>(a.bb_hi, i, h.x);
+      store1<OP>(a.bb_lo, i, h.y);
     } else if (i < nb + nf) {
       const long long j = i - nb;
       const int n = (int)(j / a.Kf), k = (int)(j % a.Kf);
@@ -512,9 +574,9 @@ __global__ void tc_tables_kernel(TableArgs a) {
         const float2 x = a.Xc[(size_t)m * a.W + ix];
         val = (r == s) ? x.x : (r == 0 ? x.y : -x.y);
       }
-      const float2 h = split_tf32(val);
-      a.bf_hi[j] = h.x;
-      a.bf_lo[j] = h.y;
+      const float2 h = split2<OP>(val);
+      store1<OP>(a.bf_hi, j, h.x);
+      store1<OP>(a.bf_lo, j, h.y);
     } else {
       const long long j = i - nb - nf;
       const int iy = (int)(j / (a.Kb / 2)), m = (int)(j % (a.Kb / 2));
@@ -525,7 +587,8 @@ __global__ void tc_tables_kernel(TableArgs a) {
 
 // The forward operand of given phases: u = e^{i phi} (unit_phasor), split; and one accumulator
 // buffer cleared for the launch after next.
-__global__ void tc_phase_kernel(int W, int H, int Kf, const float *phi, float *u_hi, float *u_lo,
+template <int OP>
+__global__ void tc_phase_kernel(int W, int H, int Kf, const float *phi, void *u_hi, void *u_lo,
                                 unsigned long long *acc_clear, int n_clear) {
   grid_wait();
   const long long N = (long long)W * H, stride = (long long)gridDim.x * blockDim.x;
@@ -533,7 +596,7 @@ __global__ void tc_phase_kernel(int W, int H, int Kf, const float *phi, float *u
     const int iy = (int)(j / W), ix = (int)(j % W);
     float sn, cs;
     unit_phasor(phi[j], sn, cs);
-    store_split(u_hi, u_lo, (size_t)iy * Kf + 2 * ix, cs, sn);
+    store_split<OP>(u_hi, u_lo, (size_t)iy * Kf + 2 * ix, cs, sn);
   }
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_clear; i += stride) acc_clear[i] = 0ull;
   grid_release();
@@ -546,7 +609,7 @@ struct PrepArgs {
   const float *w_in;
   float *w_out;                      // written by block 0
   const float2 *YT;                  // [H][Kb/2]
-  float *p_hi, *p_lo;                // [..][Kb]
+  void *p_hi, *p_lo;                 // [..][Kb] operand elements
   float inv_fx_n;
   float *trace;                      // NULL, or e, u of the fields read (block 0)
 };
@@ -570,10 +633,12 @@ constexpr int kPrepThreads = 256;
 // same bits) and the coefficients c_m = w_m' V_m/|V_m| with w_m' = w_m <|V|>/|V_m| (|V_m| < 1e-30:
 // c_m = w_m, w kept) in shared memory, then writes its share of P[iy][2m..2m+1] = c_m Y_m(iy),
 // split.  Block 0 writes the new weights (and the trace); the blocks clear the next buffer.
+template <int OP>
 __global__ void __launch_bounds__(kPrepThreads) tc_prep_kernel(PrepArgs a) {
   extern __shared__ float2 cs[];  // [M]
   __shared__ ffp part[2][kPrepThreads / 32];
   __shared__ float ext[2][kPrepThreads / 32];
+  __shared__ float cmx[kPrepThreads / 32];
   grid_wait();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   ffp s = {0.f, 0.f}, si = {0.f, 0.f};
@@ -616,6 +681,7 @@ __global__ void __launch_bounds__(kPrepThreads) tc_prep_kernel(PrepArgs a) {
     a.trace[0] = e.hi + e.lo;
     a.trace[1] = (hi + lo > 0.f) ? 1.f - (hi - lo) / (hi + lo) : 0.f;
   }
+  float cmax = 0.f;  // largest |c_m| (= w_m'): the coefficients are scaled by its inverse below
   for (int m = t; m < a.M; m += kPrepThreads) {
     const float2 v = cs[m];
     const float w = __ldcg(a.w_in + m);
@@ -630,10 +696,20 @@ __global__ void __launch_bounds__(kPrepThreads) tc_prep_kernel(PrepArgs a) {
     }
     if (blockIdx.x == 0) a.w_out[m] = wn;
     cs[m] = c;
+    cmax = fmaxf(cmax, wn);
   }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+  if (lane == 0) cmx[warp] = cmax;
   const long long stride = (long long)gridDim.x * kPrepThreads;
   for (long long i = blockIdx.x * (long long)kPrepThreads + t; i < 2LL * a.M; i += stride) a.acc_clear[i] = 0ull;
   __syncthreads();
+  // A factor common to all coefficients leaves arg S unchanged (Sec. 4; the weights' scale is
+  // free): P is formed from c_m / max |c| so that its magnitudes stay near 1 whatever the
+  // weights' scale (the FP16 operands lose precision below ~0.25).
+  float top = cmx[0];
+  for (int i = 1; i < kPrepThreads / 32; i++) top = fmaxf(top, cmx[i]);
+  const float scale = top > 0.f ? 1.f / top : 1.f;
   // this block's rows: an even share of the H rows, all Kb/2 (padded) traps of each
   const int half = a.Kb / 2;
   const int r0 = (int)((long long)a.H * blockIdx.x / gridDim.x);
@@ -641,22 +717,23 @@ __global__ void __launch_bounds__(kPrepThreads) tc_prep_kernel(PrepArgs a) {
   const int n = (r1 - r0) * half;
   for (int i = t; i < n; i += kPrepThreads) {
     const int iy = r0 + i / half, m = i - (i / half) * half;
-    const float2 c = m < a.M ? cs[m] : make_float2(0.f, 0.f);
+    const float2 c = m < a.M ? make_float2(cs[m].x * scale, cs[m].y * scale) : make_float2(0.f, 0.f);
     const size_t j = (size_t)iy * half + m;
     const float2 y = __ldg(a.YT + j);
-    store_split(a.p_hi, a.p_lo, 2 * j, c.x * y.x - c.y * y.y, c.x * y.y + c.y * y.x);
+    store_split<OP>(a.p_hi, a.p_lo, 2 * j, c.x * y.x - c.y * y.y, c.x * y.y + c.y * y.x);
   }
   grid_release();
 }
 
 // Operands of the plain GEMM entry point: src [rows][K] -> hi, lo [rows_pad][K_pad], zero padded.
-__global__ void tc_split_kernel(const float *src, int rows, int K, int K_pad, long long total, float *hi, float *lo) {
+template <int OP>
+__global__ void tc_split_kernel(const float *src, int rows, int K, int K_pad, long long total, void *hi, void *lo) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(i / K_pad), k = (int)(i % K_pad);
     const float x = (r < rows && k < K) ? src[(size_t)r * K + k] : 0.f;
-    const float2 h = split_tf32(x);
-    hi[i] = h.x;
-    lo[i] = h.y;
+    const float2 h = split2<OP>(x);
+    store1<OP>(hi, i, h.x);
+    store1<OP>(lo, i, h.y);
   }
 }
 

@@ -77,7 +77,7 @@ SIGNATURES = {
     "hot_destroy": (None, [_vp]),
     "hot_last_error": (ctypes.c_char_p, []),
     "hot_sfu_rate": (_c_int, [_c_int, _dp, ctypes.POINTER(_c_int)]),
-    "hot_tf32x3_gemm": (_c_int, [_c_int, _c_int, _c_int, _vp, _vp, _vp, _c_int, _vp]),
+    "hot_tc_gemm": (_c_int, [_c_int, _c_int, _c_int, _vp, _vp, _vp, _c_int, _c_int, _vp]),
     "hot_field_noalloc": (_c_int, [_c_int, _c_int, _c_double, _c_double, _c_double, _c_int, _vp, _vp, _c_int,
                                    _vp, _vp, _vp]),
 }
@@ -398,15 +398,18 @@ def hot_sfu_rate(op: int = 0):
     return r.value, n.value
 
 
-def hot_tf32x3_gemm(A, B, C, tile_n: int = 64, cuda_stream: int | None = None) -> None:
-    """C = A B^T on the tensor cores (3xTF32): A (rows, K), B (cols, K), C (rows, cols) are
-    contiguous float32 CUDA tensors.  Synchronises."""
+HOT_TC_TF32, HOT_TC_FP16 = 0, 1
+
+
+def hot_tc_gemm(A, B, C, tile_n: int = 64, operands: int = HOT_TC_TF32, cuda_stream: int | None = None) -> None:
+    """C = A B^T on the tensor cores, operands split in two TF32 or FP16 parts: A (rows, K),
+    B (cols, K), C (rows, cols) are contiguous float32 CUDA tensors.  Synchronises."""
     rows, K = A.shape
     cols = B.shape[0]
     if B.shape[1] != K or tuple(C.shape) != (rows, cols):
-        raise ValueError("hot_tf32x3_gemm: shapes do not match")
-    _ok(lib.hot_tf32x3_gemm(int(rows), int(cols), int(K), _vp(A.data_ptr()), _vp(B.data_ptr()), _vp(C.data_ptr()),
-                            int(tile_n), _vp(cuda_stream or 0)), "hot_tf32x3_gemm")
+        raise ValueError("hot_tc_gemm: shapes do not match")
+    _ok(lib.hot_tc_gemm(int(rows), int(cols), int(K), _vp(A.data_ptr()), _vp(B.data_ptr()), _vp(C.data_ptr()),
+                        int(tile_n), int(operands), _vp(cuda_stream or 0)), "hot_tc_gemm")
 
 
 HOT_NOALLOC_SCRATCH_BYTES = 16 << 20

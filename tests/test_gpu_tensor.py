@@ -1,10 +1,10 @@
 """HOT_PREC_TENSOR: the separable GSW iteration as complex matrix products on the tcgen05
-tensor cores (3xTF32), through the C ABI.
+tensor cores (operands split in two FP16 parts), through the C ABI.
 
-- the GEMM alone (hot_tf32x3_gemm): bit-exact on small integers (every product and partial sum
-  is exact in TF32/FP32, so any slip of layout, transposition, swizzle or K order shows), and
-  within the 3xTF32 error bound of the FP64 product on random data (a dropped low part gives
-  ~5e-4 relative errors, 50x over the bound);
+- the GEMM alone (hot_tc_gemm), both operand types: bit-exact on small integers (every product
+  and partial sum is exact in TF32/FP16 and FP32, so any slip of layout, transposition, swizzle
+  or K order shows), and within the split's error bound of the FP64 product on random data (a
+  dropped low part gives ~5e-4 relative errors, 100x over the bound);
 - GSW in the tensor mode against the FP64 oracle with the tolerances of every other mode
   (|V_m| 1e-4 relative after one iteration, e and u 1e-3, conditioning-aware phases);
 - bit-identical resume, graph replay vs direct launches, the convergence trace, and the calls
@@ -34,32 +34,39 @@ def hot():
     return h
 
 
-def gemm(hot, A, B, tile_n):
+def gemm(hot, A, B, tile_n, operands):
     import torch
     a = torch.from_numpy(np.ascontiguousarray(A, dtype=np.float32)).cuda()
     b = torch.from_numpy(np.ascontiguousarray(B, dtype=np.float32)).cuda()
     c = torch.full((A.shape[0], B.shape[0]), float("nan"), dtype=torch.float32, device="cuda")
-    hot.hot_tf32x3_gemm(a, b, c, tile_n)
+    hot.hot_tc_gemm(a, b, c, tile_n, operands)
     return c.cpu().numpy()
 
 
+OPERANDS = [0, 1]  # HOT_TC_TF32, HOT_TC_FP16
+
+
+@pytest.mark.parametrize("operands", OPERANDS)
 @pytest.mark.parametrize("tile_n", [32, 64, 128, 256])
 @pytest.mark.parametrize("rows,cols,K", [(128, 64, 32), (200, 130, 75), (1, 1, 1), (257, 300, 96), (300, 520, 200)])
-def test_gemm_exact_on_small_integers(hot, rows, cols, K, tile_n):
+def test_gemm_exact_on_small_integers(hot, rows, cols, K, tile_n, operands):
     rng = np.random.default_rng(rows * 7 + cols + K)
     A = rng.integers(-8, 9, size=(rows, K)).astype(np.float32)
     B = rng.integers(-8, 9, size=(cols, K)).astype(np.float32)
-    C = gemm(hot, A, B, tile_n)
+    C = gemm(hot, A, B, tile_n, operands)
     assert np.array_equal(C, (A.astype(np.int64) @ B.astype(np.int64).T).astype(np.float32))
 
 
+@pytest.mark.parametrize("operands", OPERANDS)
 @pytest.mark.parametrize("tile_n", [32, 64, 128, 256])
 @pytest.mark.parametrize("rows,cols,K", [(300, 200, 1000), (130, 70, 33)])
-def test_gemm_within_3xtf32_bound(hot, rows, cols, K, tile_n):
+def test_gemm_within_split_bound(hot, rows, cols, K, tile_n, operands):
+    """Operands of magnitude ~1 (uniform on [0.5, 1] with random sign: the FP16 split keeps its
+    full precision there, as on the mode's unit phasors)."""
     rng = np.random.default_rng(rows + cols + K)
-    A = rng.standard_normal((rows, K)).astype(np.float32)
-    B = rng.standard_normal((cols, K)).astype(np.float32)
-    C = gemm(hot, A, B, tile_n).astype(np.float64)
+    A = (rng.uniform(0.5, 1.0, (rows, K)) * rng.choice([-1, 1], (rows, K))).astype(np.float32)
+    B = (rng.uniform(0.5, 1.0, (cols, K)) * rng.choice([-1, 1], (cols, K))).astype(np.float32)
+    C = gemm(hot, A, B, tile_n, operands).astype(np.float64)
     ref = A.astype(np.float64) @ B.astype(np.float64).T
     scale = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64).T
     # per product ~2^-20 relative (split), plus FP32 accumulation over K terms
