@@ -188,9 +188,14 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- engine (GPU)
 
 def kernel_source_hash(kernel: str = "step") -> str:
+    """First 16 hex digits of the SHA-256 of the kernels' source with comments and blank space
+    removed (so that a profile stays matched to code whose comments alone changed)."""
     name = "tc_kernels.cuh" if kernel == "tc" else "gsw_kernels.cuh"
-    src = os.path.join(ROOT, "paper_0907_4027_gb300", "csrc", name)
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    src = open(os.path.join(ROOT, "paper_0907_4027_gb300", "csrc", name)).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    src = " ".join(src.split())
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def profiled_traffic(workload: str, kernel: str = "step"):

@@ -9,22 +9,24 @@
 // with u = e^{i phi}.  Each complex product is one real GEMM on the 2x2 real embedding of the
 // complex numbers: operands are stored complex-interleaved (real, imaginary) along K, and the
 // constant right-hand operand holds the blocks [[xr, -xi], [xi, xr]] (back) or [[xr, xi], [-xi, xr]]
-// (forward, the conjugate).  The GEMMs run on tcgen05.mma kind::tf32 with FP32 accumulators in
-// tensor memory.  TF32 keeps 10 mantissa bits, so every operand is split x = hi + lo with hi the
-// TF32 truncation and lo the FP32 remainder, and a product takes three MMAs,
-// a_hi b_hi + a_hi b_lo + a_lo b_hi (the omitted a_lo b_lo is below 2^-20 relative): the
-// products keep about FP32 accuracy.
+// (forward, the conjugate).  The GEMMs run on tcgen05.mma with FP32 accumulators in tensor
+// memory.  A 16-bit or TF32 tensor-core operand keeps 11 significant bits, so every operand is
+// split x = hi + lo and a product takes three MMAs, a_hi b_hi + a_hi b_lo + a_lo b_hi (the omitted
+// a_lo b_lo is ~2^-22 relative): the products keep about FP32 accuracy.  The GSW iteration uses
+// two FP16 parts (kind::f16: twice the TF32 rate, half the bytes; its operands are unit phasors and
+// coefficients scaled to <= 1, where FP16 keeps its 11 bits); the GEMM also runs two TF32 parts
+// (kind::tf32, the FP32 exponent range).
 //
 // A CTA computes one 128 x BN tile of a GEMM over a range of K, warp-specialised: one thread of
-// warp 0 issues TMA loads of 32-element K slices (128-byte rows, 128-byte swizzle) of A_hi, A_lo,
-// B_hi, B_lo into a ring of shared-memory stages; one thread of warp 1 issues the 12 MMAs of a
-// slice into one of 2-4 tensor-memory accumulators and returns the stage to the loader with
+// warp 0 issues TMA loads of K slices (one 128-byte row per matrix row, 128-byte swizzle) of A_hi,
+// A_lo, B_hi, B_lo into a ring of shared-memory stages; one thread of warp 1 issues the 12 MMAs of
+// a slice into one of 2-4 tensor-memory accumulators and returns the stage to the loader with
 // tcgen05.commit; the drain warps (TMEM lane quadrant = warp % 4, i.e. 32 rows each, and a group
 // of <= 128 columns) add every slice's accumulator into FP32 registers while the MMAs of the next
-// slices run in the other accumulators.  The tensor core's own accumulation into TMEM is not round-to-nearest (measured:
-// a magnitude bias growing with the MMAs accumulated, ~1e-4 relative on small |V_m| after 190),
-// so each accumulator holds the 12 MMAs of one slice only and the K sum runs in the registers
-// (round-to-nearest, fixed order).  Then the epilogue:
+// slices run in the other accumulators.  The tensor core's own accumulation into TMEM is not
+// round-to-nearest (measured: a magnitude bias growing with the MMAs accumulated, ~1e-4 relative on
+// small |V_m| after 190), so each accumulator holds the 12 MMAs of one slice only and the K sum
+// runs in the registers (round-to-nearest, fixed order).  Then the epilogue:
 //   back:    phi = arg S (atan2f), u = e^{i phi}, written as phases and as the split U operand;
 //   forward: the tile's rows weighted by conj(Y_m(iy)) and summed, added into the 64-bit
 //            fixed-point field accumulators (integer atomics: exact and order-independent, so
