@@ -94,8 +94,9 @@ int hot_set_phase(hot_ctx *c, const float *phi, int on_device);
  * runs three kernels per iteration (weight update and operand P, back-projection GEMM with the
  * phases in its epilogue, forward GEMM with the field sums in its epilogue); its operands
  * (about 4 (2W + 2M)(2M + 2W) + 8 H (W + M) + 8 H M bytes) are built on the first hot_gsw after the
- * traps are set.  HOT_PREC_TENSOR rejects the persistent form (hot_use_persistent), row-band
- * steps (hot_sharded_begin), batches (hot_batch_create) and hot_autotune with HOT_EINVAL. */
+ * traps are set (row-band steps, hot_sharded_*, run the same kernels).  HOT_PREC_TENSOR rejects the
+ * persistent form (hot_use_persistent), batches (hot_batch_create) and hot_autotune with
+ * HOT_EINVAL. */
 int hot_set_precision(hot_ctx *c, int precision);
 
 /* Runs `iters` GSW iterations (Sec. 3, Fig. 2) from the current phases and weights:

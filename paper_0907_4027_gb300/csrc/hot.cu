@@ -904,11 +904,15 @@ int hot_set_band(hot_ctx *c, int total_height, int y0) {
 int hot_sharded_begin(hot_ctx *c) {
   if (!c) return fail(HOT_EINVAL, "hot_sharded_begin: NULL context");
   if (!c->M) return fail(HOT_ESTATE, "hot_sharded_begin: no traps set");
-  if (c->precision == HOT_PREC_TENSOR)
-    return fail(HOT_EINVAL, "hot_sharded_begin: row bands run the direct or separable kernels, not HOT_PREC_TENSOR");
   c->shard_k = -1;
   c->have_fields = false;
-  const int rc = launch_step(c, false, true, false, 0);
+  int rc = HOT_OK;
+  if (c->precision == HOT_PREC_TENSOR) {
+    rc = ensure_tc_plan(c);
+    if (rc == HOT_OK) rc = launch_tc(c, false, 0);
+  } else {
+    rc = launch_step(c, false, true, false, 0);
+  }
   if (rc == HOT_OK) c->shard_k = 0;
   return rc;
 }
@@ -917,7 +921,7 @@ int hot_sharded_step(hot_ctx *c, int k) {
   if (!c) return fail(HOT_EINVAL, "hot_sharded_step: NULL context");
   if (c->shard_k < 0 || k != c->shard_k + 1)
     return fail(HOT_ESTATE, "hot_sharded_step: launch %d does not follow launch %d", k, c->shard_k);
-  const int rc = launch_step(c, true, true, false, k);
+  const int rc = c->precision == HOT_PREC_TENSOR ? launch_tc(c, false, k) : launch_step(c, true, true, false, k);
   if (rc == HOT_OK) c->shard_k = k;
   return rc;
 }

@@ -57,7 +57,7 @@ def emulate(bands, iters):
     return [h.sharded_end(iters) for h in bands]
 
 
-@pytest.mark.parametrize("precision", ["accurate", "fast", "separable"])
+@pytest.mark.parametrize("precision", ["accurate", "fast", "separable", "tensor"])
 @pytest.mark.parametrize("W,H,M,world", [(100, 37, 13, 2), (64, 64, 130, 3), (33, 20, 3, 4)])
 def test_bands_match_unsharded_and_oracle(env, W, H, M, world, precision):
     torch, hot = env
@@ -90,10 +90,11 @@ def test_bands_match_unsharded_and_oracle(env, W, H, M, world, precision):
     assert phi.shape == (w.N,)
 
 
-def test_single_band_is_the_plain_context(env):
+@pytest.mark.parametrize("precision", ["fast", "tensor"])
+def test_single_band_is_the_plain_context(env, precision):
     """A band covering the whole hologram gives hot_gsw's result bit for bit."""
     torch, hot = env
-    w = wl.random_case(64, 48, 20, seed=2, precision="fast")
+    w = wl.random_case(64, 48, 20, seed=2, precision=precision)
     bands = make_bands(torch, hot, w, 1)
     try:
         eu = emulate(bands, 3)[0]

@@ -176,8 +176,6 @@ def test_rejected_calls_and_other_entry_points(hot):
             h.autotune(2)
         with pytest.raises(hot.HotError, match="HOT_EINVAL"):
             hot.Batch([h])
-        with pytest.raises(hot.HotError, match="HOT_EINVAL"):
-            h.sharded_begin()
         import torch
         phi = torch.from_numpy(np.asarray(w.phi0, dtype=np.float32)).cuda()
         Vd = torch.empty(2 * w.M, dtype=torch.float32, device="cuda")
