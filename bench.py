@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision-report", action="store_true",
                     help="errors of both precision modes against the FP64 oracle, per result")
+    ap.add_argument("--m-sweep", action="store_true",
+                    help="time per GSW iteration vs trap count M = 1..4096 on a 768^2 SLM (Fig. 5 analogue)")
     ap.add_argument("--grid-sweep", action="store_true",
                     help="efficiency and uniformity vs trap count on n x n grids (n = 2..9, 768^2 SLM)")
     ap.add_argument("--single", type=int, default=0, metavar="K",
@@ -498,6 +500,67 @@ def run_adam(args):
     return 0
 
 
+def run_m_sweep(args):
+    """Fig. 5 analogue (time per trap per GSW iteration vs M): 768 x 768 SLM, random 3-D traps
+    (seed 0), M = 1 .. 4096, in the fast, separable and tensor modes (--precision picks one).
+    Per point: the marginal time of one iteration (graph-replayed hot_gsw(K) minus hot_gsw(K/4),
+    CUDA events, median of 5) and the time of the forward field alone (hot_gsw(0): F(phi0) and
+    the Eq. 4 metrics).  A least-squares line t = a + b M over M >= 16 gives the fixed cost a and
+    the cost per trap b, beside the SFU bound of the direct evaluation (4 SFU ops per pixel-trap
+    pair)."""
+    import torch
+    from paper_0907_4027_gb300 import _build
+    _build.build()
+    from paper_0907_4027_gb300 import hot, workloads as wl
+
+    W = H = 768
+    Ms = [1, 2, 4, 8, 16, 32, 64, 100, 128, 256, 512, 1024, 2048, 4096]
+    modes = [args.precision] if args.precision else ["fast", "separable", "tensor"]
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sfu_us_per_trap = W * H * SFU_OPS_PER_UPDATE / (sms * SFU_LANES_PER_SM * 2070e6) * 1e6
+
+    def timed(h, phi0, k, reps=5):
+        out = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            h.set_phase(phi0)
+            a.record(stream)
+            h.gsw(k, metrics=False)
+            b.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b) * 1e3)
+        return statistics.median(out)
+
+    results = {}
+    for mode in modes:
+        rows = []
+        for M in Ms:
+            w = wl.random_case(W, H, M, seed=0, precision=mode)
+            with hot.Hologram.from_workload(w, stream.cuda_stream) as h:
+                phi0 = torch.tensor(w.phi0, dtype=torch.float32, device="cuda")
+                K = 20 if M <= 1024 else 8
+                h.gsw(K, metrics=False)
+                h.gsw(K // 4, metrics=False)
+                h.gsw(0, metrics=False)
+                t_iter = (timed(h, phi0, K) - timed(h, phi0, K // 4)) / (K - K // 4)
+                t_fwd = timed(h, phi0, 0)
+            rows.append({"M": M, "us_per_iteration": round(t_iter, 3), "us_forward_only": round(t_fwd, 3),
+                         "us_per_trap_per_iteration": round(t_iter / M, 5),
+                         "updates_per_s": W * H * M / (t_iter * 1e-6)})
+        fit = [r for r in rows if r["M"] >= 16]
+        xs = np.array([r["M"] for r in fit], dtype=np.float64)
+        ys = np.array([r["us_per_iteration"] for r in fit])
+        b, a = np.polyfit(xs, ys, 1)
+        results[mode] = {"points": rows, "fit_M_ge_16": {"fixed_us": round(float(a), 3),
+                                                         "us_per_trap": round(float(b), 5)}}
+    print(json.dumps({"metric": "time per GSW iteration vs trap count (768x768 SLM)", "W": W, "H": H,
+                      "sfu_bound_us_per_trap": round(sfu_us_per_trap, 5),
+                      "paper_context": "0.44 ms per trap per iteration on a GTX 260 (SLM size not stated)",
+                      "results": results}), flush=True)
+    return 0
+
+
 def run_grid_sweep(args):
     """Sec. 5 / Fig. 7 analogue: e and u of n x n square grids (spacing 4 um, n = 2..9) on a
     768 x 768 SLM at a fixed 20 Hz frame rate.  Per grid: the random superposition (SR, seeded
@@ -729,6 +792,8 @@ def main():
         return run_batch(args)
     if args.grid_sweep:
         return run_grid_sweep(args)
+    if args.m_sweep:
+        return run_m_sweep(args)
     if args.precision_report:
         return run_precision_report(args)
     if args.workload == "diff256_1024":
