@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 REL_V = 1e-4
 ABS_EU = 1e-3
-TOL_S = {"accurate": 2e-6, "fast": 2e-5, "separable": 4e-6}
+TOL_S = {"accurate": 2e-6, "fast": 2e-5, "separable": 4e-6, "tensor": 4e-6}
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
@@ -162,10 +162,10 @@ def quantized_agreement(gpu_u8, ophi, S, eps_S):
 
 
 @pytest.mark.parametrize("name,precision", [("grid16_256", None), ("rand100_512", None),
-                                            ("rand100_512", "separable")])
+                                            ("rand100_512", "separable"), ("rand100_512", "tensor")])
 def test_full_workload_matches_oracle(hot, name, precision):
     """grid16_256 (accurate, 10 iterations) and rand100_512 (fast, 30 iterations, 8-bit), and
-    rand100_512 in the separable mode."""
+    rand100_512 in the separable and tensor modes."""
     w = wl.NAMED[name]()
     if precision:
         w.precision = precision
@@ -361,7 +361,9 @@ def test_maximum_trap_count(hot, precision):
     are rejected.  (The first weight update here spreads the weights over a factor of ~400, so
     the back-projection cancels strongly at some pixels; the fast mode's 5e-7 sincos error is then
     amplified past the 1e-4 bound on |V_m|, as the conditioning-aware phase bound predicts, and the
-    case is run in the two modes whose per-term error is ~1e-7.)"""
+    case is run in the two modes whose per-term error is ~1e-7.  The tensor mode gives 3.2e-4 here:
+    the tensor core's accumulation truncates at ~2^-22 of the accumulator per MMA, an error that
+    follows the strongest traps' coefficients and that this cancellation amplifies the same way.)"""
     w = wl.random_case(160, 120, 4096, seed=31, precision=precision)
     with make(hot, w) as h:
         h.gsw(1)
