@@ -55,7 +55,7 @@ def parse():
                          "tensor: the FP16 tensor-core roofline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision-report", action="store_true",
-                    help="errors of both precision modes against the FP64 oracle, per result")
+                    help="errors of the four precision modes against the FP64 oracle, per result")
     ap.add_argument("--m-sweep", action="store_true",
                     help="time per GSW iteration vs trap count M = 1..4096 on a 768^2 SLM (Fig. 5 analogue)")
     ap.add_argument("--grid-sweep", action="store_true",
