@@ -108,12 +108,13 @@ int hot_set_precision(hot_ctx *c, int precision);
  * eff_out / unif_out (host, nullable): if either is non-NULL the call synchronises and
  * writes them; otherwise it returns once the work is queued.  Readings where the paper
  * is silent: if |V_m| < 1e-30 the unit field is taken as 1 and w_m is kept; arg(0) = 0.
- * By default each iteration is one kernel launch, the sequence replayed as a CUDA graph; with
- * hot_use_persistent the iterations run in one cooperative launch whose blocks meet at a
- * grid-wide barrier between iterations.  There a barrier wait longer than the wait limit
- * (hot_set_wait_limit) makes the kernel leave early, and the next synchronising call
- * (this one with eff_out/unif_out, hot_sync, hot_get_fields, hot_get_metrics) returns
- * HOT_ETIMEOUT: the accumulators are reset and the phases are undefined.
+ * By default each iteration is one kernel launch (three in HOT_PREC_TENSOR), the sequence
+ * replayed as a CUDA graph; with hot_use_persistent the iterations run in one cooperative launch
+ * whose blocks meet at a grid-wide barrier between iterations.  There a barrier wait longer than
+ * the wait limit (hot_set_wait_limit) makes the kernel leave early, and the next synchronising
+ * call (this one with eff_out/unif_out, hot_sync, hot_get_fields, hot_get_metrics) returns
+ * HOT_ETIMEOUT: the accumulators are reset and the phases are undefined.  The tensor-core
+ * kernels bound their pipeline waits by the same limit, with the same outcome.
  * HOT_ESTATE before hot_set_traps; HOT_EINVAL if iters < 0. */
 int hot_gsw(hot_ctx *c, int iters, double *eff_out, double *unif_out);
 
