@@ -73,6 +73,30 @@ def test_forward_lens_term_shifted_gauss_sum(oracle):
     assert abs(abs(V[0]) - 2.0 / n) < 1e-12
 
 
+def test_eq2_separates_into_column_and_row_parts(oracle):
+    """Eq. 2 is a sum of a part in x_j and a part in y_j (the lens term z (x^2 + y^2) splits too),
+    the basis of the separable and tensor-core modes: every mixed second difference
+    Delta(ix1, iy1) + Delta(ix2, iy2) - Delta(ix1, iy2) - Delta(ix2, iy1) vanishes, while the pure
+    second differences in x and in y both equal 2 pi z p^2 / (lambda f^2) (twice the lens term's
+    coefficient z pi / (lambda f^2) times p^2), which a cross term such as x y or a wrong factor on
+    one axis would break."""
+    rng = np.random.default_rng(7)
+    W, H = 640, 480
+    g = geom(W, H)
+    for xyz in wl.random_traps(6, 60.0, 15.0, seed=3):
+        scale = 2 * np.pi * float(xyz[2]) * P * P / (LAM * F * F)
+        for _ in range(5):
+            ix1, ix2 = (int(v) for v in rng.integers(0, W, 2))
+            iy1, iy2 = (int(v) for v in rng.integers(0, H, 2))
+            d = [[oracle.delta(g, xyz, ix, iy) for iy in (iy1, iy2)] for ix in (ix1, ix2)]
+            mixed = d[0][0] + d[1][1] - d[0][1] - d[1][0]
+            assert abs(mixed) < 1e-9 * (1 + max(abs(v) for row in d for v in row))
+            c = oracle.delta(g, xyz, ix1, iy1)
+            dxx = oracle.delta(g, xyz, ix1 + 1, iy1) - 2 * c + oracle.delta(g, xyz, ix1 - 1, iy1)
+            dyy = oracle.delta(g, xyz, ix1, iy1 + 1) - 2 * c + oracle.delta(g, xyz, ix1, iy1 - 1)
+            assert abs(dxx - scale) < 1e-9 * (1 + abs(c)) and abs(dyy - scale) < 1e-9 * (1 + abs(c))
+
+
 def test_single_trap_hologram_gives_unit_field(oracle):
     """Sec. 3: phi_j = Delta_j^1 sends all light to trap 1, V_1 = 1 (e = u = 1)."""
     W, H = 11, 6
