@@ -329,6 +329,14 @@ void hot_destroy(hot_ctx *c);
  * device; takes a few milliseconds. */
 int hot_sfu_rate(int op, double *per_clk_per_sm, int *sms);
 
+/* Launch shapes HOT_PREC_TENSOR would use for a width x height hologram with M traps on a GPU
+ * with `sms` SMs (host computation only: no device work, no context).  shape (host, 9 ints)
+ * receives: [0] tile width of the back-projection GEMM, [1] of the forward GEMM (32, 64, 128 or
+ * 256 columns), [2] K splits of the forward GEMM, [3] K slices (64 elements) per split, [4] K of
+ * the back-projection GEMM (2M padded to a slice), [5] K of the forward GEMM (2W padded),
+ * [6] rows padded to the 128-row tile, [7] 2W and [8] 2M padded to their tile widths. */
+int hot_tc_shape(int width, int height, int M, int sms, int *shape);
+
 /* The matrix product of HOT_PREC_TENSOR on its own (no counterpart in the paper):
  * C = A B^T for DEVICE float32 arrays A [rows][K], B [cols][K] (row-major) into C [rows][cols],
  * on the tcgen05 tensor cores with every operand split into two parts (a b ~ a_hi b_hi +

@@ -1742,6 +1742,15 @@ __global__ void __launch_bounds__(1024) sfu_rate_kernel(float *out, long long *c
 
 }  // namespace
 
+extern "C" int hot_tc_shape(int width, int height, int M, int sms, int *shape) {
+  if (width < 1 || height < 1 || M < 1 || sms < 1 || !shape)
+    return fail(HOT_EINVAL, "hot_tc_shape: invalid argument");
+  const hot_tc::Shape sh = hot_tc::shape_for(width, height, M, sms);
+  const int v[9] = {sh.bn_back, sh.bn_fwd, sh.fwd_splits, sh.fwd_cps, sh.Kb, sh.Kf, sh.rows_h, sh.rows_b, sh.rows_f};
+  for (int i = 0; i < 9; i++) shape[i] = v[i];
+  return HOT_OK;
+}
+
 extern "C" int hot_tc_gemm(int rows, int cols, int K, const float *A, const float *B, float *C, int tile_n,
                            int operands, void *cuda_stream) {
   if (rows < 1 || cols < 1 || K < 1) return fail(HOT_EINVAL, "hot_tc_gemm: sizes %d x %d x %d", rows, cols, K);

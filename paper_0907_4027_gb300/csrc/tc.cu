@@ -124,6 +124,24 @@ int pick_width(int rows, int cols, int k_chunks, int sms, bool split_k) {
 
 }  // namespace
 
+Shape shape_for(int W, int H, int M, int sms) {
+  Shape sh;
+  sh.Kb = round_up(2 * M, kSliceK);
+  sh.Kf = round_up(2 * W, kSliceK);
+  sh.rows_h = round_up(H, tc::kBM);
+  sh.bn_back = pick_width(H, 2 * W, sh.Kb / kSliceK, sms, false);
+  sh.bn_fwd = pick_width(H, 2 * M, sh.Kf / kSliceK, sms, true);
+  sh.rows_b = round_up(2 * W, sh.bn_back);
+  sh.rows_f = round_up(2 * M, sh.bn_fwd);
+  // forward GEMM: the K range split over CTAs so that the tiles fill the SMs about once
+  const int tiles_f = (sh.rows_h / tc::kBM) * (sh.rows_f / sh.bn_fwd);
+  const int kcf = sh.Kf / kSliceK;
+  const int splits = std::max(1, std::min(kcf, sms / std::max(tiles_f, 1)));
+  sh.fwd_cps = (kcf + splits - 1) / splits;
+  sh.fwd_splits = (kcf + sh.fwd_cps - 1) / sh.fwd_cps;  // every split has >= 1 slice
+  return sh;
+}
+
 void plan_destroy(Plan *p) {
   if (!p) return;
   for (void *b : {p->bb_hi, p->bb_lo, p->bf_hi, p->bf_lo, p->p_hi, p->p_lo, p->u_hi, p->u_lo})
@@ -162,22 +180,19 @@ cudaError_t plan_create(Plan **out, int W, int H, int M, const float2 *Xc, const
   p->M = M;
   p->Xc = Xc;
   p->Yc = Yc;
-  p->Kb = round_up(2 * M, kSliceK);
-  p->Kf = round_up(2 * W, kSliceK);
-  p->rows_h = round_up(H, tc::kBM);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev);
-  p->bn_back = pick_width(H, 2 * W, p->Kb / kSliceK, p->sms, false);
-  p->bn_fwd = pick_width(H, 2 * M, p->Kf / kSliceK, p->sms, true);
-  p->rows_b = round_up(2 * W, p->bn_back);
-  p->rows_f = round_up(2 * M, p->bn_fwd);
-  // forward GEMM: the K range split over CTAs so that the tiles fill the SMs about once
-  const int tiles_f = (p->rows_h / tc::kBM) * (p->rows_f / p->bn_fwd);
-  const int kcf = p->Kf / kSliceK;
-  const int splits = std::max(1, std::min(kcf, p->sms / std::max(tiles_f, 1)));
-  p->fwd_cps = (kcf + splits - 1) / splits;
-  p->fwd_splits = (kcf + p->fwd_cps - 1) / p->fwd_cps;  // every split has >= 1 slice
+  const Shape sh = shape_for(W, H, M, p->sms);
+  p->Kb = sh.Kb;
+  p->Kf = sh.Kf;
+  p->rows_h = sh.rows_h;
+  p->bn_back = sh.bn_back;
+  p->bn_fwd = sh.bn_fwd;
+  p->rows_b = sh.rows_b;
+  p->rows_f = sh.rows_f;
+  p->fwd_cps = sh.fwd_cps;
+  p->fwd_splits = sh.fwd_splits;
   *what = "allocating the tensor-core operands";
   const size_t nb = (size_t)p->rows_b * p->Kb, nf = (size_t)p->rows_f * p->Kf;
   const size_t np = (size_t)p->rows_h * p->Kb, nu = (size_t)p->rows_h * p->Kf;

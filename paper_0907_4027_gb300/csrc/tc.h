@@ -22,6 +22,16 @@ struct Step {
   long long limit_ns;                // that bound
 };
 
+// Launch shapes of the tensor mode for a W x H hologram with M traps on `sms` SMs (host only).
+struct Shape {
+  int Kb, Kf;              // K of the back (2M) and forward (2W) GEMMs, padded to a K slice
+  int rows_h;              // H padded to the tile height
+  int bn_back, bn_fwd;     // tile widths (32, 64, 128 or 256)
+  int rows_b, rows_f;      // 2W and 2M padded to the tile widths
+  int fwd_splits, fwd_cps; // K splits of the forward GEMM and K slices per split
+};
+Shape shape_for(int W, int H, int M, int sms);
+
 // Builds the operands of the traps' complex column and row tables Xc [M][W], Yc [M][H] (queued
 // on st).  On failure returns the CUDA error and names the step in *what.
 cudaError_t plan_create(Plan **out, int W, int H, int M, const float2 *Xc, const float2 *Yc, cudaStream_t st,

@@ -78,6 +78,7 @@ SIGNATURES = {
     "hot_last_error": (ctypes.c_char_p, []),
     "hot_sfu_rate": (_c_int, [_c_int, _dp, ctypes.POINTER(_c_int)]),
     "hot_tc_gemm": (_c_int, [_c_int, _c_int, _c_int, _vp, _vp, _vp, _c_int, _c_int, _vp]),
+    "hot_tc_shape": (_c_int, [_c_int, _c_int, _c_int, _c_int, _vp]),
     "hot_field_noalloc": (_c_int, [_c_int, _c_int, _c_double, _c_double, _c_double, _c_int, _vp, _vp, _c_int,
                                    _vp, _vp, _vp]),
 }
@@ -399,6 +400,14 @@ def hot_sfu_rate(op: int = 0):
 
 
 HOT_TC_TF32, HOT_TC_FP16 = 0, 1
+TC_SHAPE_KEYS = ("bn_back", "bn_fwd", "fwd_splits", "fwd_slices_per_split", "Kb", "Kf", "rows_h", "rows_b", "rows_f")
+
+
+def hot_tc_shape(width: int, height: int, M: int, sms: int) -> dict:
+    """Launch shapes of the tensor mode (host computation only)."""
+    v = np.zeros(len(TC_SHAPE_KEYS), dtype=np.int32)
+    _ok(lib.hot_tc_shape(int(width), int(height), int(M), int(sms), v.ctypes.data_as(_vp)), "hot_tc_shape")
+    return {k: int(x) for k, x in zip(TC_SHAPE_KEYS, v)}
 
 
 def hot_tc_gemm(A, B, C, tile_n: int = 64, operands: int = HOT_TC_TF32, cuda_stream: int | None = None) -> None:
