@@ -148,6 +148,7 @@ def hot_set_phase(ctx: int, phi) -> None:
 
 
 def hot_set_precision(ctx: int, precision) -> None:
+    """precision: "accurate", "fast", "separable", "tensor" or the HOT_PREC_* value."""
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     _ok(lib.hot_set_precision(_vp(ctx), int(precision)), "hot_set_precision")

@@ -40,7 +40,7 @@ class Workload:
     phi0: np.ndarray                # (H*W,) float64 holding float32 values, radians in [0, 2pi)
     iters: int
     w0: np.ndarray = None           # (M,) float64; None -> all ones
-    precision: str = "accurate"     # "accurate" | "fast"
+    precision: str = "accurate"     # "accurate" | "fast" | "separable" | "tensor"
     quantize: bool = False
     pitch: float = PITCH
     wavelength: float = WAVELENGTH
