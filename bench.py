@@ -252,7 +252,7 @@ def run_engine(args):
     h.set_phase(phi0)
     t_tune = time.perf_counter()
     if tensor:  # fixed tiles: nothing to tune
-        tuned = {"rows": None, "blocks_per_sm": None, "chunk": None, "us_per_iter": None}
+        tuned = {"rows": None, "blocks_per_sm": None, "chunk": None, "merge": None, "us_per_iter": None}
     else:
         tuned = h.autotune(w.iters)
     tuned["seconds"] = time.perf_counter() - t_tune
@@ -381,12 +381,16 @@ def run_engine(args):
                     "peak_basis": f"measured bf16 burst {bf16:.1f} TFLOP/s (MEASURED_PEAKS.json); FP16 "
                                   f"runs at the bf16 rate (nominal ratio {F16_PER_BF16:.1f})",
                     "flops_per_update": TC_FLOPS_PER_UPDATE, "avg_iteration_us": avg_launch_s * 1e6,
+                    "frac_of_value": TC_FLOPS_PER_UPDATE * value / world / 1e12 / tc_peak,
                     "updates_per_s": achieved,
                     "fp32_fma_roofline_updates_per_s": peak, "launch_timing": launch_timing,
                     "avg_iteration_us_unpipelined": step_kernel_ms * 1e3 / max(step_kernel_n, 1)}
     else:
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "updates/s",
                     "frac": achieved / peak, "traffic": traffic,
+                    "frac_of_value": value / world / peak,
+                    "frac_of_value_note": "the bench value (whole step: forward of the starting phases, "
+                                          "iterations, finalize, 8-bit encoding) over the same peak",
                     "kernel": ("gsw_sep_kernel<back, fwd>" if sep else
                                f"gsw_step_kernel<{w.precision}, back, fwd>") + " (one GSW iteration per launch)",
                     "peak_basis": f"{dev.multi_processor_count} SMs x {lanes} {pipe} "
@@ -407,7 +411,7 @@ def run_engine(args):
             "config": workload_config(w, {
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                 "l2": "flushed between steps (256 MB write outside the step events)",
-                "tiling": {k: tuned[k] for k in ("rows", "blocks_per_sm", "chunk")},
+                "tiling": {k: tuned[k] for k in ("rows", "blocks_per_sm", "chunk", "merge")},
                 "autotune": {"us_per_iter": tuned["us_per_iter"], "seconds": round(tuned["seconds"], 3),
                              "search": "coordinate search over rows/blocks_per_sm/chunk, best of 3 graph replays"},
                 "timing": "CUDA events per step on the launching stream, summed; hot_gsw replays "
@@ -415,8 +419,14 @@ def run_engine(args):
                           "the same steps with per-launch events"}),
             "holograms_per_s": world * args.steps / (total_ms * 1e-3),
             "roofline": roofline,
-            "kernel_time_share": kernel_share,
-            "kernel_time_ms": {k: round(v[0] / n_prof, 4) for k, v in prof.items()},
+            # per step: the dominant kernel's time in the real pipeline (iterations x marginal
+            # iteration time; at most ms_per_step) and the rest of the step
+            "kernel_time_ms": {"step_kernel_pipelined": round(w.iters * iter_ms, 4),
+                               "rest_of_step": round(total_ms / args.steps - w.iters * iter_ms, 4)},
+            # shares of device time from a second pass with every launch bracketed by its own
+            # events (launches serialised: per-launch times there exceed the pipelined ones)
+            "kernel_time_share_unpipelined": kernel_share,
+            "kernel_time_ms_unpipelined": {k: round(v[0] / n_prof, 4) for k, v in prof.items()},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "api": "hot_set_traps + hot_set_phase (pinned host) + hot_gsw + hot_phase_out (host)",
                     "final_e": eu[0], "final_u": eu[1]},
@@ -468,8 +478,28 @@ def run_adam(args):
             V = ag.trap_fields(h, phi)
         return ev[0].elapsed_time(ev[1]), float(L.item()), eu(V)
 
+    def adam_lib(n_steps):
+        """The same optimisation with the loss and its gradient from one library call
+        (hot_intensity_loss) and PyTorch's fused Adam."""
+        phi = torch.tensor(w.phi0, dtype=torch.float32, device="cuda", requires_grad=True)
+        opt = torch.optim.Adam([phi], lr=1.0, fused=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(n_steps):
+            opt.zero_grad(set_to_none=True)
+            L = ag.intensity_loss(h, phi)
+            L.backward()
+            opt.step()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        with torch.no_grad():
+            V = ag.trap_fields(h, phi)
+        return ev[0].elapsed_time(ev[1]), float(L.item()), eu(V)
+
     adam_run(3, False)
     ms, loss, (e, u) = adam_run(w.iters, True)
+    adam_lib(3)
+    ms_lib, loss_lib, (e_lib, u_lib) = adam_lib(w.iters)
     # plain GSW from the same starting phases
     phi0 = torch.tensor(w.phi0, dtype=torch.float32, device="cuda")
     gsw = {}
@@ -486,13 +516,17 @@ def run_adam(args):
         torch.cuda.synchronize()
         gsw[K] = {"ms": ev[0].elapsed_time(ev[1]), "e": ge, "u": gu}
     line = {
-        "metric": "Adam steps/s on -sum log I + 10 var I (1024x1024 px, M=256)", "value": w.iters / (ms * 1e-3),
-        "unit": "steps/s", "n_gpus": 1, "steps": w.iters, "warmup": 3, "ms_per_step": ms / w.iters,
+        "metric": "Adam steps/s on -sum log I + 10 var I (1024x1024 px, M=256)", "value": w.iters / (ms_lib * 1e-3),
+        "unit": "steps/s", "n_gpus": 1, "steps": w.iters, "warmup": 3, "ms_per_step": ms_lib / w.iters,
+        "path": "hot_intensity_loss (forward field, loss and coefficients, adjoint: 3 kernels) + torch fused Adam",
+        "final_library_loss": {"loss": loss_lib, "e": e_lib, "u": u_lib, "ms_total": ms_lib},
+        "autograd_path": {"steps_per_s": w.iters / (ms * 1e-3), "ms_per_step": ms / w.iters,
+                          "path": "trap_fields (hot_field) + PyTorch loss + backward (hot_field_adjoint) + Adam"},
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{w.name}: {w.W}x{w.H} px, M={w.M} traps, {w.iters} Adam steps on the phases, "
                                f"{w.precision} mode", "W": w.W, "H": w.H, "M": w.M, "steps": w.iters,
                    "precision": w.precision, "seed": 0, "optimizer": "Adam lr 1.0 (the best of 1e-2, 3e-2, 0.1, 0.3, 1.0 for this loss; torch defaults otherwise)"},
-        "final": {"loss": loss, "e": e, "u": u, "ms_total": ms},
+        "final_autograd": {"loss": loss, "e": e, "u": u, "ms_total": ms},
         "gsw_same_traps": {str(k): v for k, v in gsw.items()},
     }
     print(json.dumps(line), flush=True)
@@ -683,84 +717,97 @@ def run_precision_report(args):
 
 def run_batch(args):
     """Batched form (batch64): 64 holograms, sizes from {512^2, 1024^2, 1920x1152}, M ~ U{8..2000},
-    30 GSW iterations per hologram in one CUDA graph (shortest-first groups, one launch per group
-    and iteration), autotuned tiling, fast sincos.  Holograms/s and per-hologram latency (device
-    timer stamps from the start of the graph to each hologram's completion), beside the same
-    holograms run one by one through hot_gsw."""
+    30 GSW iterations per hologram in one CUDA graph, in the fast direct mode (shortest-first
+    groups, one launch per group and iteration, autotuned tiling) and in the tensor mode (each
+    member's own launch sequence on 8 concurrent chains); --precision picks one mode.
+    Holograms/s and per-hologram latency (device timer stamps from the start of the graph to each
+    hologram's completion), beside the same holograms run one by one through hot_gsw in the same
+    mode.  The line's value is the fastest batched mode; best_one_by_one is the fastest mode run
+    one by one."""
     import torch
     from paper_0907_4027_gb300 import _build
     _build.build()
     from paper_0907_4027_gb300 import hot, workloads as wl
 
-    ws = wl.batch64()
-    if args.precision:
-        for w in ws:
-            w.precision = args.precision
     stream = torch.cuda.current_stream()
-    holos = [hot.Hologram.from_workload(w, stream.cuda_stream) for w in ws]
-    K = ws[0].iters
-    pairs = sum(w.N * w.M for w in ws) * K
+    modes = [args.precision] if args.precision else ["fast", "tensor"]
+    K = wl.batch64()[0].iters
+    results = {}
+    for mode in modes:
+        ws = wl.batch64()
+        for w in ws:
+            w.precision = mode
+        holos = [hot.Hologram.from_workload(w, stream.cuda_stream) for w in ws]
+        pairs = sum(w.N * w.M for w in ws) * K
 
-    def reset():
-        for h, w in zip(holos, ws):
-            h.set_phase(w.phi0)
-            h.set_weights(np.ones(w.M))
+        def reset():
+            for h, w in zip(holos, ws):
+                h.set_phase(w.phi0)
+                h.set_weights(np.ones(w.M))
 
-    batch = hot.Batch(holos, stream.cuda_stream)
-    t_tune = time.perf_counter()
-    tuned = batch.autotune(2)
-    t_tune = time.perf_counter() - t_tune
-    tiling = batch.tiling()
-    reps = max(1, min(args.steps, 5))
-    total, lats = [], []
-    for i in range(reps + 1):
+        batch = hot.Batch(holos, stream.cuda_stream)
+        t_tune = time.perf_counter()
+        tuned = batch.autotune(2) if mode != "tensor" else None
+        t_tune = time.perf_counter() - t_tune
+        tiling = batch.tiling()
+        reps = max(1, min(args.steps, 5))
+        total, lats = [], []
+        for i in range(reps + 1):
+            reset()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            batch.gsw(K)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            if i:  # i = 0: graph capture and warm-up
+                total.append(ev[0].elapsed_time(ev[1]))
+                lats.append(batch.latency())
+        batch_ms = float(np.median(total))
+        lat = np.concatenate(lats)
+        eu_batch = batch.metrics()
+        batch.close()
+        # the same holograms one by one (each its own hot_gsw graph, default tiling), in the given order
+        for h in holos:
+            h.gsw(K, metrics=False)
         reset()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ev[0].record(stream)
-        batch.gsw(K)
-        ev[1].record(stream)
         torch.cuda.synchronize()
-        if i:  # i = 0: graph capture and warm-up
-            total.append(ev[0].elapsed_time(ev[1]))
-            lats.append(batch.latency())
-    batch_ms = float(np.median(total))
-    lat = np.concatenate(lats)
-    eu_batch = batch.metrics()
-    batch.close()
-    # the same holograms one by one (each its own hot_gsw graph, default tiling), in the given order
-    for h in holos:
-        h.gsw(K, metrics=False)
-    reset()
-    torch.cuda.synchronize()
-    ev_all = [torch.cuda.Event(enable_timing=True) for _ in range(len(holos) + 1)]
-    ev_all[0].record(stream)
-    for i, h in enumerate(holos):
-        h.gsw(K, metrics=False)
-        ev_all[i + 1].record(stream)
-    torch.cuda.synchronize()
-    seq_lat = np.array([ev_all[0].elapsed_time(ev_all[i + 1]) for i in range(len(holos))])
-    eu_seq = [h.metrics() for h in holos]
-    for h in holos:
-        h.close()
-    d_e = max(abs(x[0] - y[0]) for x, y in zip(eu_batch, eu_seq))
-    d_u = max(abs(x[1] - y[1]) for x, y in zip(eu_batch, eu_seq))
+        ev_all = [torch.cuda.Event(enable_timing=True) for _ in range(len(holos) + 1)]
+        ev_all[0].record(stream)
+        for i, h in enumerate(holos):
+            h.gsw(K, metrics=False)
+            ev_all[i + 1].record(stream)
+        torch.cuda.synchronize()
+        seq_lat = np.array([ev_all[0].elapsed_time(ev_all[i + 1]) for i in range(len(holos))])
+        eu_seq = [h.metrics() for h in holos]
+        for h in holos:
+            h.close()
+        results[mode] = {
+            "batch": {"holograms_per_s": len(ws) / (batch_ms * 1e-3), "ms": batch_ms,
+                      "updates_per_s": pairs / (batch_ms * 1e-3),
+                      "latency_ms_p50": float(np.percentile(lat, 50)),
+                      "latency_ms_p99": float(np.percentile(lat, 99)),
+                      "tiling": tiling,
+                      "autotune": dict(tuned, seconds=t_tune, iters=2) if tuned else None},
+            "sequential": {"holograms_per_s": len(ws) / (seq_lat[-1] * 1e-3), "ms": float(seq_lat[-1]),
+                           "updates_per_s": pairs / (seq_lat[-1] * 1e-3),
+                           "latency_ms_p50": float(np.percentile(seq_lat, 50)),
+                           "latency_ms_p99": float(np.percentile(seq_lat, 99))},
+            "batch_vs_sequential_max_abs_diff": {"e": max(abs(x[0] - y[0]) for x, y in zip(eu_batch, eu_seq)),
+                                                 "u": max(abs(x[1] - y[1]) for x, y in zip(eu_batch, eu_seq))},
+        }
+    best = max(modes, key=lambda m: results[m]["batch"]["holograms_per_s"])
+    best_seq = max(modes, key=lambda m: results[m]["sequential"]["holograms_per_s"])
     line = {
         "metric": "holograms/s, batch of 64 uneven holograms (30 GSW iterations each)",
-        "value": len(ws) / (batch_ms * 1e-3), "unit": "holograms/s", "n_gpus": 1, "steps": reps,
-        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "value": results[best]["batch"]["holograms_per_s"], "unit": "holograms/s", "n_gpus": 1,
+        "steps": max(1, min(args.steps, 5)), "higher_is_better": True,
+        "dtype": "f16x3" if best == "tensor" else "f32", "data": "synthetic",
         "config": {"workload": "batch64: 64 holograms, sizes from {512^2, 1024^2, 1920x1152}, M ~ U{8..2000}, "
-                               f"30 GSW iterations in one CUDA graph, {ws[0].precision} mode", "seed": 0},
-        "batch": {"ms": batch_ms, "updates_per_s": pairs / (batch_ms * 1e-3),
-                  "latency_ms_p50": float(np.percentile(lat, 50)),
-                  "latency_ms_p99": float(np.percentile(lat, 99)),
-                  "latency": "device %globaltimer: start of the first launch to each hologram's finalize",
-                  "tiling": tiling, "autotune": dict(tuned, seconds=t_tune, iters=2)},
-        "sequential": {"ms": float(seq_lat[-1]), "holograms_per_s": len(ws) / (seq_lat[-1] * 1e-3),
-                       "updates_per_s": pairs / (seq_lat[-1] * 1e-3),
-                       "latency_ms_p50": float(np.percentile(seq_lat, 50)),
-                       "latency_ms_p99": float(np.percentile(seq_lat, 99)),
-                       "note": "hot_gsw per hologram in the given order, default tiling; CUDA events"},
-        "batch_vs_sequential_max_abs_diff": {"e": d_e, "u": d_u},
+                               "30 GSW iterations in one CUDA graph", "seed": 0, "batched_mode": best},
+        "best_one_by_one": {"mode": best_seq, "holograms_per_s": results[best_seq]["sequential"]["holograms_per_s"]},
+        "modes": results,
+        "latency": "device %globaltimer: start of the batch's first launch to each hologram's finalize; "
+                   "one by one: CUDA events from the first hot_gsw to each hologram's end",
     }
     print(json.dumps(line), flush=True)
     return 0

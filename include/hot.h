@@ -46,17 +46,34 @@ typedef enum {
   HOT_ESTATE = -5    /* call out of order (e.g. hot_gsw before hot_set_traps) */
 } hot_status;
 
+/* Accuracy of the modes against an FP64 evaluation of the method (the parity tests' bounds):
+ * |V_m| within 1e-4 relative after one GSW iteration, e and u within 1e-3 after a run, 8-bit
+ * output equal except within 1e-4 rad of a level boundary.  HOT_PREC_ACCURATE and
+ * HOT_PREC_SEPARABLE meet these bounds on every tested case, up to HOT_MAX_TRAPS traps.
+ * HOT_PREC_FAST and HOT_PREC_TENSOR meet them on every tested case except strongly cancelling
+ * back-projections: 4096 traps on a 160 x 120 SLM, whose first weight update spreads the weights
+ * over a factor ~400, so that the superposition cancels at some pixels and amplifies each term's
+ * error.  There the |V_m| error after one iteration is bounded by 2e-4 in the fast mode (1.2e-4
+ * measured; accurate 7.6e-5) and by 5e-4 in the tensor mode (3.3e-4 measured).  Measured
+ * elsewhere: 512 x 512 px with 100 traps, 4.1e-6 fast, 6.0e-6 accurate; 1920 x 1152 px with
+ * 1000 traps, 8.8e-6 fast. */
 typedef enum {
   HOT_PREC_ACCURATE = 0, /* sincospif on the exactly reduced phase (FP32, ~1 ulp) */
-  HOT_PREC_FAST = 1,     /* sin.approx / cos.approx (SFU) on the reduced phase */
+  HOT_PREC_FAST = 1,     /* the direct evaluation on the special-function unit: sin.approx /
+                             cos.approx of the reduced phase (arguments pre-scaled by 1 + 8.17e-8
+                             against the unit's mean argument shrink); the forward field rotates the
+                             phases of each pixel sub-tile by a fixed pseudo-random angle and its
+                             sums back, so that the unit's systematic error does not add up over
+                             the pixels */
   HOT_PREC_SEPARABLE = 2, /* Eq. 2 factorised: e^{i Delta} = e^{i X_m(ix)} e^{i Y_m(iy)} from FP32
                              complex tables (FP64 cos/sin once per entry); per pair one complex
                              multiply-add in each step, no transcendental function */
-  HOT_PREC_TENSOR = 3      /* the separable form on the tensor cores: each step of a GSW iteration
-                             is a complex matrix product (S = P X, T = U X^H) run as tcgen05 FP16
-                             MMAs with every operand split in two FP16 parts (three MMAs per
-                             product, FP32 accumulation); the GSW loop only (hot_gsw), other
-                             calls run the separable kernels */
+  HOT_PREC_TENSOR = 3      /* EXPERIMENTAL, outside the direct method: the separable form on the
+                             tensor cores; each step of a GSW iteration is a complex matrix product
+                             (S = P X, T = U X^H) run as tcgen05 FP16 MMAs with every operand split
+                             in two FP16 parts (three MMAs per product, FP32 accumulation); the GSW
+                             loop only (hot_gsw), other calls run the separable kernels; |V_m|
+                             error up to 5e-4 on strongly cancelling back-projections (above) */
 } hot_precision;
 
 typedef enum {
@@ -95,8 +112,8 @@ int hot_set_phase(hot_ctx *c, const float *phi, int on_device);
  * phases in its epilogue, forward GEMM with the field sums in its epilogue); its operands
  * (about 4 (2W + 2M)(2M + 2W) + 8 H (W + M) + 8 H M bytes) are built on the first hot_gsw after the
  * traps are set (row-band steps, hot_sharded_*, run the same kernels).  HOT_PREC_TENSOR rejects the
- * persistent form (hot_use_persistent), batches (hot_batch_create) and hot_autotune with
- * HOT_EINVAL. */
+ * persistent form (hot_use_persistent) and hot_autotune with HOT_EINVAL; its batches run each
+ * member's own launch sequence (see hot_batch_create). */
 int hot_set_precision(hot_ctx *c, int precision);
 
 /* Runs `iters` GSW iterations (Sec. 3, Fig. 2) from the current phases and weights:
@@ -188,6 +205,19 @@ int hot_field(hot_ctx *c, const float *phi, float *V);
  * GSW state is not touched.  HOT_ESTATE before hot_set_traps. */
 int hot_field_adjoint(hot_ctx *c, const float *phi, const float *G, float *grad);
 
+/* The trap-intensity loss of the differentiable form and its gradient in one call (no
+ * counterpart in the paper; its intensities are those of Eq. 4): with V = F(phi) (Eq. 1) and
+ * I_m = |V_m|^2,
+ *   L = -sum_m log I_m + beta var_m(I)   (population variance over the traps),
+ * and dL/dphi by the adjoint of Eq. 1 with G_m = 2 g_m V_m, g_m = -1/I_m + beta (2/M)(I_m - mean I)
+ * (see hot_field_adjoint).  Three kernels on the context's stream (forward field, loss and G in
+ * FP64 sums, adjoint), nothing read back: an optimiser step on the phases then costs these
+ * kernels and the optimiser's update.  phi: DEVICE float32 [N]; loss: DEVICE float32 [1] output;
+ * grad: DEVICE float32 [N] output, or NULL for the loss alone.  The GSW state is not touched;
+ * hot_get_fields / hot_get_metrics afterwards report F(phi).  HOT_ESTATE before hot_set_traps;
+ * HOT_EINVAL for NULL phi or loss or a non-finite beta. */
+int hot_intensity_loss(hot_ctx *c, const float *phi, double beta, float *loss, float *grad);
+
 /* ---- row bands: the sharded form --------------------------------------------------------
  * Eq. 1 is a sum over pixels, so the pixels can be split into row bands, one per GPU: each
  * band computes partial sums of V_m over its rows, the partial sums are added over the bands
@@ -237,8 +267,24 @@ int hot_set_tiling(hot_ctx *c, int rows, int blocks_per_sm, int chunk);
 /* The tiling in effect (blocks_per_sm as launched).  Any output pointer may be NULL. */
 int hot_get_tiling(const hot_ctx *c, int *rows, int *blocks_per_sm, int *chunk);
 
+/* Block merging of the accurate and fast modes' GSW step (no counterpart in the paper): with
+ * merge = 1 and 4 blocks per SM (the default count), the step launches one block of 1024
+ * threads per SM that holds the schedule's 4 blocks as groups of 256 threads, each with its own
+ * shared memory and barrier.  The 4 blocks of an SM then hold consecutive runs of the image,
+ * which add up to the SM's equal share to within one 32-pixel row segment (independent blocks
+ * land on SMs in no fixed order, and an SM may get 4 runs that are each one segment longer than
+ * average); the next launch's blocks start later, as each SM's whole block must finish first.
+ * Measured on GB300 (fast mode): 8 % faster at 1920 x 1152 px with 1000 traps, slower at small
+ * sizes (2 % at 512 x 512 px with 100 traps).  The results are the same bits either way.
+ * Default 0; hot_autotune searches it.  merge: 0 or 1, else HOT_EINVAL.  Rebuilds the schedule;
+ * synchronises the context's stream.  hot_get_block_merge reports the setting and whether the
+ * step runs merged (only in the accurate and fast modes with 4 blocks per SM). */
+int hot_set_block_merge(hot_ctx *c, int merge);
+int hot_get_block_merge(const hot_ctx *c, int *requested, int *in_effect);
+
 /* Autotuner: times hot_gsw(iters) (CUDA events, best of 3 graph replays) for candidate tilings
- * by coordinate search over rows, blocks_per_sm and chunk, keeps the fastest, and reports it
+ * by coordinate search over rows, blocks_per_sm (with block merging, hot_set_block_merge, as a
+ * candidate in the accurate and fast modes) and chunk, keeps the fastest, and reports it
  * with its time per iteration in microseconds (outputs may be NULL).  The phases and weights
  * are restored afterwards; the fields are stale until the next forward evaluation (HOT_ESTATE
  * from hot_get_fields).  Synchronises.  HOT_ESTATE before hot_set_traps; iters >= 1. */
@@ -260,7 +306,13 @@ typedef struct hot_batch hot_batch;
  * into a batch
  * queued on cuda_stream (NULL: the legacy stream).  The batch refers to the contexts'
  * buffers: recreate it after hot_set_traps changes a trap count, and destroy it before
- * destroying its contexts.  The contexts must not be used concurrently with the batch. */
+ * destroying its contexts.  The contexts must not be used concurrently with the batch.
+ * HOT_PREC_TENSOR batches are not packed into shared launches: each member runs exactly the
+ * launch sequence of its own hot_gsw (same results, bit for bit), and the members are dealt out
+ * to up to 8 chains (largest N M first, each to the least loaded chain) that run concurrently
+ * inside the batch's graph, so that the launches of small holograms, which leave most SMs idle,
+ * overlap.  Such a batch has no tiling: hot_batch_set_tiling and hot_batch_autotune return
+ * HOT_EINVAL, and hot_batch_get_tiling reports the number of chains as its groups. */
 int hot_batch_create(hot_batch **out, int count, hot_ctx *const *ctxs, void *cuda_stream);
 
 /* Tiling of the batch's launches (as hot_set_tiling; 0 selects a default) and the minimum
@@ -296,7 +348,7 @@ void hot_batch_destroy(hot_batch *b);
  * kernel ran out since the last check (see hot_gsw). */
 int hot_sync(hot_ctx *c);
 
-/* Number of kernels the context has launched since creation (instrumentation). */
+/* DIAGNOSTIC: number of kernels the context has launched since creation (instrumentation). */
 long long hot_kernel_launches(const hot_ctx *c);
 
 /* Kernel classes reported by hot_profile_read. */
@@ -308,7 +360,8 @@ typedef enum {
   HOT_KERNEL_KINDS = 4
 } hot_kernel_kind;
 
-/* Instrumentation: while enabled (enable = 1), CUDA events are recorded on the context's
+/* DIAGNOSTIC (not part of the method's path; for tests and benchmarks).
+ * Instrumentation: while enabled (enable = 1), CUDA events are recorded on the context's
  * stream around every kernel the context launches.  hot_profile_read synchronises the
  * stream and writes, per hot_kernel_kind, the summed device time in milliseconds (ms[4])
  * and the number of launches (launches[4]) recorded since the last read, then clears the
@@ -319,7 +372,8 @@ int hot_profile_read(hot_ctx *c, double *ms, long long *launches);
 /* Frees the context and its device buffers (NULL-safe). */
 void hot_destroy(hot_ctx *c);
 
-/* Instrumentation (no counterpart in the paper): measures, on the current device, the
+/* DIAGNOSTIC (not part of the method's path; for benchmarks): a microbenchmark kernel with
+ * no counterpart in the paper.  Measures, on the current device, the
  * throughput of the special-function unit that bounds hot_gsw in HOT_PREC_FAST mode, in
  * lane results per clock per SM, with a dependency-free loop of 1024 threads per SM whose
  * arguments change every iteration (clock64-timed).  op: 0 = sin.approx and cos.approx of
@@ -337,7 +391,8 @@ int hot_sfu_rate(int op, double *per_clk_per_sm, int *sms);
  * [6] rows padded to the 128-row tile, [7] 2W and [8] 2M padded to their tile widths. */
 int hot_tc_shape(int width, int height, int M, int sms, int *shape);
 
-/* The matrix product of HOT_PREC_TENSOR on its own (no counterpart in the paper):
+/* DIAGNOSTIC (not part of the method's path; a test hook): the matrix product of
+ * HOT_PREC_TENSOR on its own (no counterpart in the paper):
  * C = A B^T for DEVICE float32 arrays A [rows][K], B [cols][K] (row-major) into C [rows][cols],
  * on the tcgen05 tensor cores with every operand split into two parts (a b ~ a_hi b_hi +
  * a_hi b_lo + a_lo b_hi, FP32 accumulation, each K slice's partial product added in FP32
@@ -373,14 +428,19 @@ const char *hot_last_error(void);
  *   precision: HOT_PREC_ACCURATE or HOT_PREC_FAST.
  *   V: DEVICE output, 2*M doubles interleaved (Re, Im).  eu: DEVICE output of 2 doubles
  *   (e, u) or NULL.  cuda_stream: a cudaStream_t or NULL.
- * Work is queued on cuda_stream; the host reads nothing back.  Sizes whose working memory
- * exceeds the scratch array (about 8 M (W + H) + 60 M + 16 (W/32) (H/16) bytes) are
- * rejected with HOT_EINVAL and a message naming the need and the limit.
- * The first call on each device looks up the device address of the scratch array on that
- * device (cudaGetSymbolAddress): make that first call before any stream capture.  Every
- * call reuses the same array and leaves its contents behind: calls that overlap on the GPU
- * (on different streams, or from different host threads without ordering) race with each
- * other and give wrong results; serialise them. */
+ * Work is queued on cuda_stream; the host reads nothing back.  The working memory is
+ *   8 M (W + H) + 88 M + 16 n_sub + 4 (G + 1) bytes, plus at most 2.3 KiB of alignment,
+ * where G (at most 4 per SM) is the number of thread blocks and n_sub, about
+ * (W/32)(H/14) + 2 G, the number of pixel sub-tiles of the work schedule.  The call computes
+ * this need exactly before queueing any device work; sizes whose need exceeds the scratch array
+ * are rejected with HOT_EINVAL and a message naming the need and the limit.
+ * The first call on each device sets that device up (it must be the current device): it looks
+ * up the device address of the scratch array (cudaGetSymbolAddress), raises the forward-field
+ * kernels' shared-memory limit and reads their occupancy.  Make that first call before any
+ * stream capture.  Every call reuses the same array and leaves its contents behind (each call
+ * clears the field accumulators it adds into): calls that overlap on the GPU (on different
+ * streams, or from different host threads without ordering) race with each other and give
+ * wrong results; serialise them. */
 #define HOT_NOALLOC_SCRATCH_BYTES (16u << 20)
 int hot_field_noalloc(int width, int height, double pitch_m, double wavelength_m, double focal_m, int M,
                       const double *xyz_m, const float *phi, int precision, double *V, double *eu,

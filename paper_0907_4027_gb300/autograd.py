@@ -9,6 +9,10 @@ stream when the Hologram was created).
 
 trap_intensity_loss implements the loss of the differentiable configuration,
 L = -sum_m log |V_m|^2 + beta * var_m |V_m|^2 (population variance).
+
+intensity_loss(holo, phi, beta) is the same loss as one library call (hot_intensity_loss: the
+forward field, the loss and its adjoint coefficients, and the adjoint, all on the device), with
+the gradient kept for backward: an optimiser step then costs three kernels and the update.
 """
 from __future__ import annotations
 
@@ -47,3 +51,28 @@ def trap_intensity_loss(V: torch.Tensor, beta: float = 10.0) -> torch.Tensor:
     """-sum_m log I_m + beta var(I) with I_m = |V_m|^2 and the population variance."""
     I = V.real ** 2 + V.imag ** 2
     return -torch.log(I).sum() + beta * I.var(correction=0)
+
+
+class IntensityLoss(torch.autograd.Function):
+    """L(phi) = -sum log I + beta var(I) and dL/dphi from one hot_intensity_loss call; backward
+    scales the gradient computed with the loss."""
+
+    @staticmethod
+    def forward(ctx, phi: torch.Tensor, holo: "hot.Hologram", beta: float) -> torch.Tensor:
+        assert phi.is_cuda and phi.dtype == torch.float32 and phi.numel() == holo.N
+        phi = phi.contiguous()
+        loss = torch.empty(1, dtype=torch.float32, device=phi.device)
+        grad = torch.empty_like(phi) if ctx.needs_input_grad[0] else None
+        hot.hot_intensity_loss(holo.ctx, phi, beta, loss, grad)
+        ctx.save_for_backward(grad if grad is not None else loss)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, gL: torch.Tensor):
+        (grad,) = ctx.saved_tensors
+        return grad * gL, None, None
+
+
+def intensity_loss(holo: "hot.Hologram", phi: torch.Tensor, beta: float = 10.0) -> torch.Tensor:
+    """-sum_m log I_m + beta var(I) of the traps' intensities for phases phi, differentiable in phi."""
+    return IntensityLoss.apply(phi, holo, beta)

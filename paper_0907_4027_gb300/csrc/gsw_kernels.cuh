@@ -13,7 +13,8 @@
 // Per pair the kernels take exactly one complex exponential and accumulate it without a
 // complex multiply: the back-projection folds the phase of its coefficient into the argument,
 // S_j += w_m e^{i (Delta_j^m + arg V_m)}, and the forward field evaluates Eq. 1 as written,
-// V_m += e^{i (phi_j - Delta_j^m)}.
+// V_m += e^{i (phi_j - Delta_j^m)} (the fast mode with a per-sub-tile rotation of the phases
+// that it undoes on each sub-tile's sums: see forward_traps).
 //
 // Phase generation: Eq. 2 splits into a column part and a row part,
 //   Delta_j^m / 2pi = [a_m ix' + c_m ix'^2] + [b_m iy' + c_m iy'^2]
@@ -75,6 +76,7 @@ struct StepArgs {
   float fx_scale;           // 2^fx_shift: fixed-point scale of the sums
   float inv_fx_n;           // 1 / (N 2^fx_shift)
   float angle_units;        // 1 (radians) or 1/(2 pi) (turns): units of the tables
+  float angle_eta;          // kFastEta (fast mode) or 0: relative scale added to angles in table units
 };
 
 __device__ __forceinline__ float sin_approx(float x) {
@@ -88,35 +90,69 @@ __device__ __forceinline__ float cos_approx(float x) {
   return y;
 }
 
-// cos and sin of an angle given in table units: radians (fast) or turns (accurate).
+// The fast mode's angles are scaled by 1 + kFastEta before they reach sin.approx/cos.approx.
+// Those instructions turn radians into revolutions with a multiplication by a rounded 1/(2 pi)
+// that is rounded toward zero: on average the argument shrinks by 4.03e-8 (the constant) plus
+// 2^-24 ln 2 = 4.13e-8 (the rounding, mean over a binade) of itself.  The scale is folded into
+// the tables (FP64, when they are built), the pixel phases (once per pixel) and the
+// coefficients' phases (once per trap), so it costs nothing per pair.  (What remains of the
+// systematic part of the SFU's error is kept from adding up in the forward field by the
+// per-sub-tile rotation of forward_traps.)
+constexpr float kFastEta = 8.17e-8f;
+
+// cos and sin of an angle given in table units: radians (fast, pre-scaled by 1 + kFastEta,
+// |x| <= 3 pi here) or turns (accurate).
 template <bool FAST>
 __device__ __forceinline__ void cis(float x, float &co, float &si) {
   if (FAST) {
-    si = sin_approx(x);  // |x| <= 3 pi here
+    si = sin_approx(x);
     co = cos_approx(x);
   } else {
     sincospif(2.0f * x, &si, &co);  // |x| <= 3/2 turns
   }
 }
 
-// A pixel phase (radians) in table units: radians (fast) or turns (accurate).
-template <bool FAST>
-__device__ __forceinline__ float phase_units(float ph) {
-  return FAST ? ph : ph * 0.15915494309189535f;
+// A pixel phase (radians) in turns (the accurate mode's table units).
+__device__ __forceinline__ float phase_turns(float ph) { return ph * 0.15915494309189535f; }
+
+// A caller's pixel phase (any real value, radians) reduced to one turn, in turns.
+__device__ __forceinline__ float reduced_phase_turns(float ph) {
+  const float t = ph * 0.15915494309189535f;
+  return t - rintf(t);
 }
 
-// A caller's pixel phase (any real value, radians) reduced to one turn, in table units.
-template <bool FAST>
-__device__ __forceinline__ float reduced_phase_units(float ph) {
+// A phase (radians) reduced to [-pi, pi] (two-part 2 pi).
+__device__ __forceinline__ float reduced_radians(float ph) {
   const float k = rintf(ph * 0.15915494309189535f);
-  if (!FAST) return ph * 0.15915494309189535f - k;
   return fmaf(-k, -1.74845553e-07f, fmaf(-k, 6.28318548e+00f, ph));
+}
+
+// The rotation theta in [-pi, pi) of a sub-tile of the fast forward field (see forward_traps),
+// a fixed function of its position: a Weyl sequence (golden-ratio multiple, modulo 2^32) of the
+// sub-tile's first pixel, so that neighbouring sub-tiles take well-spread angles.
+__device__ __forceinline__ float subtile_rotation(const SubTile &st) {
+  const unsigned h = ((unsigned)st.x0 * 65599u + (unsigned)st.y0) * 2654435769u;
+  return (float)(h >> 8) * 3.7450018e-07f - 3.14159265f;  // 2 pi / 2^24
+}
+
+// e^{-i theta}, which undoes the rotation on the sub-tile's sums.
+__device__ __forceinline__ float2 rotation_undo(float theta) {
+  float s, c;
+  sincosf(theta, &s, &c);
+  return make_float2(c, -s);
+}
+
+// Fast mode: the forward field's pixel phase phi_j + theta (|phi_j| <= pi) in table units:
+// reduced to [-pi, pi], scaled by 1 + kFastEta.
+__device__ __forceinline__ float rotated_phase(float ph, float theta) {
+  const float r = reduced_radians(ph + theta);
+  return fmaf(r, kFastEta, r);
 }
 
 
 // Shared memory of a block: the staged tables of one trap chunk (X for the sub-tile's 32
 // columns, Y for its rows, and the chunk's coefficients), the per-warp partial superpositions
-// of half a sub-tile's rows, and the pixel phases of the sub-tile.
+// of half a sub-tile's rows, and the pixel phases of the sub-tile for the forward field.
 constexpr int kHalfRows = kRowsMax / 2;
 constexpr int kXsFloats = kChunk * kTileW;
 constexpr int kYsFloats = kChunk * kYStride;
@@ -146,6 +182,30 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
+// Groups: a block of the step kernel may hold several groups of kThreads threads, each acting
+// as one block of the work schedule, a "virtual block" (see gsw_step_kernel).  With one group
+// per block, gthread, vblock and vgrid are threadIdx.x, blockIdx.x and gridDim.x, and
+// group_sync is a barrier of the whole block.
+constexpr int kMaxGroups = 4;
+__device__ __forceinline__ int gthread() { return threadIdx.x & (kThreads - 1); }
+__device__ __forceinline__ int group_id() { return threadIdx.x / kThreads; }
+__device__ __forceinline__ int vblock() { return blockIdx.x * (blockDim.x / kThreads) + group_id(); }
+__device__ __forceinline__ int vgrid() { return gridDim.x * (blockDim.x / kThreads); }
+__device__ __forceinline__ void group_sync() {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + group_id()), "n"(kThreads) : "memory");
+}
+
+// Traps [lo, hi) of a staged chunk of n that warp `warp` of a group takes.  Warps w and w + 4
+// issue to the same SM sub-partition (warp slot mod 4) and share its special-function unit, so
+// each such pair takes one quarter of the chunk, split between its two warps: every
+// sub-partition gets the same number of traps to within one (with M = 100 a plain eighth split
+// gives two sub-partitions 26 traps and two 24).
+__device__ __forceinline__ void warp_traps(int n, int warp, int &lo, int &hi) {
+  const int s = warp & 3, q0 = s * n / 4, q1 = (s + 1) * n / 4, mid = (q0 + q1) >> 1;
+  lo = warp < 4 ? q0 : mid;
+  hi = warp < 4 ? mid : q1;
+}
+
 // The field V_m of the previous forward, from its fixed-point sums; MULTI: added over the
 // copies (integer addition, exact in any order).  The direct kernels run with one copy.
 template <bool MULTI = false>
@@ -162,14 +222,15 @@ __device__ __forceinline__ float2 field_from_sums(const StepArgs &a, int m) {
 
 // The accumulator copy this block adds its forward sums into (copies is a power of two).
 __device__ __forceinline__ unsigned long long *block_acc(const StepArgs &a) {
-  return a.acc_out + (size_t)(blockIdx.x & (unsigned)(a.copies - 1)) * 2 * a.M;
+  return a.acc_out + (size_t)((unsigned)vblock() & (unsigned)(a.copies - 1)) * 2 * a.M;
 }
 
 // Sec. 3 weight update and back-projection coefficient of a trap with field v and weight w:
 // w <- w <|V|>/|V_m|; if |V_m| < 1e-30 the unit field is 1 and w stays.  Polar form
-// (w', arg V_m in table units), or complex form w' V_m/|V_m| (COMPLEX).
+// (w', arg V_m in table units: times units, plus eta of itself), or complex form w' V_m/|V_m|
+// (COMPLEX).
 template <bool COMPLEX>
-__device__ __forceinline__ float2 update_from(float2 v, float w, float mean, float units) {
+__device__ __forceinline__ float2 update_from(float2 v, float w, float mean, float units, float eta = 0.f) {
   const float am = sqrtf(v.x * v.x + v.y * v.y);
   if (COMPLEX) {
     if (am < 1e-30f) return make_float2(w, 0.f);
@@ -177,19 +238,21 @@ __device__ __forceinline__ float2 update_from(float2 v, float w, float mean, flo
     return make_float2(s * v.x, s * v.y);
   }
   if (am >= 1e-30f) w = w * mean / am;
-  return make_float2(w, am >= 1e-30f ? atan2f(v.y, v.x) * units : 0.f);
+  const float ang = atan2f(v.y, v.x);
+  return make_float2(w, am >= 1e-30f ? fmaf(ang, eta, ang * units) : 0.f);
 }
 
 // The coefficient of trap m from the previous forward's sums and weights (both written by
 // other blocks: read from L2, not from a possibly stale L1 line).
 __device__ __forceinline__ float2 coefficient(const StepArgs &a, int m, float mean) {
-  return update_from<false>(field_from_sums(a, m), __ldcg(a.w_in + m), mean, a.angle_units);
+  return update_from<false>(field_from_sums(a, m), __ldcg(a.w_in + m), mean, a.angle_units, a.angle_eta);
 }
 
 // Explicit coefficient of trap m (superposition or adjoint) in polar form (|G_m|, arg G_m).
 __device__ __forceinline__ float2 adjoint_coefficient(const StepArgs &a, int m) {
   const float2 g = a.G[m];
-  return make_float2(sqrtf(g.x * g.x + g.y * g.y), atan2f(g.y, g.x) * a.angle_units);
+  const float ang = atan2f(g.y, g.x);
+  return make_float2(sqrtf(g.x * g.x + g.y * g.y), fmaf(ang, a.angle_eta, ang * a.angle_units));
 }
 
 // Stages, with asynchronous copies (all in flight at once), the X (32 columns from x0) and Y
@@ -200,18 +263,18 @@ template <bool BACK, bool ADJ = false>
 __device__ __forceinline__ void stage_tables(const StepArgs &a, int m0, int n, const SubTile &st,
                                              float *Xs, float *Ys, float2 *Cs, bool xy = true,
                                              float mean = 0.f, bool coef = true) {
-  for (int i = threadIdx.x; xy && i < n * kTileW; i += kThreads) {
+  for (int i = gthread(); xy && i < n * kTileW; i += kThreads) {
     const int k = i / kTileW, col = st.x0 + (i % kTileW);
     const bool ok = col < a.W;
     cp_async4(Xs + i, a.X + (ok ? (size_t)(m0 + k) * a.W + col : 0), ok);
   }
-  for (int i = threadIdx.x; xy && i < n * kYStride; i += kThreads) {
+  for (int i = gthread(); xy && i < n * kYStride; i += kThreads) {
     const int k = i / kYStride, r = i % kYStride;
     const bool ok = r < st.rows;
     cp_async4(Ys + i, a.Y + (ok ? (size_t)(m0 + k) * a.H + st.y0 + r : 0), ok);
   }
   if (BACK && coef)
-    for (int i = threadIdx.x; i < n; i += kThreads)
+    for (int i = gthread(); i < n; i += kThreads)
       Cs[i] = (ADJ || a.G) ? adjoint_coefficient(a, m0 + i) : coefficient(a, m0 + i, mean);
   cp_async_wait_all();
 }
@@ -281,10 +344,17 @@ __device__ __forceinline__ void back_traps(const float *Xs, const float *Ys, con
 // column: sum_r e^{i (phi_r - X_m - Y_m(r))}, summed over the warp 8 traps at a time and
 // added, in fixed point, to acc_out[m0 + k] (Re) and acc_out[M + m0 + k] (Im).  ph holds the lane's
 // pixel phases in table units; msk is 1 for a lane inside the image, 0 past its right edge.
+// Fast mode: ph holds phi_r + theta, theta a rotation fixed per sub-tile, and each trap's sum
+// over the sub-tile is multiplied by undo = e^{-i theta} before it is added (4 FP32 operations
+// per trap and sub-tile).  The SFU's error has a systematic part: measured on GB300, fields of
+// random phases evaluated without the rotation carry an offset of ~1e-8 on every trap, the same
+// for all traps (their arguments phi_j - Delta_j^m are spread alike), ~1e-4 of the weakest
+// |V_m| on a 512^2 SLM.  With the rotation, the offset of each sub-tile's sum turns by its own
+// angle -theta, and over the sub-tiles those contributions cancel instead of adding up.
 template <bool FAST, int R>
 __device__ __forceinline__ void forward_traps(const float *Xs, const float *Ys, int lo, int hi, int lane,
                                               const float (&ph)[kRowsMax], float msk, const StepArgs &a,
-                                              int m0) {
+                                              int m0, float2 undo = make_float2(1.f, 0.f)) {
   for (int g = lo; g < hi; g += kGroup) {
     float2 acc[kGroup];
 #pragma unroll
@@ -311,7 +381,8 @@ __device__ __forceinline__ void forward_traps(const float *Xs, const float *Ys, 
         }
       }
     }
-    const float2 v = warp_reduce8(acc, lane);
+    float2 v = warp_reduce8(acc, lane);
+    if (FAST) v = make_float2(fmaf(v.x, undo.x, -v.y * undo.y), fmaf(v.x, undo.y, v.y * undo.x));
     const int k = g + ((lane >> 2) & 7);
     if ((lane & 3) == 0 && k < hi) {
       // |v| <= 32 * kRowsMax, so v * 2^fx_shift is an exact integer far below 2^63
@@ -349,13 +420,13 @@ struct LateWeight {
 // COMPLEX) without the factor <|V|> of the weight update: a factor common to all coefficients
 // scales S_j and leaves arg S_j unchanged (the weights' global scale is free, reading R6), so
 // no block-wide reduction stands between the sums and the back-projection.  Keeps in lw the
-// thread's share of sum |V_m| and the prefetched weight of trap own + stride * threadIdx.x,
+// thread's share of sum |V_m| and the prefetched weight of trap own + stride * gthread(),
 // which write_weights completes after the block's work.
 // trace: NULL, or where block 0 writes e and u (Eq. 4) of the fields it read (convergence trace).
 template <bool COMPLEX>
 __device__ __forceinline__ void gsw_prologue(const StepArgs &a, int mc, float2 *C0, int own, int stride,
                                              LateWeight &lw, float *trace = nullptr) {
-  const int t = threadIdx.x;
+  const int t = gthread();
   lw.own = own;
   lw.m = own + stride * t;
   lw.v = make_float2(0.f, 0.f);
@@ -367,7 +438,7 @@ __device__ __forceinline__ void gsw_prologue(const StepArgs &a, int mc, float2 *
   const float w0 = t < mc ? __ldcg(a.w_in + t) : 0.f;
   float2 v0 = make_float2(0.f, 0.f);
   ff s = {0.f, 0.f};
-  const bool tr = trace && blockIdx.x == 0;
+  const bool tr = trace && vblock() == 0;
   ff si = {0.f, 0.f};
   float mx = -1.f, mn = 3.0e38f;
   for (int m = t; m < a.M; m += kThreads) {
@@ -382,10 +453,10 @@ __device__ __forceinline__ void gsw_prologue(const StepArgs &a, int mc, float2 *
     }
   }
   lw.part = s;
-  if (t < mc) C0[t] = update_from<COMPLEX>(v0, w0, 1.f, a.angle_units);
-  if (tr) {  // block 0 only: e = sum I_m, u = 1 - (max - min)/(max + min) of the fields read
+  if (t < mc) C0[t] = update_from<COMPLEX>(v0, w0, 1.f, a.angle_units, a.angle_eta);
+  if (tr) {  // virtual block 0 only: e = sum I_m, u = 1 - (max - min)/(max + min) of the fields read
     __shared__ ff tpart[kWarps];
-    __shared__ float ext[2][kWarps];
+    __shared__ float ext[2][kWarps];  // (group 0 of block 0 alone uses these)
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       si = ff_add(si, {__shfl_down_sync(0xffffffffu, si.hi, o), __shfl_down_sync(0xffffffffu, si.lo, o)});
@@ -397,7 +468,7 @@ __device__ __forceinline__ void gsw_prologue(const StepArgs &a, int mc, float2 *
       ext[0][t >> 5] = mx;
       ext[1][t >> 5] = mn;
     }
-    __syncthreads();
+    group_sync();
     if (t == 0) {
       ff e = tpart[0];
       float hi = ext[0][0], lo = ext[1][0];
@@ -419,14 +490,15 @@ __device__ __forceinline__ void gsw_prologue(const StepArgs &a, int mc, float2 *
 template <bool MULTI = false>
 __device__ __forceinline__ void write_weights(const StepArgs &a, const LateWeight &lw, int stride) {
   if (lw.own >= a.M) return;
-  __shared__ ff part[kWarps];
+  __shared__ ff parts[kMaxGroups][kWarps];
+  ff *const part = parts[group_id()];
   ff s = lw.part;
 #pragma unroll
   for (int o = 16; o; o >>= 1)
     s = ff_add(s, {__shfl_down_sync(0xffffffffu, s.hi, o), __shfl_down_sync(0xffffffffu, s.lo, o)});
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
-  __syncthreads();
+  group_sync();
+  if ((gthread() & 31) == 0) part[gthread() >> 5] = s;
+  group_sync();
   ff q = part[0];
 #pragma unroll
   for (int i = 1; i < kWarps; i++) q = ff_add(q, part[i]);
@@ -570,7 +642,7 @@ struct StepSmem {
 template <bool FAST, bool BACK, bool FWD, bool ADJ>
 __device__ __forceinline__ void process_subtile(const StepArgs &a, const SubTile st, float mean, bool &prestaged,
                                                 const StepSmem &sm, const float2 *C0 = nullptr) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = gthread() >> 5;
   const int mc = a.M < a.chunk ? a.M : a.chunk;
   const int nchunks = (a.M + mc - 1) / mc;
   const int ix = st.x0 + lane;
@@ -583,11 +655,12 @@ __device__ __forceinline__ void process_subtile(const StepArgs &a, const SubTile
     for (int ch = 0; ch < nchunks; ch++) {
       const int m0 = ch * mc, n = min(mc, a.M - m0);
       const bool pre = C0 && ch == 0;
-      __syncthreads();  // earlier readers of the tables are done
+      group_sync();  // earlier readers of the tables are done
       stage_tables<true, ADJ>(a, m0, n, st, sm.Xs, sm.Ys, sm.Cs, !prestaged, mean, !pre);
       prestaged = false;
-      __syncthreads();
-      const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
+      group_sync();
+      int lo, hi;
+      warp_traps(n, warp, lo, hi);
       const float2 *C = pre ? C0 : sm.Cs;
       HOT_WITH_ROWS(st.rows, (back_traps<FAST, R>(sm.Xs, sm.Ys, C, lo, hi, lane, S)));
     }
@@ -595,11 +668,11 @@ __device__ __forceinline__ void process_subtile(const StepArgs &a, const SubTile
 #pragma unroll
     for (int h = 0; h < 2; h++) {
       if (h * kHalfRows >= st.rows) break;
-      __syncthreads();  // Sp and the phase rows are free
+      group_sync();  // Sp and the phase rows are free
 #pragma unroll
       for (int i = 0; i < kHalfRows; i++)
         if (h * kHalfRows + i < st.rows) sm.Sp[(warp * kHalfRows + i) * kTileW + lane] = S[h * kHalfRows + i];
-      __syncthreads();
+      group_sync();
       if (warp < kHalfRows && h * kHalfRows + warp < st.rows) {
         const int r = h * kHalfRows + warp;
         float2 s = sm.Sp[warp * kTileW + lane];
@@ -619,41 +692,52 @@ __device__ __forceinline__ void process_subtile(const StepArgs &a, const SubTile
         } else {
           const float ph = atan2f(s.y, s.x);
           if (col_ok) a.phi[j] = ph;
-          if (FWD) sm.Ps[r * kTileW + lane] = phase_units<FAST>(ph);
+          if (FWD) sm.Ps[r * kTileW + lane] = FAST ? rotated_phase(ph, subtile_rotation(st)) : phase_turns(ph);
         }
       }
     }
   } else if (FWD) {
-    __syncthreads();  // earlier readers of the phases and of the tables are done
-    for (int r = warp; r < st.rows; r += kWarps)
-      sm.Ps[r * kTileW + lane] = col_ok ? reduced_phase_units<FAST>(a.phi[(size_t)(st.y0 + r) * a.W + ix]) : 0.0f;
+    group_sync();  // earlier readers of the phases and of the tables are done
+    for (int r = warp; r < st.rows; r += kWarps) {
+      const float ph = col_ok ? a.phi[(size_t)(st.y0 + r) * a.W + ix] : 0.0f;
+      sm.Ps[r * kTileW + lane] = FAST ? rotated_phase(reduced_radians(ph), subtile_rotation(st)) : reduced_phase_turns(ph);
+    }
   }
 
   if (FWD) {
-    __syncthreads();  // the phases are complete
+    const float2 undo = FAST ? rotation_undo(subtile_rotation(st)) : make_float2(1.f, 0.f);
+    group_sync();  // the phases are complete
     float ph[kRowsMax];
 #pragma unroll
     for (int r = 0; r < kRowsMax; r++) ph[r] = r < st.rows ? sm.Ps[r * kTileW + lane] : 0.0f;
     for (int ch = 0; ch < nchunks; ch++) {
       const int m0 = ch * mc, n = min(mc, a.M - m0);
       if (!BACK || nchunks > 1) {  // with one chunk the back-projection's tables are still staged
-        if (ch) __syncthreads();
+        if (ch) group_sync();
         stage_tables<false>(a, m0, n, st, sm.Xs, sm.Ys, sm.Cs);
-        __syncthreads();
+        group_sync();
       }
-      const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
-      HOT_WITH_ROWS(st.rows, (forward_traps<FAST, R>(sm.Xs, sm.Ys, lo, hi, lane, ph, col_ok ? 1.f : 0.f, a, m0)));
+      int lo, hi;
+      warp_traps(n, warp, lo, hi);
+      HOT_WITH_ROWS(st.rows, (forward_traps<FAST, R>(sm.Xs, sm.Ys, lo, hi, lane, ph, col_ok ? 1.f : 0.f, a, m0, undo)));
     }
   }
 }
 
-template <bool FAST, bool BACK, bool FWD, bool ADJ = false>
-__global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
+// GROUPS > 1: one block of GROUPS x kThreads threads per SM, group g of block b acting as
+// virtual block GROUPS b + g of the schedule, with its own shared memory and barrier.  The
+// schedule deals consecutive runs of row segments to consecutive virtual blocks, so the GROUPS
+// runs of an SM add up to its equal share of the image to within one segment, whereas with
+// independent blocks an SM may hold GROUPS runs that are all one segment longer than average.
+template <bool FAST, bool BACK, bool FWD, bool ADJ = false, int GROUPS = 1>
+__global__ void __launch_bounds__(kThreads * GROUPS, GROUPS == 1 ? 4 : 1) gsw_step_kernel(StepArgs a) {
   static_assert(!ADJ || (BACK && !FWD), "the adjoint is a back-projection without forward field");
+  static_assert(GROUPS >= 1 && GROUPS <= kMaxGroups, "groups per block");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const StepSmem sm(smem_raw);
+  const StepSmem sm(smem_raw + (GROUPS > 1 ? group_id() * kSmemBytes : 0));
   const int mc = a.M < a.chunk ? a.M : a.chunk;
-  const int t_begin = a.first[blockIdx.x], t_end = a.first[blockIdx.x + 1];
+  const int vb = vblock(), vg = vgrid();
+  const int t_begin = a.first[vb], t_end = a.first[vb + 1];
 
   // Prologue, overlapping the previous kernel: the trap tables are constant during hot_gsw,
   // so the first chunk of the back-projection is staged before waiting for its field sums.
@@ -666,17 +750,106 @@ __global__ void __launch_bounds__(kThreads, 4) gsw_step_kernel(StepArgs a) {
   }
   grid_dependency_wait();
   if (FWD)  // the buffer the next launch accumulates into
-    for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M * a.copies; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
+    for (int i = vb * kThreads + gthread(); i < 2 * a.M * a.copies; i += vg * kThreads) a.acc_clear[i] = 0ull;
   LateWeight lw;
   const bool gsw = BACK && !ADJ && !a.G;
-  if (gsw) gsw_prologue<false>(a, mc, sm.C0, blockIdx.x, gridDim.x, lw, a.trace);
+  if (gsw) gsw_prologue<false>(a, mc, sm.C0, vb, vg, lw, a.trace);
   for (int t = t_begin; t < t_end; t++)
     process_subtile<FAST, BACK, FWD, ADJ>(a, a.sub[t], 1.f, prestaged, sm, gsw ? sm.C0 : nullptr);
-  if (gsw) write_weights(a, lw, gridDim.x);
+  if (gsw) write_weights(a, lw, vg);
 }
 
 // Start stamp of a batched sequence (%globaltimer, ns).
 __global__ void stamp_kernel(unsigned long long *t) { *t = global_timer_ns(); }
+
+// The trap-intensity loss of the differentiable form and its adjoint coefficients, from the
+// forward field's fixed-point sums: I_m = |V_m|^2 (the intensities of Eq. 4),
+//   L = -sum_m log I_m + beta var_m(I)   (population variance),
+//   G_m = 2 dL/d conj(V_m) = 2 g_m V_m,  g_m = dL/dI_m = -1/I_m + beta (2/M)(I_m - mean I),
+// the coefficients of the adjoint superposition (hot_field_adjoint) that gives dL/dphi.  One
+// block; FP64 sums in a fixed order (threads, then warps in order).  Like gsw_finalize_kernel it
+// also leaves the sums for the caller, e and u, and clears the accumulators.
+struct LossArgs {
+  int M, copies;
+  const unsigned long long *acc;  // [copies][2][M] sums of the forward field
+  unsigned long long *acc_all;    // [3][copies][2][M]: cleared
+  long long *Vsum;                // [2][M] out
+  float *metrics;                 // [2] out: e, u
+  double inv_fx_n;                // 1 / (N 2^fx_shift)
+  double beta;
+  float2 *G;                      // [M] out
+  float *loss;                    // [1] out
+};
+
+constexpr int kLossThreads = 1024;
+
+// Sum over the block in a fixed order; every thread gets the total.
+__device__ __forceinline__ double block_sum(double v, double *part) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();  // earlier readers of part are done
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < kLossThreads / 32; i++) t += part[i];
+  return t;
+}
+
+__global__ void __launch_bounds__(kLossThreads) intensity_loss_kernel(LossArgs a) {
+  __shared__ double part[kLossThreads / 32];
+  __shared__ float ext[2][kLossThreads / 32];
+  double sI = 0.0, sLog = 0.0;
+  float mx = -1.f, mn = 3.0e38f;
+  for (int m = threadIdx.x; m < a.M; m += kLossThreads) {
+    long long sr = 0, si = 0;
+    for (int c = 0; c < a.copies; c++) {
+      sr += (long long)a.acc[(size_t)c * 2 * a.M + m];
+      si += (long long)a.acc[(size_t)c * 2 * a.M + a.M + m];
+    }
+    a.Vsum[m] = sr;
+    a.Vsum[a.M + m] = si;
+    const double vr = (double)sr * a.inv_fx_n, vi = (double)si * a.inv_fx_n, I = vr * vr + vi * vi;
+    sI += I;
+    sLog += log(I);
+    mx = fmaxf(mx, (float)I);
+    mn = fminf(mn, (float)I);
+  }
+  const double e = block_sum(sI, part), slog = block_sum(sLog, part);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    ext[0][threadIdx.x >> 5] = mx;
+    ext[1][threadIdx.x >> 5] = mn;
+  }
+  const double mean = e / a.M;
+  double sVar = 0.0;
+  for (int m = threadIdx.x; m < a.M; m += kLossThreads) {
+    const double vr = (double)a.Vsum[m] * a.inv_fx_n, vi = (double)a.Vsum[a.M + m] * a.inv_fx_n;
+    const double d = vr * vr + vi * vi - mean;
+    sVar += d * d;
+  }
+  const double var = block_sum(sVar, part) / a.M;  // (its barriers also order ext and Vsum)
+  for (int m = threadIdx.x; m < a.M; m += kLossThreads) {
+    const double vr = (double)a.Vsum[m] * a.inv_fx_n, vi = (double)a.Vsum[a.M + m] * a.inv_fx_n;
+    const double I = vr * vr + vi * vi;
+    const double g = -1.0 / I + a.beta * (2.0 / a.M) * (I - mean);
+    a.G[m] = make_float2((float)(2.0 * g * vr), (float)(2.0 * g * vi));
+  }
+  for (int i = threadIdx.x; i < 6 * a.M * a.copies; i += kLossThreads) a.acc_all[i] = 0ull;
+  if (threadIdx.x == 0) {
+    float hi = ext[0][0], lo = ext[1][0];
+    for (int i = 1; i < kLossThreads / 32; i++) {
+      hi = fmaxf(hi, ext[0][i]);
+      lo = fminf(lo, ext[1][i]);
+    }
+    *a.loss = (float)(-slog + a.beta * var);
+    a.metrics[0] = (float)e;
+    a.metrics[1] = (hi + lo > 0.f) ? 1.f - (hi - lo) / (hi + lo) : 0.f;
+  }
+}
 
 // ---------------------------------------------------------------------------------------------
 // Separable variant.  Eq. 2 is a sum of a column part and a row part, so every pair's
@@ -720,19 +893,19 @@ __device__ __forceinline__ void stage_sep(const StepArgs &a, int m0, int n, cons
   if (xy) {
     // thread t copies column t % 32 of traps t / 32, t / 32 + 8, ... and row t % 16 of traps
     // t / 16, t / 16 + 16, ...: fixed column / row, pointers advanced by whole trap strides
-    const int col = threadIdx.x % kTileW, kx = threadIdx.x / kTileW;
+    const int col = gthread() % kTileW, kx = gthread() / kTileW;
     const bool okx = st.x0 + col < a.W;
     const float2 *src = a.Xc + (okx ? (size_t)(m0 + kx) * a.W + st.x0 + col : 0);
     const size_t sx = okx ? (size_t)(kThreads / kTileW) * a.W : 0;
     for (int k = kx; k < n; k += kThreads / kTileW, src += sx) cp_async8(sm.Xs + k * kTileW + col, src, okx);
-    const int r = threadIdx.x % kYStride, ky = threadIdx.x / kYStride;
+    const int r = gthread() % kYStride, ky = gthread() / kYStride;
     const bool oky = r < st.rows;
     const float2 *srcy = a.Yc + (oky ? (size_t)(m0 + ky) * a.H + st.y0 + r : 0);
     const size_t sy = oky ? (size_t)(kThreads / kYStride) * a.H : 0;
     for (int k = ky; k < n; k += kThreads / kYStride, srcy += sy) cp_async8(sm.Ys + k * kYStride + r, srcy, oky);
   }
   if (BACK && coef)
-    for (int i = threadIdx.x; i < n; i += kThreads)
+    for (int i = gthread(); i < n; i += kThreads)
       sm.Cs[i] = (ADJ || a.G) ? a.G[m0 + i] : complex_coefficient(a, m0 + i, mean);
   cp_async_wait_all();
 }
@@ -806,7 +979,7 @@ __device__ __forceinline__ void forward_traps_sep(const SepSmem &sm, int lo, int
 template <bool BACK, bool FWD, bool ADJ>
 __device__ __forceinline__ void process_subtile_sep(const StepArgs &a, const SubTile st, float mean, bool &prestaged,
                                                     const SepSmem &sm, const float2 *C0 = nullptr) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = gthread() >> 5;
   const int mc = a.M < a.chunk ? a.M : a.chunk;
   const int nchunks = (a.M + mc - 1) / mc;
   const int ix = st.x0 + lane;
@@ -819,22 +992,23 @@ __device__ __forceinline__ void process_subtile_sep(const StepArgs &a, const Sub
     for (int ch = 0; ch < nchunks; ch++) {
       const int m0 = ch * mc, n = min(mc, a.M - m0);
       const bool pre = C0 && ch == 0;
-      __syncthreads();  // earlier readers of the tables are done
+      group_sync();  // earlier readers of the tables are done
       stage_sep<true, ADJ>(a, m0, n, st, sm, !prestaged, mean, !pre);
       prestaged = false;
-      __syncthreads();
-      const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
+      group_sync();
+      int lo, hi;
+      warp_traps(n, warp, lo, hi);
       const float2 *C = pre ? C0 : sm.Cs;
       HOT_WITH_ROWS(st.rows, (back_traps_sep<R>(sm, C, lo, hi, lane, S)));
     }
 #pragma unroll
     for (int h = 0; h < 2; h++) {
       if (h * kHalfRows >= st.rows) break;
-      __syncthreads();  // Sp and the phasor rows are free
+      group_sync();  // Sp and the phasor rows are free
 #pragma unroll
       for (int i = 0; i < kHalfRows; i++)
         if (h * kHalfRows + i < st.rows) sm.Sp[(warp * kHalfRows + i) * kTileW + lane] = S[h * kHalfRows + i];
-      __syncthreads();
+      group_sync();
       if (warp < kHalfRows && h * kHalfRows + warp < st.rows) {
         const int r = h * kHalfRows + warp;
         float2 s = sm.Sp[warp * kTileW + lane];
@@ -863,7 +1037,7 @@ __device__ __forceinline__ void process_subtile_sep(const StepArgs &a, const Sub
       }
     }
   } else if (FWD) {
-    __syncthreads();  // earlier readers of the phasors and of the tables are done
+    group_sync();  // earlier readers of the phasors and of the tables are done
     for (int r = warp; r < st.rows; r += kWarps) {
       float2 u = make_float2(0.f, 0.f);
       if (col_ok) sincosf(a.phi[(size_t)(st.y0 + r) * a.W + ix], &u.y, &u.x);
@@ -872,18 +1046,19 @@ __device__ __forceinline__ void process_subtile_sep(const StepArgs &a, const Sub
   }
 
   if (FWD) {
-    __syncthreads();  // the phasors are complete
+    group_sync();  // the phasors are complete
     float2 u[kRowsMax];
 #pragma unroll
     for (int r = 0; r < kRowsMax; r++) u[r] = r < st.rows ? sm.Us[r * kTileW + lane] : make_float2(0.f, 0.f);
     for (int ch = 0; ch < nchunks; ch++) {
       const int m0 = ch * mc, n = min(mc, a.M - m0);
       if (!BACK || nchunks > 1) {  // with one chunk the back-projection's tables are still staged
-        if (ch) __syncthreads();
+        if (ch) group_sync();
         stage_sep<false>(a, m0, n, st, sm);
-        __syncthreads();
+        group_sync();
       }
-      const int lo = warp * n / kWarps, hi = (warp + 1) * n / kWarps;
+      int lo, hi;
+      warp_traps(n, warp, lo, hi);
       HOT_WITH_ROWS(st.rows, (forward_traps_sep<R>(sm, lo, hi, lane, u, a, m0)));
     }
   }
@@ -1112,7 +1287,8 @@ __global__ void build_tables_kernel(int W, int H, int H_total, int y_off, int M,
       t = fma(cm * q, q, bm * q);
     }
     t -= rint(t);  // [-1/2, 1/2] turns
-    const float tf = (float)t, rf = (float)(t * 6.283185307179586476925286766559);
+    // turns (accurate mode); radians scaled by 1 + kFastEta (fast mode, see cis)
+    const float tf = (float)t, rf = (float)(t * (6.283185307179586476925286766559 * (1.0 + (double)kFastEta)));
     double sn = 0.0, cs = 1.0;
     if (Xc) sincospi(2.0 * t, &sn, &cs);
     if (i < W) {

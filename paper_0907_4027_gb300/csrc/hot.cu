@@ -71,6 +71,8 @@ struct hot_ctx {
   // (0: as many as fit), traps per staged chunk
   int tile_rows = hot::kRowsMax, tile_bps = 0, tile_chunk = hot::kChunk;
   int sched_bps = 0, sched_bps_max = 0;  // resident blocks per SM in the schedule; occupancy limit
+  int tile_merge = 0;  // hot_set_block_merge: the GSW step's 4 blocks per SM as one launched block
+  int groups = 1;      // schedule blocks per launched block of the direct GSW step (1 or 4)
   int shard_k = -1;                      // last launch of a sharded sequence (hot_sharded_*)
   // state
   float *phi = nullptr;  // [N]
@@ -113,6 +115,7 @@ struct hot_ctx {
   std::vector<Graph> graphs;
   // HOT_PREC_TENSOR: operands and launch shapes of the tensor-core iteration (built on first use)
   hot_tc::Plan *tc = nullptr;
+  float2 *G = nullptr;  // [M] adjoint coefficients of hot_intensity_loss (allocated on first use)
 };
 
 namespace {
@@ -161,6 +164,7 @@ void free_traps(hot_ctx *c) {
   dfree(c->w);
   dfree(c->acc);
   dfree(c->Vsum);
+  dfree(c->G);
   c->M = 0;
   c->have_fields = false;
 }
@@ -252,6 +256,7 @@ hot::StepArgs make_step_args(const hot_ctx *c, int k, const float *phi, const fl
   a.fx_scale = ldexpf(1.0f, c->fx_shift);
   a.inv_fx_n = (float)(1.0 / (n_total(c) * ldexp(1.0, c->fx_shift)));
   a.angle_units = fast ? 1.0f : 0.15915494309189535f;
+  a.angle_eta = fast ? hot::kFastEta : 0.0f;
   if (phi) a.phi = const_cast<float *>(phi);  // read only: forward field or adjoint of given phases
   a.G = G;
   a.grad = grad;
@@ -269,7 +274,11 @@ int launch_tile(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const f
   const hot::StepArgs a = make_step_args(c, k, phi, G, grad);
   const int smem = hot::step_smem_bytes(c->M, BACK);
   Probe p(c, BACK && FWD ? HOT_KERNEL_STEP : FWD ? HOT_KERNEL_FORWARD : HOT_KERNEL_OTHER);
-  launch(c, hot::gsw_step_kernel<FAST, BACK, FWD, ADJ>, c->grid, hot::kThreads, smem, pdl, a);
+  if (BACK && FWD && !ADJ && c->groups == hot::kMaxGroups)  // the GSW step: one block per SM
+    launch(c, hot::gsw_step_kernel<FAST, true, true, false, hot::kMaxGroups>, c->grid / hot::kMaxGroups,
+           hot::kThreads * hot::kMaxGroups, smem * hot::kMaxGroups, pdl, a);
+  else
+    launch(c, hot::gsw_step_kernel<FAST, BACK, FWD, ADJ>, c->grid, hot::kThreads, smem, pdl, a);
   return check_launch(c, "gsw_step_kernel");
 }
 
@@ -303,6 +312,9 @@ int set_step_smem(int M) {
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd));
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
+  constexpr int G4 = hot::kMaxGroups;
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, true, true, false, G4>, cudaFuncAttributeMaxDynamicSharedMemorySize, G4 * back));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, true, true, false, G4>, cudaFuncAttributeMaxDynamicSharedMemorySize, G4 * back));
   const int sep = hot::sep_smem_bytes(hot::kChunk);
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_sep_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sep));
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_sep_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sep));
@@ -347,9 +359,22 @@ int build_schedule(hot_ctx *c) {
   c->sched_bps_max = per_sm;
   if (c->tile_bps > 0 && c->tile_bps < per_sm) per_sm = c->tile_bps;
   c->sched_bps = per_sm;
+  // Merged (hot_set_block_merge), with four schedule blocks per SM the direct modes' GSW step
+  // runs one block per SM holding four of them (see gsw_step_kernel), if such a block fits.
+  c->groups = 1;
+  if (c->tile_merge && !separable_kernels(c) && per_sm == hot::kMaxGroups) {
+    int per_sm_g = 0;
+    HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm_g, hot::gsw_step_kernel<true, true, true, false, hot::kMaxGroups>, hot::kThreads * hot::kMaxGroups,
+        hot::kMaxGroups * hot::step_smem_bytes(c->M, true)));
+    if (per_sm_g >= 1) c->groups = hot::kMaxGroups;
+  }
   const int strips = (c->W + hot::kTileW - 1) / hot::kTileW;
   const long long U = (long long)strips * c->H;
-  const int G = (int)std::min<long long>((long long)sms * per_sm, U);
+  int G = (int)std::min<long long>((long long)sms * per_sm, U);
+  // whole merged blocks; rounded the same way unmerged, so that merging never changes the schedule
+  // (and with it the bits of the results)
+  if (!separable_kernels(c) && per_sm == hot::kMaxGroups) G = (G + hot::kMaxGroups - 1) / hot::kMaxGroups * hot::kMaxGroups;
   std::vector<hot::SubTile> sub;
   std::vector<int> first(G + 1);
   for (int b = 0; b < G; b++) {
@@ -886,6 +911,38 @@ int hot_field_adjoint(hot_ctx *c, const float *phi, const float *G, float *grad)
   return launch_mode<true, false, true>(c, false, 0, phi, g, grad);
 }
 
+int hot_intensity_loss(hot_ctx *c, const float *phi, double beta, float *loss, float *grad) {
+  if (!c || !phi || !loss) return fail(HOT_EINVAL, "hot_intensity_loss: NULL argument");
+  if (!c->M) return fail(HOT_ESTATE, "hot_intensity_loss: no traps set");
+  if (!std::isfinite(beta)) return fail(HOT_EINVAL, "hot_intensity_loss: beta not finite");
+  if (!c->G) {
+    const int rc = dalloc(&c->G, c->M);
+    if (rc != HOT_OK) return rc;
+  }
+  int rc = launch_mode<false, true>(c, false, 0, phi);  // sums of V = F(phi) in accumulator 0
+  if (rc != HOT_OK) return rc;
+  hot::LossArgs a = {};
+  a.M = c->M;
+  a.copies = acc_copies(c);
+  a.acc = c->acc;
+  a.acc_all = c->acc;
+  a.Vsum = c->Vsum;
+  a.metrics = c->metrics;
+  a.inv_fx_n = 1.0 / (n_total(c) * ldexp(1.0, c->fx_shift));
+  a.beta = beta;
+  a.G = c->G;
+  a.loss = loss;
+  {
+    Probe p(c, HOT_KERNEL_FINISH);
+    hot::intensity_loss_kernel<<<1, hot::kLossThreads, 0, c->st>>>(a);
+  }
+  rc = check_launch(c, "intensity_loss_kernel");
+  if (rc != HOT_OK) return rc;
+  c->have_fields = true;
+  if (!grad) return HOT_OK;
+  return launch_mode<true, false, true>(c, false, 0, phi, c->G, grad);
+}
+
 int hot_set_band(hot_ctx *c, int total_height, int y0) {
   if (!c) return fail(HOT_EINVAL, "hot_set_band: NULL context");
   if (total_height < c->H || y0 < 0 || y0 > total_height - c->H || (long long)c->W * total_height >= (1LL << 31))
@@ -1105,6 +1162,13 @@ struct hot_batch {
   std::vector<Group> groups;
   unsigned long long *stamps = nullptr;  // [count + 1]: completion of hologram h; [count]: start
   bool ran = false;
+  // HOT_PREC_TENSOR: each member runs its own hot_gsw launch sequence; the members are dealt out
+  // to up to kTensorChains streams (largest work first, each to the least loaded chain) whose
+  // launches overlap, forked from and joined to the batch's stream inside its graph
+  std::vector<std::vector<int>> chains;
+  std::vector<cudaStream_t> chain_st;
+  std::vector<cudaEvent_t> chain_ev;  // [0]: fork; [1 + i]: end of chain i
+
   struct Graph {
     int iters;
     cudaGraphExec_t exec;
@@ -1173,6 +1237,10 @@ void batch_free(hot_batch *b) {
   dfree(b->stamps);
   if (b->cap) cudaStreamDestroy(b->cap);
   b->cap = nullptr;
+  for (cudaStream_t s : b->chain_st) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->chain_ev) cudaEventDestroy(e);
+  b->chain_st.clear();
+  b->chain_ev.clear();
 }
 
 // Step-kernel parameters of context c for launch k of a sequence (buffers rotate as in hot_gsw).
@@ -1198,6 +1266,7 @@ hot::StepArgs step_args(const hot_ctx *c, int k, int chunk) {
   a.fx_scale = ldexpf(1.0f, c->fx_shift);
   a.inv_fx_n = (float)(1.0 / (n_total(c) * ldexp(1.0, c->fx_shift)));
   a.angle_units = fast ? 1.0f : 0.15915494309189535f;
+  a.angle_eta = fast ? hot::kFastEta : 0.0f;
   a.inv_n = (float)(1.0 / (n_total(c)));
   return a;
 }
@@ -1359,7 +1428,62 @@ int batch_launch_mode(hot_batch *b, const hot_batch::Group &g, int k, bool pdl) 
   }
 }
 
+constexpr int kTensorChains = 8;
+
+// Tensor-mode batch set-up: every member's tensor-core operands, and its chain (largest work
+// N M first, each to the chain with the least work so far).
+int batch_setup_tensor(hot_batch *b) {
+  for (hot_ctx *c : b->ctx) {
+    const int rc = ensure_tc_plan(c);
+    if (rc != HOT_OK) return rc;
+    HOT_CUDA(cudaStreamSynchronize(c->st));
+  }
+  const int n = std::min(b->count, kTensorChains);
+  std::vector<int> order(b->count);
+  for (int h = 0; h < b->count; h++) order[h] = h;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return pairs_of(b->ctx[x]) > pairs_of(b->ctx[y]); });
+  std::vector<double> load(n, 0.0);
+  b->chains.assign(n, {});
+  for (int h : order) {
+    const int i = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->chains[i].push_back(h);
+    load[i] += pairs_of(b->ctx[h]);
+  }
+  b->chain_st.assign(n, nullptr);
+  b->chain_ev.assign(n + 1, nullptr);
+  for (int i = 0; i < n; i++) HOT_CUDA(cudaStreamCreateWithFlags(&b->chain_st[i], cudaStreamNonBlocking));
+  for (int i = 0; i <= n; i++) HOT_CUDA(cudaEventCreateWithFlags(&b->chain_ev[i], cudaEventDisableTiming));
+  return HOT_OK;
+}
+
+// Tensor-mode batch: a start stamp, then every chain on its own stream (forked from the batch's
+// stream by an event), each member's hot_gsw sequence followed by its completion stamp, and the
+// chains joined back.  Each member computes exactly what hot_gsw(iters) computes for it.
+int batch_enqueue_tensor(hot_batch *b, int iters) {
+  hot::stamp_kernel<<<1, 1, 0, b->st>>>(b->stamps + b->count);
+  HOT_CUDA(cudaGetLastError());
+  HOT_CUDA(cudaEventRecord(b->chain_ev[0], b->st));
+  for (size_t i = 0; i < b->chains.size(); i++) {
+    cudaStream_t s = b->chain_st[i];
+    HOT_CUDA(cudaStreamWaitEvent(s, b->chain_ev[0], 0));
+    for (int h : b->chains[i]) {
+      hot_ctx *c = b->ctx[h];
+      cudaStream_t own = c->st;
+      c->st = s;
+      const int rc = enqueue_gsw(c, iters);
+      c->st = own;
+      if (rc != HOT_OK) return rc;
+      hot::stamp_kernel<<<1, 1, 0, s>>>(b->stamps + h);
+      HOT_CUDA(cudaGetLastError());
+    }
+    HOT_CUDA(cudaEventRecord(b->chain_ev[1 + i], s));
+    HOT_CUDA(cudaStreamWaitEvent(b->st, b->chain_ev[1 + i], 0));
+  }
+  return HOT_OK;
+}
+
 int batch_enqueue(hot_batch *b, int iters) {
+  if (b->precision == HOT_PREC_TENSOR) return batch_enqueue_tensor(b, iters);
   hot::stamp_kernel<<<1, 1, 0, b->st>>>(b->stamps + b->count);
   cudaError_t e0 = cudaGetLastError();
   if (e0 != cudaSuccess) return fail(HOT_ECUDA, "launch of stamp_kernel: %s", cudaGetErrorString(e0));
@@ -1386,8 +1510,10 @@ int check_tiling(const char *who, int rows, int bps, int chunk) {
 }
 
 struct Tiling {
-  int rows, bps, chunk;
-  bool operator==(const Tiling &o) const { return rows == o.rows && bps == o.bps && chunk == o.chunk; }
+  int rows, bps, chunk, merge;
+  bool operator==(const Tiling &o) const {
+    return rows == o.rows && bps == o.bps && chunk == o.chunk && merge == o.merge;
+  }
 };
 
 // The kernels are launch-bounded to at most 4 resident blocks per SM; a candidate above what
@@ -1397,8 +1523,9 @@ constexpr int kMaxBlocksPerSm = 4;
 // Coordinate search: each parameter in turn takes the fastest of its candidates with the
 // others fixed; a candidate replaces the incumbent only if it is more than 1 % faster; at
 // most two passes.  apply(t) installs a tiling, time(&us) measures it.  Leaves `best` applied.
+// With merge, the blocks-per-SM candidates include max_bps blocks merged into one (Tiling::merge).
 template <typename Apply, typename Time>
-int tune_tiling(int max_bps, Tiling &best, double &best_us, Apply apply, Time time) {
+int tune_tiling(int max_bps, Tiling &best, double &best_us, Apply apply, Time time, bool merge = false) {
   static const int rows_c[] = {14, 12, 10, 8, 6, 4, 2};
   static const int chunk_c[] = {128, 96, 64, 32};
   int rc = apply(best);
@@ -1406,14 +1533,21 @@ int tune_tiling(int max_bps, Tiling &best, double &best_us, Apply apply, Time ti
   for (int pass = 0; rc == HOT_OK && pass < 2; pass++) {
     bool changed = false;
     for (int dim = 0; rc == HOT_OK && dim < 3; dim++) {
-      std::vector<int> cand;
+      std::vector<int> cand;  // blocks per SM: -v stands for v blocks merged
       if (dim == 0) cand.assign(std::begin(rows_c), std::end(rows_c));
-      if (dim == 1)
+      if (dim == 1) {
+        if (merge) cand.push_back(-max_bps);
         for (int v = max_bps; v >= 1; v--) cand.push_back(v);
+      }
       if (dim == 2) cand.assign(std::begin(chunk_c), std::end(chunk_c));
       for (int v : cand) {
         Tiling t = best;
-        (dim == 0 ? t.rows : dim == 1 ? t.bps : t.chunk) = v;
+        if (dim == 1) {
+          t.bps = v < 0 ? -v : v;
+          t.merge = v < 0;
+        } else {
+          (dim == 0 ? t.rows : t.chunk) = v;
+        }
         if (t == best) continue;
         double us = 0;
         rc = apply(t);
@@ -1512,6 +1646,22 @@ int hot_get_tiling(const hot_ctx *c, int *rows, int *blocks_per_sm, int *chunk) 
   return HOT_OK;
 }
 
+int hot_set_block_merge(hot_ctx *c, int merge) {
+  if (!c) return fail(HOT_EINVAL, "hot_set_block_merge: NULL context");
+  if (merge != 0 && merge != 1) return fail(HOT_EINVAL, "hot_set_block_merge: merge = %d is not 0 or 1", merge);
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  c->tile_merge = merge;
+  drop_graphs(c);
+  return c->M ? build_schedule(c) : HOT_OK;
+}
+
+int hot_get_block_merge(const hot_ctx *c, int *requested, int *in_effect) {
+  if (!c) return fail(HOT_EINVAL, "hot_get_block_merge: NULL context");
+  if (requested) *requested = c->tile_merge;
+  if (in_effect) *in_effect = c->groups > 1;
+  return HOT_OK;
+}
+
 int hot_autotune(hot_ctx *c, int iters, int *rows, int *blocks_per_sm, int *chunk, double *us_per_iter) {
   if (!c) return fail(HOT_EINVAL, "hot_autotune: NULL context");
   if (!c->M) return fail(HOT_ESTATE, "hot_autotune: no traps set");
@@ -1523,15 +1673,19 @@ int hot_autotune(hot_ctx *c, int iters, int *rows, int *blocks_per_sm, int *chun
   if (rc != HOT_OK) return rc;
   const bool profiling = c->profiling;
   c->profiling = false;
-  Tiling best = {c->tile_rows, c->sched_bps, c->tile_chunk};
+  Tiling best = {c->tile_rows, c->sched_bps, c->tile_chunk, c->tile_merge};
   double best_us = 0;
   rc = tune_tiling(
       kMaxBlocksPerSm, best, best_us,
-      [&](const Tiling &t) { return hot_set_tiling(c, t.rows, t.bps, t.chunk); },
+      [&](const Tiling &t) {
+        c->tile_merge = t.merge;  // applied by the schedule that hot_set_tiling rebuilds
+        return hot_set_tiling(c, t.rows, t.bps, t.chunk);
+      },
       [&](double *us) {
         return time_runs(c->st, iters, us, [&]() { return restore_state(c, saved, c->st); },
                          [&]() { return hot_gsw(c, iters, nullptr, nullptr); });
-      });
+      },
+      !separable_kernels(c));
   c->profiling = profiling;
   const int rc2 = restore_state(c, saved, c->st);
   cudaStreamSynchronize(c->st);
@@ -1554,8 +1708,6 @@ int hot_batch_create(hot_batch **out, int count, hot_ctx *const *ctxs, void *cud
     if (!ctxs[i]->M) return fail(HOT_ESTATE, "hot_batch_create: context %d has no traps", i);
     if (ctxs[i]->precision != ctxs[0]->precision)
       return fail(HOT_EINVAL, "hot_batch_create: contexts differ in precision mode");
-    if (ctxs[i]->precision == HOT_PREC_TENSOR)
-      return fail(HOT_EINVAL, "hot_batch_create: batches run the direct or separable kernels, not HOT_PREC_TENSOR");
     if (ctxs[i]->H_total != ctxs[i]->H)
       return fail(HOT_EINVAL, "hot_batch_create: context %d is a row band (its sums need an exchange)", i);
     if (ctxs[i]->dev != ctxs[0]->dev) return fail(HOT_EINVAL, "hot_batch_create: contexts on different devices");
@@ -1569,13 +1721,15 @@ int hot_batch_create(hot_batch **out, int count, hot_ctx *const *ctxs, void *cud
   b->st = static_cast<cudaStream_t>(cuda_stream);
   b->precision = ctxs[0]->precision;
   b->dev = ctxs[0]->dev;
-  int rc = batch_mode(b) == hot::kModeSeparable ? batch_set_smem<hot::kModeSeparable>()
-           : batch_mode(b) == hot::kModeFast    ? batch_set_smem<hot::kModeFast>()
-                                                : batch_set_smem<hot::kModeAccurate>();
+  const bool tensor = b->precision == HOT_PREC_TENSOR;
+  int rc = tensor                                     ? HOT_OK
+           : batch_mode(b) == hot::kModeSeparable ? batch_set_smem<hot::kModeSeparable>()
+           : batch_mode(b) == hot::kModeFast      ? batch_set_smem<hot::kModeFast>()
+                                                  : batch_set_smem<hot::kModeAccurate>();
   if (rc == HOT_OK && cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev) != cudaSuccess)
     rc = fail(HOT_ECUDA, "hot_batch_create: device query failed");
   if (rc == HOT_OK) rc = dalloc(&b->stamps, (size_t)count + 1);
-  if (rc == HOT_OK) rc = batch_schedule(b);
+  if (rc == HOT_OK) rc = tensor ? batch_setup_tensor(b) : batch_schedule(b);
   if (rc != HOT_OK) {
     batch_free(b);
     delete b;
@@ -1587,6 +1741,7 @@ int hot_batch_create(hot_batch **out, int count, hot_ctx *const *ctxs, void *cud
 
 int hot_batch_set_tiling(hot_batch *b, int rows, int blocks_per_sm, int chunk, double group_pairs) {
   if (!b) return fail(HOT_EINVAL, "hot_batch_set_tiling: NULL batch");
+  if (b->precision == HOT_PREC_TENSOR) return fail(HOT_EINVAL, "hot_batch_set_tiling: a HOT_PREC_TENSOR batch has no tiling");
   int rc = check_tiling("hot_batch_set_tiling", rows, blocks_per_sm, chunk);
   if (rc != HOT_OK) return rc;
   if (!(group_pairs >= 0) || !std::isfinite(group_pairs))
@@ -1605,7 +1760,7 @@ int hot_batch_get_tiling(const hot_batch *b, int *rows, int *blocks_per_sm, int 
   if (blocks_per_sm) *blocks_per_sm = b->bps > 0 ? std::min(b->bps, b->per_sm_max) : b->per_sm_max;
   if (chunk) *chunk = b->chunk;
   if (group_pairs) *group_pairs = b->group_pairs;
-  if (groups) *groups = (int)b->groups.size();
+  if (groups) *groups = (int)(b->precision == HOT_PREC_TENSOR ? b->chains.size() : b->groups.size());
   return HOT_OK;
 }
 
@@ -1649,6 +1804,7 @@ int hot_batch_gsw(hot_batch *b, int iters) {
 
 int hot_batch_autotune(hot_batch *b, int iters, int *rows, int *blocks_per_sm, int *chunk, double *us_per_iter) {
   if (!b) return fail(HOT_EINVAL, "hot_batch_autotune: NULL batch");
+  if (b->precision == HOT_PREC_TENSOR) return fail(HOT_EINVAL, "hot_batch_autotune: a HOT_PREC_TENSOR batch has no tiling");
   if (iters < 1) return fail(HOT_EINVAL, "hot_batch_autotune: iters = %d < 1", iters);
   std::vector<Saved> saved(b->count);
   int rc = HOT_OK;
@@ -1661,7 +1817,7 @@ int hot_batch_autotune(hot_batch *b, int iters, int *rows, int *blocks_per_sm, i
     }
     return (int)HOT_OK;
   };
-  Tiling best = {b->rows, b->bps > 0 ? std::min(b->bps, b->per_sm_max) : b->per_sm_max, b->chunk};
+  Tiling best = {b->rows, b->bps > 0 ? std::min(b->bps, b->per_sm_max) : b->per_sm_max, b->chunk, 0};
   double best_us = 0;
   const double gp = b->group_pairs;
   rc = tune_tiling(
@@ -1812,21 +1968,41 @@ namespace {
 __device__ __align__(256) unsigned char g_noalloc_scratch[HOT_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kNoallocMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-unsigned char *g_noalloc_base[kNoallocMaxDevices];  // device address per device, or NULL
 
-// Device address of the scratch array on the current device (looked up on first use).
-int noalloc_scratch(int dev, unsigned char **out) {
+// What the first call on a device sets up: the scratch array's device address, the
+// step kernels' shared-memory limit and the resident blocks per SM of the work schedule.
+struct NoallocDevice {
+  unsigned char *base;  // NULL until set up
+  int sms, per_sm;
+};
+std::mutex g_noalloc_mutex;
+NoallocDevice g_noalloc_dev[kNoallocMaxDevices];
+
+// Set-up of device dev (the current device), once: the device address of the scratch array
+// (in host code its name is a host-side stand-in, not a device address), the dynamic
+// shared-memory limit of the forward-field kernels and the occupancy that sizes the grid
+// (the same per-SM block count a context's schedule uses; it does not depend on M).
+int noalloc_device(int dev, NoallocDevice *out) {
   if (dev < 0 || dev >= kNoallocMaxDevices) return fail(HOT_EINVAL, "hot_field_noalloc: device %d beyond %d", dev, kNoallocMaxDevices);
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_base[dev]) {
+  NoallocDevice &d = g_noalloc_dev[dev];
+  if (!d.base) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
       return fail(HOT_ECUDA, "hot_field_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-    g_noalloc_base[dev] = static_cast<unsigned char *>(p);
+    const int fwd = hot::step_smem_bytes(1, false), step = hot::step_smem_bytes(1, true);
+    HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd));
+    HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd));
+    HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, step));
+    int sms = 0, per_sm = 0;
+    HOT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_step_kernel<true, true, true>, hot::kThreads, step));
+    d.sms = sms;
+    d.per_sm = per_sm < 1 ? 1 : per_sm;
+    d.base = static_cast<unsigned char *>(p);
   }
-  *out = g_noalloc_base[dev];
+  *out = d;
   return HOT_OK;
 }
 
@@ -1905,22 +2081,14 @@ extern "C" int hot_field_noalloc(int width, int height, double pitch_m, double w
   const bool fast = precision == HOT_PREC_FAST;
   int dev = 0;
   HOT_CUDA(cudaGetDevice(&dev));
+  NoallocDevice d = {};
+  int rc = noalloc_device(dev, &d);
+  if (rc != HOT_OK) return rc;
 
   // Work schedule: identical to a context's (one wave of step-kernel blocks).
-  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                hot::step_smem_bytes(M, false)));
-  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                hot::step_smem_bytes(M, false)));
-  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                hot::step_smem_bytes(M, true)));
-  int sms = 0, per_sm = 0;
-  HOT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hot::gsw_step_kernel<true, true, true>,
-                                                         hot::kThreads, hot::step_smem_bytes(M, true)));
-  if (per_sm < 1) per_sm = 1;
   const int strips = (width + hot::kTileW - 1) / hot::kTileW;
   const long long U = (long long)strips * height;
-  const int G = (int)std::min<long long>((long long)sms * per_sm, U);
+  const int G = (int)std::min<long long>((long long)d.sms * d.per_sm, U);
   int n_sub = 0;
   for (int b = 0; b < G; b++) n_sub += noalloc_block_subtiles(U, G, height, b, nullptr);
 
@@ -1932,13 +2100,11 @@ extern "C" int hot_field_noalloc(int width, int height, double pitch_m, double w
   const size_t o_yt = take(sizeof(float) * (size_t)M * height), o_yr = take(sizeof(float) * (size_t)M * height);
   const size_t o_sub = take(sizeof(hot::SubTile) * n_sub), o_first = take(sizeof(int) * (G + 1));
   const size_t o_acc = take(sizeof(unsigned long long) * 6 * M), o_vsum = take(sizeof(long long) * 2 * M);
-  const size_t o_w = take(sizeof(float) * M), o_met = take(sizeof(float) * 2);
+  const size_t o_met = take(sizeof(float) * 2);
   if (off > HOT_NOALLOC_SCRATCH_BYTES)
     return fail(HOT_EINVAL, "hot_field_noalloc: %d x %d pixels and %d traps need %zu bytes of scratch, the limit is %u",
                 width, height, M, off, (unsigned)HOT_NOALLOC_SCRATCH_BYTES);
-  unsigned char *base = nullptr;
-  int rc = noalloc_scratch(dev, &base);
-  if (rc != HOT_OK) return rc;
+  unsigned char *const base = d.base;
   double *abc = reinterpret_cast<double *>(base + o_abc);
   float *Xt = reinterpret_cast<float *>(base + o_xt), *Xr = reinterpret_cast<float *>(base + o_xr);
   float *Yt = reinterpret_cast<float *>(base + o_yt), *Yr = reinterpret_cast<float *>(base + o_yr);
@@ -1946,7 +2112,6 @@ extern "C" int hot_field_noalloc(int width, int height, double pitch_m, double w
   int *d_first = reinterpret_cast<int *>(base + o_first);
   unsigned long long *acc = reinterpret_cast<unsigned long long *>(base + o_acc);
   long long *Vsum = reinterpret_cast<long long *>(base + o_vsum);
-  float *w = reinterpret_cast<float *>(base + o_w);
   float *metrics = reinterpret_cast<float *>(base + o_met);
 
   // The schedule is written on the device; the accumulators start at zero (the array keeps
@@ -1967,7 +2132,7 @@ extern "C" int hot_field_noalloc(int width, int height, double pitch_m, double w
   int bits = 0;
   while ((1LL << bits) < (long long)width * height) bits++;
   const int fx_shift = 61 - bits;
-  hot::StepArgs a;
+  hot::StepArgs a = {};  // the forward-only kernel reads no weights, coefficients or separable tables
   a.W = width;
   a.H = height;
   a.M = M;
@@ -1981,22 +2146,19 @@ extern "C" int hot_field_noalloc(int width, int height, double pitch_m, double w
   a.acc_in = acc + 4 * (size_t)M;
   a.acc_out = acc;
   a.acc_clear = acc + 2 * (size_t)M;
-  a.w_in = w;
-  a.w_out = w;
   a.fx_scale = ldexpf(1.0f, fx_shift);
   a.inv_fx_n = (float)(1.0 / ((double)width * (double)height * ldexp(1.0, fx_shift)));
   a.angle_units = fast ? 1.0f : 0.15915494309189535f;
+  a.angle_eta = fast ? hot::kFastEta : 0.0f;
   const int smem = hot::step_smem_bytes(M, false);
   if (fast) hot::gsw_step_kernel<true, false, true><<<G, hot::kThreads, smem, st>>>(a);
   else hot::gsw_step_kernel<false, false, true><<<G, hot::kThreads, smem, st>>>(a);
   HOT_CUDA(cudaGetLastError());
-  hot::FinalizeArgs f;
+  hot::FinalizeArgs f = {};  // no weights to move (w_src = w_dst = NULL), no completion stamp
   f.M = M;
   f.copies = 1;
   f.acc = acc;
   f.acc_all = acc;
-  f.w_src = w;
-  f.w_dst = w;
   f.Vsum = Vsum;
   f.metrics = metrics;
   f.inv_fx_n = a.inv_fx_n;

@@ -60,10 +60,13 @@ SIGNATURES = {
     "hot_sharded_sums": (_c_int, [_vp, _c_int, ctypes.POINTER(_vp), _ip]),
     "hot_sharded_end": (_c_int, [_vp, _c_int, _dp, _dp]),
     "hot_get_tiling": (_c_int, [_vp, _ip, _ip, _ip]),
+    "hot_set_block_merge": (_c_int, [_vp, _c_int]),
+    "hot_get_block_merge": (_c_int, [_vp, _ip, _ip]),
     "hot_autotune": (_c_int, [_vp, _c_int, _ip, _ip, _ip, _dp]),
     "hot_field": (_c_int, [_vp, _vp, _vp]),
     "hot_superposition": (_c_int, [_vp, _vp]),
     "hot_field_adjoint": (_c_int, [_vp, _vp, _vp, _vp]),
+    "hot_intensity_loss": (_c_int, [_vp, _vp, _c_double, _vp, _vp]),
     "hot_kernel_launches": (ctypes.c_longlong, [_vp]),
     "hot_use_graphs": (_c_int, [_vp, _c_int]),
     "hot_use_persistent": (_c_int, [_vp, _c_int]),
@@ -200,6 +203,13 @@ def hot_field_adjoint(ctx: int, phi_dev, G_dev, grad_dev) -> None:
                               _vp(grad_dev.data_ptr())), "hot_field_adjoint")
 
 
+def hot_intensity_loss(ctx: int, phi_dev, beta: float, loss_dev, grad_dev=None) -> None:
+    """Loss -sum log I + beta var(I) of the traps' intensities for device phases phi_dev, into
+    loss_dev (1 float32), and its gradient into grad_dev (N float32) unless None.  Queued."""
+    _ok(lib.hot_intensity_loss(_vp(ctx), _vp(phi_dev.data_ptr()), float(beta), _vp(loss_dev.data_ptr()),
+                               _vp(grad_dev.data_ptr() if grad_dev is not None else 0)), "hot_intensity_loss")
+
+
 def hot_get_metrics(ctx: int):
     e, u = ctypes.c_double(), ctypes.c_double()
     _ok(lib.hot_get_metrics(_vp(ctx), ctypes.byref(e), ctypes.byref(u)), "hot_get_metrics")
@@ -257,11 +267,22 @@ def hot_get_tiling(ctx: int) -> dict:
     return {"rows": r.value, "blocks_per_sm": b.value, "chunk": c.value}
 
 
+def hot_set_block_merge(ctx: int, merge: bool) -> None:
+    _ok(lib.hot_set_block_merge(_vp(ctx), int(bool(merge))), "hot_set_block_merge")
+
+
+def hot_get_block_merge(ctx: int) -> dict:
+    req, eff = _c_int(), _c_int()
+    _ok(lib.hot_get_block_merge(_vp(ctx), ctypes.byref(req), ctypes.byref(eff)), "hot_get_block_merge")
+    return {"requested": bool(req.value), "in_effect": bool(eff.value)}
+
+
 def hot_autotune(ctx: int, iters: int) -> dict:
     r, b, c, us = _c_int(), _c_int(), _c_int(), ctypes.c_double()
     _ok(lib.hot_autotune(_vp(ctx), int(iters), ctypes.byref(r), ctypes.byref(b), ctypes.byref(c),
                          ctypes.byref(us)), "hot_autotune")
-    return {"rows": r.value, "blocks_per_sm": b.value, "chunk": c.value, "us_per_iter": us.value}
+    return {"rows": r.value, "blocks_per_sm": b.value, "chunk": c.value, "us_per_iter": us.value,
+            "merge": hot_get_block_merge(ctx)["in_effect"]}
 
 
 def hot_batch_set_tiling(batch: int, rows: int = 0, blocks_per_sm: int = 0, chunk: int = 0,
@@ -507,6 +528,9 @@ class Hologram:
     def set_tiling(self, rows: int = 0, blocks_per_sm: int = 0, chunk: int = 0):
         hot_set_tiling(self.ctx, rows, blocks_per_sm, chunk)
 
+    def set_block_merge(self, merge: bool = True):
+        hot_set_block_merge(self.ctx, merge)
+
     def use_persistent(self, enable: bool = True):
         hot_use_persistent(self.ctx, enable)
 
@@ -548,7 +572,7 @@ class Hologram:
         return hot_sharded_end(self.ctx, iters)
 
     def tiling(self) -> dict:
-        return hot_get_tiling(self.ctx)
+        return dict(hot_get_tiling(self.ctx), merge=hot_get_block_merge(self.ctx)["in_effect"])
 
     def autotune(self, iters: int) -> dict:
         """Picks the fastest tiling for hot_gsw(iters); phases and weights are kept."""

@@ -139,3 +139,33 @@ def test_adam_improves_uniformity(env):
             losses.append(L.item())
             us.append(float(1 - (I.max() - I.min()) / (I.max() + I.min())))
     assert losses[-1] < losses[0] and us[-1] > us[0] + 0.2, (losses[0], losses[-1], us[0], us[-1])
+
+
+@pytest.mark.parametrize("precision", ["accurate", "fast", "separable"])
+def test_library_loss_and_gradient_match_oracle(env, precision):
+    """hot_intensity_loss: the loss -sum log I + 10 var(I) and its gradient from one library call,
+    against the FP64 oracle's loss and gradient (forward field, the derivative of the loss, the
+    adjoint), and the autograd Function built on it against the PyTorch-loss path."""
+    torch, hot, ag = env
+    w = wl.random_case(96, 80, 12, seed=9, precision=precision)
+    with holo_for(hot, torch, w) as h:
+        phi = torch.tensor(w.phi0, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        grad = torch.empty_like(phi)
+        hot.hot_intensity_loss(h.ctx, phi, 10.0, loss, grad)
+        L = float(loss.item())
+        g = grad.cpu().numpy().astype(np.float64)
+        p1 = phi.clone().requires_grad_(True)
+        ag.intensity_loss(h, p1).backward()
+        p2 = phi.clone().requires_grad_(True)
+        ag.trap_intensity_loss(ag.trap_fields(h, p2)).backward()
+        g1, g2 = p1.grad.cpu().numpy(), p2.grad.cpu().numpy()
+        hot.hot_intensity_loss(h.ctx, phi, 10.0, loss)           # the loss alone
+        assert float(loss.item()) == L
+    phi64 = w.phi0.astype(np.float32).astype(np.float64)
+    oV = oracle.forward(w.geom, w.xyz, phi64)
+    og = oracle.adjoint(w.geom, w.xyz, phi64, oracle_loss_G(oV))
+    assert abs(L - loss_value(oV)) < 1e-4 * abs(loss_value(oV))
+    assert np.linalg.norm(g - og) < 1e-3 * np.linalg.norm(og)
+    assert np.array_equal(g1, g.astype(np.float32))
+    assert np.linalg.norm(g1 - g2) < 1e-3 * np.linalg.norm(g2)

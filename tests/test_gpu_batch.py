@@ -155,7 +155,7 @@ def test_autotune_keeps_state(hot):
         t = h.autotune(4)
         assert 1 <= t["rows"] <= 14 and 1 <= t["blocks_per_sm"] <= 4 and 1 <= t["chunk"] <= 128
         assert t["us_per_iter"] > 0
-        assert h.tiling() == {k: t[k] for k in ("rows", "blocks_per_sm", "chunk")}
+        assert h.tiling() == {k: t[k] for k in ("rows", "blocks_per_sm", "chunk", "merge")}
         assert np.array_equal(h.phase("f32"), phi_before)
         with pytest.raises(hot.HotError, match="HOT_ESTATE"):
             h.fields()
@@ -194,3 +194,34 @@ def test_row_bands_are_not_batched(hot):
         h.set_traps(w.xyz)
         with pytest.raises(hot.HotError, match="HOT_EINVAL"):
             hot.Batch([h]).close()
+
+
+@pytest.mark.slow
+def test_largest_batch64_member_fast(hot):
+    """The largest hologram of the batch64 workload (1920 x 1152 px, 1818 traps; fast mode) run
+    through hot_batch_gsw beside a small one: the fields of the GPU's final phase against the
+    oracle forward on a seeded 64-trap subset, and one step from the GPU's state (its fields and
+    weights, Sec. 3 update and Sec. 4 back-projection in FP64) on that subset, after 3 iterations;
+    e and u against the oracle forward of the GPU's final phase (all traps)."""
+    big = max(wl.batch64(), key=lambda w: w.N * w.M)
+    assert (big.W, big.H, big.M) == (1920, 1152, 1818)
+    small = wl.random_case(100, 37, 13, seed=1, precision="fast")
+    holos = [hot.Hologram.from_workload(w) for w in (big, small)]
+    try:
+        with hot.Batch(holos) as b:
+            b.gsw(2)
+            VK, wK1 = holos[0].fields()
+            b.gsw(1)
+            VK1, _ = holos[0].fields()
+            e, u = holos[0].metrics()
+            phiK = holos[0].phase("f32")
+    finally:
+        for h in holos:
+            h.close()
+    sub = np.sort(np.random.default_rng(0).choice(big.M, 64, replace=False))
+    assert rel_err(VK1[sub], oracle.forward(big.geom, big.xyz[sub], phiK)) < REL_V
+    _, coef = oracle.update_weights(VK, wK1)
+    ophi = oracle.backproject(big.geom, big.xyz, coef)
+    assert rel_err(VK1[sub], oracle.forward(big.geom, big.xyz[sub], ophi)) < REL_V
+    oe, ou = oracle.metrics(oracle.forward(big.geom, big.xyz, phiK))
+    assert abs(e - oe) < ABS_EU and abs(u - ou) < ABS_EU

@@ -20,6 +20,9 @@ pytestmark = pytest.mark.gpu
 REL_V = 1e-4
 ABS_EU = 1e-3
 TOL_S = {"accurate": 2e-6, "fast": 2e-5, "separable": 4e-6, "tensor": 4e-6}
+# The stated limits of HOT_PREC_FAST and HOT_PREC_TENSOR on strongly cancelling
+# back-projections (include/hot.h)
+ILLCOND_REL_V = {"fast": 2e-4, "tensor": 5e-4}
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
@@ -194,11 +197,14 @@ def test_full_workload_matches_oracle(hot, name, precision):
 
 
 @pytest.mark.slow
-def test_rand1000_1920_metrics_and_trap_subset(hot):
-    """1920 x 1152, 1000 traps, 50 iterations: the full-run e and u against the stored oracle
-    run (tests/golden), the fields of the GPU's final phase against the oracle forward (all
-    traps), and one step from the GPU's state on a seeded 64-trap subset of V."""
+@pytest.mark.parametrize("precision", ["accurate", "fast"])
+def test_rand1000_1920_metrics_and_trap_subset(hot, precision):
+    """1920 x 1152, 1000 traps, 50 iterations, in the accurate and the fast mode: the full-run e
+    and u against the stored oracle run (tests/golden), the fields of the GPU's final phase
+    against the oracle forward on a seeded 64-trap subset, and one step from the GPU's state on
+    that subset."""
     w = wl.rand1000_1920()
+    w.precision = precision
     K = w.iters
     with make(hot, w) as h:
         h.gsw(K - 1, metrics=False)
@@ -355,15 +361,17 @@ def test_checkpoint_resume_across_contexts(hot):
     assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1][0], got[1][0]) and np.array_equal(ref[1][1], got[1][1])
 
 
-@pytest.mark.parametrize("precision", ["accurate", "separable"])
+@pytest.mark.parametrize("precision", ["accurate", "fast", "separable", "tensor"])
 def test_maximum_trap_count(hot, precision):
     """HOT_MAX_TRAPS (4096) traps on a small SLM: 32 staged trap chunks per sub-tile; M + 1 traps
-    are rejected.  (The first weight update here spreads the weights over a factor of ~400, so
-    the back-projection cancels strongly at some pixels; the fast mode's 5e-7 sincos error is then
-    amplified past the 1e-4 bound on |V_m|, as the conditioning-aware phase bound predicts, and the
-    case is run in the two modes whose per-term error is ~1e-7.  The tensor mode gives 3.2e-4 here:
-    the tensor core's accumulation truncates at ~2^-22 of the accumulator per MMA, an error that
-    follows the strongest traps' coefficients and that this cancellation amplifies the same way.)"""
+    are rejected.  The first weight update here spreads the weights over a factor of ~400, so the
+    back-projection cancels strongly at some pixels and amplifies each mode's per-term error.  The
+    accurate and separable modes stay within the 1e-4 bound on |V_m| (~8e-5 accurate).  The fast
+    and tensor modes are held to their stated limits for such cases (include/hot.h): the fast
+    mode's SFU evaluations err by ~2e-7 rad per term (1.2e-4 measured here, 2e-4 stated); the
+    tensor core's accumulation truncates at ~2^-22 of the accumulator per MMA, an error that
+    follows the strongest traps' coefficients (3.3e-4 measured, 5e-4 stated)."""
+    bound = ILLCOND_REL_V.get(precision, REL_V)
     w = wl.random_case(160, 120, 4096, seed=31, precision=precision)
     with make(hot, w) as h:
         h.gsw(1)
@@ -373,7 +381,29 @@ def test_maximum_trap_count(hot, precision):
         with pytest.raises(hot.HotError, match="HOT_EINVAL"):
             h.set_traps(xyz)
     r1 = oracle.gsw(w.geom, w.xyz, 1, w.phi0)
-    assert rel_err(V1, r1["V"]) < REL_V
+    assert rel_err(V1, r1["V"]) < bound, rel_err(V1, r1["V"])
     np.testing.assert_allclose(w1, r1["w"], rtol=REL_V)
     r2 = oracle.gsw(w.geom, w.xyz, 2, w.phi0)
     assert abs(e - r2["e"]) < ABS_EU and abs(u - r2["u"]) < ABS_EU
+
+
+@pytest.mark.parametrize("precision", ["accurate", "fast"])
+@pytest.mark.parametrize("W,H,M", [(600, 300, 300), (100, 37, 13), (512, 512, 100)])
+def test_block_merge_gives_the_same_bits(hot, W, H, M, precision):
+    """hot_set_block_merge: the GSW step as one block per SM holding the schedule's four blocks
+    computes the same bits as four separate blocks (and as the persistent kernel), with several
+    chunks and sub-tiles per block, ragged tiles and the bench's size."""
+    w = wl.random_case(W, H, M, seed=W + H, precision=precision)
+    out = []
+    for merge, persistent in ((0, False), (1, False), (1, True)):
+        with make(hot, w) as h:
+            h.set_block_merge(merge)
+            h.use_persistent(persistent)
+            assert h.tiling()["merge"] == bool(merge and h.tiling()["blocks_per_sm"] == 4)
+            eu = h.gsw(3)
+            out.append((h.phase("f32"), *h.fields(), eu))
+    for p, V, wt, eu in out[1:]:
+        assert np.array_equal(out[0][0], p) and np.array_equal(out[0][1], V) and np.array_equal(out[0][2], wt)
+        assert eu == out[0][3]
+    with make(hot, w) as h:
+        assert hot.lib.hot_set_block_merge(h.ctx, 2) == hot.HOT_EINVAL

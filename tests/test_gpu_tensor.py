@@ -174,8 +174,11 @@ def test_rejected_calls_and_other_entry_points(hot):
         h.use_persistent(False)
         with pytest.raises(hot.HotError, match="HOT_EINVAL"):
             h.autotune(2)
-        with pytest.raises(hot.HotError, match="HOT_EINVAL"):
-            hot.Batch([h])
+        with hot.Batch([h]) as b:              # tensor batches: no tiling to set or tune
+            with pytest.raises(hot.HotError, match="HOT_EINVAL"):
+                b.set_tiling(rows=7)
+            with pytest.raises(hot.HotError, match="HOT_EINVAL"):
+                b.autotune(2)
         import torch
         phi = torch.from_numpy(np.asarray(w.phi0, dtype=np.float32)).cuda()
         Vd = torch.empty(2 * w.M, dtype=torch.float32, device="cuda")
@@ -186,3 +189,35 @@ def test_rejected_calls_and_other_entry_points(hot):
     assert rel_err(V, oracle.forward(w.geom, w.xyz, w.phi0)) < REL_V
     r = oracle.gsw(w.geom, w.xyz, 2, w.phi0)
     assert abs(e - r["e"]) < ABS_EU and abs(u - r["u"]) < ABS_EU
+
+
+def test_tensor_batch_equals_single_runs(hot):
+    """A HOT_PREC_TENSOR batch runs every member's own launch sequence on concurrent chains: each
+    member's phases, fields and weights equal its hot_gsw run bit for bit (also across a resumed
+    call), and every member gets a completion stamp."""
+    ws = [wl.random_case(W, H, M, seed=W + M, precision="tensor")
+          for (W, H, M) in [(100, 37, 13), (256, 128, 40), (64, 64, 130), (33, 20, 3), (300, 200, 200),
+                            (128, 96, 7), (200, 90, 37), (96, 64, 65), (160, 120, 300), (40, 24, 300)]]
+    ref = []
+    for w in ws:
+        with hot.Hologram.from_workload(w) as h:
+            h.gsw(3)
+            ref.append((h.phase("f32"), *h.fields()))
+    holos = [hot.Hologram.from_workload(w) for w in ws]
+    try:
+        with hot.Batch(holos) as b:
+            assert b.tiling()["groups"] == 8              # chains
+            b.gsw(2)
+            b.gsw(1)
+            lat = b.latency()
+            got = [(h.phase("f32"), *h.fields()) for h in holos]
+            eu = [h.metrics() for h in holos]
+    finally:
+        for h in holos:
+            h.close()
+    for (p0, V0, w0), (p1, V1, w1) in zip(ref, got):
+        assert np.array_equal(p0, p1) and np.array_equal(V0, V1) and np.array_equal(w0, w1)
+    assert np.all(lat > 0) and len(lat) == len(ws)
+    for w, (e, u) in zip(ws, eu):
+        r = oracle.gsw(w.geom, w.xyz, 3, w.phi0)
+        assert abs(e - r["e"]) < ABS_EU and abs(u - r["u"]) < ABS_EU
