@@ -444,93 +444,147 @@ def run_engine(args):
 
 def run_adam(args):
     """Differentiable form (diff256_1024): Adam on the phases for the trap-intensity loss
-    L = -sum log|V_m|^2 + 10 var|V_m|^2 through the autograd Function (forward field and
-    adjoint kernels), 200 steps, lr 1.0; compared with plain GSW on the same traps and phi0."""
+    L = -sum log|V_m|^2 + 10 var|V_m|^2, 200 steps, lr 1.0, in the fast, separable and accurate
+    modes (--precision picks one), three ways: (a) the autograd Function over the
+    forward-field and adjoint kernels with the loss in PyTorch; (b) the loss and its gradient from
+    one library call (hot_intensity_loss) with PyTorch's fused Adam; (c) (b) with each step
+    captured in a CUDA graph (three library kernels and the fused Adam update, no host work per
+    step).  Beside plain GSW on the same traps and phi0 at the same mode.  The line's value is (c)
+    in the workload's mode."""
     import torch
     from paper_0907_4027_gb300 import _build
     _build.build()
     from paper_0907_4027_gb300 import autograd as ag, hot, workloads as wl
 
-    w = wl.NAMED[args.workload]()
-    if args.precision:
-        w.precision = args.precision
+    base = wl.NAMED[args.workload]()
+    modes = [args.precision] if args.precision else ["fast", "separable", "accurate"]
     stream = torch.cuda.current_stream()
-    h = hot.Hologram(w.W, w.H, w.pitch, w.wavelength, w.focal, stream.cuda_stream, w.precision)
-    h.set_traps(w.xyz, w.w0)
+    beta = 10.0
 
     def eu(V):
         I = (V.abs() ** 2).double()
         return float(I.sum()), float(1 - (I.max() - I.min()) / (I.max() + I.min()))
 
-    def adam_run(n_steps, timed):
+    def timed(run, n_steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        run(n_steps)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1])
+
+    results = {}
+    for mode in modes:
+        w = wl.NAMED[args.workload]()
+        w.precision = mode
+        h = hot.Hologram(w.W, w.H, w.pitch, w.wavelength, w.focal, stream.cuda_stream, w.precision)
+        h.set_traps(w.xyz, w.w0)
+        out = {}
+
+        # (a) autograd, loss in PyTorch
         phi = torch.tensor(w.phi0, dtype=torch.float32, device="cuda", requires_grad=True)
         opt = torch.optim.Adam([phi], lr=1.0)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ev[0].record(stream)
-        for _ in range(n_steps):
-            opt.zero_grad(set_to_none=True)
-            L = ag.trap_intensity_loss(ag.trap_fields(h, phi))
-            L.backward()
-            opt.step()
-        ev[1].record(stream)
-        torch.cuda.synchronize()
-        with torch.no_grad():
-            V = ag.trap_fields(h, phi)
-        return ev[0].elapsed_time(ev[1]), float(L.item()), eu(V)
 
-    def adam_lib(n_steps):
-        """The same optimisation with the loss and its gradient from one library call
-        (hot_intensity_loss) and PyTorch's fused Adam."""
+        def step_a(n):
+            for _ in range(n):
+                opt.zero_grad(set_to_none=True)
+                ag.trap_intensity_loss(ag.trap_fields(h, phi), beta).backward()
+                opt.step()
+        step_a(3)
+        with torch.no_grad():
+            phi.copy_(torch.tensor(w.phi0, dtype=torch.float32, device="cuda"))
+        opt = torch.optim.Adam([phi], lr=1.0)
+        ms = timed(step_a, w.iters)
+        with torch.no_grad():
+            out["autograd"] = {"steps_per_s": w.iters / (ms * 1e-3), "ms_per_step": ms / w.iters,
+                               "e_u": eu(ag.trap_fields(h, phi))}
+
+        # (b) library loss and gradient, fused Adam
         phi = torch.tensor(w.phi0, dtype=torch.float32, device="cuda", requires_grad=True)
         opt = torch.optim.Adam([phi], lr=1.0, fused=True)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ev[0].record(stream)
-        for _ in range(n_steps):
-            opt.zero_grad(set_to_none=True)
-            L = ag.intensity_loss(h, phi)
-            L.backward()
-            opt.step()
-        ev[1].record(stream)
-        torch.cuda.synchronize()
-        with torch.no_grad():
-            V = ag.trap_fields(h, phi)
-        return ev[0].elapsed_time(ev[1]), float(L.item()), eu(V)
 
-    adam_run(3, False)
-    ms, loss, (e, u) = adam_run(w.iters, True)
-    adam_lib(3)
-    ms_lib, loss_lib, (e_lib, u_lib) = adam_lib(w.iters)
-    # plain GSW from the same starting phases
-    phi0 = torch.tensor(w.phi0, dtype=torch.float32, device="cuda")
-    gsw = {}
-    for K in (5, 10, 30):
-        h.set_phase(phi0)
-        h.set_weights(np.ones(w.M))
-        h.gsw(K)
-        h.set_phase(phi0)
-        h.set_weights(np.ones(w.M))
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ev[0].record(stream)
-        ge, gu = h.gsw(K)
-        ev[1].record(stream)
+        def step_b(n):
+            for _ in range(n):
+                opt.zero_grad(set_to_none=True)
+                ag.intensity_loss(h, phi, beta).backward()
+                opt.step()
+        step_b(3)
+        with torch.no_grad():
+            phi.copy_(torch.tensor(w.phi0, dtype=torch.float32, device="cuda"))
+        opt = torch.optim.Adam([phi], lr=1.0, fused=True)
+        ms = timed(step_b, w.iters)
+        with torch.no_grad():
+            out["library"] = {"steps_per_s": w.iters / (ms * 1e-3), "ms_per_step": ms / w.iters,
+                              "e_u": eu(ag.trap_fields(h, phi))}
+
+        # (c) the library step captured in a CUDA graph (a hologram on the capture stream)
+        cap = torch.cuda.Stream()
+        hc = hot.Hologram(w.W, w.H, w.pitch, w.wavelength, w.focal, cap.cuda_stream, w.precision)
+        hc.set_traps(w.xyz, w.w0)
+        phi = torch.tensor(w.phi0, dtype=torch.float32, device="cuda", requires_grad=True)
+        phi.grad = torch.zeros_like(phi)
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        opt = torch.optim.Adam([phi], lr=1.0, fused=True, capturable=True)
+
+        def step_c():
+            hot.hot_intensity_loss(hc.ctx, phi.detach(), beta, loss, phi.grad)
+            opt.step()
+        cap.wait_stream(stream)
+        with torch.cuda.stream(cap):
+            for _ in range(3):      # warm-up: optimizer state, the library's buffers
+                step_c()
+        stream.wait_stream(cap)
         torch.cuda.synchronize()
-        gsw[K] = {"ms": ev[0].elapsed_time(ev[1]), "e": ge, "u": gu}
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            step_c()
+        with torch.no_grad():
+            phi.copy_(torch.tensor(w.phi0, dtype=torch.float32, device="cuda"))
+        for st in opt.state.values():
+            for k in ("exp_avg", "exp_avg_sq"):
+                st[k].zero_()
+            st["step"].zero_()
+        torch.cuda.synchronize()
+        ms = timed(lambda n: [g.replay() for _ in range(n)], w.iters)
+        with torch.no_grad():
+            out["library_graph"] = {"steps_per_s": w.iters / (ms * 1e-3), "ms_per_step": ms / w.iters,
+                                    "e_u": eu(ag.trap_fields(h, phi)), "loss": float(loss.item())}
+        hc.close()
+
+        # plain GSW from the same starting phases
+        phi0 = torch.tensor(w.phi0, dtype=torch.float32, device="cuda")
+        gsw = {}
+        for K in (5, 10, 30):
+            h.set_phase(phi0)
+            h.set_weights(np.ones(w.M))
+            h.gsw(K)
+            h.set_phase(phi0)
+            h.set_weights(np.ones(w.M))
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            ge, gu = h.gsw(K)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            gsw[str(K)] = {"ms": ev[0].elapsed_time(ev[1]), "e": ge, "u": gu}
+        out["gsw_same_traps"] = gsw
+        h.close()
+        results[mode] = out
+    main = results[modes[0]]
     line = {
-        "metric": "Adam steps/s on -sum log I + 10 var I (1024x1024 px, M=256)", "value": w.iters / (ms_lib * 1e-3),
-        "unit": "steps/s", "n_gpus": 1, "steps": w.iters, "warmup": 3, "ms_per_step": ms_lib / w.iters,
-        "path": "hot_intensity_loss (forward field, loss and coefficients, adjoint: 3 kernels) + torch fused Adam",
-        "final_library_loss": {"loss": loss_lib, "e": e_lib, "u": u_lib, "ms_total": ms_lib},
-        "autograd_path": {"steps_per_s": w.iters / (ms * 1e-3), "ms_per_step": ms / w.iters,
-                          "path": "trap_fields (hot_field) + PyTorch loss + backward (hot_field_adjoint) + Adam"},
-        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{w.name}: {w.W}x{w.H} px, M={w.M} traps, {w.iters} Adam steps on the phases, "
-                               f"{w.precision} mode", "W": w.W, "H": w.H, "M": w.M, "steps": w.iters,
-                   "precision": w.precision, "seed": 0, "optimizer": "Adam lr 1.0 (the best of 1e-2, 3e-2, 0.1, 0.3, 1.0 for this loss; torch defaults otherwise)"},
-        "final_autograd": {"loss": loss, "e": e, "u": u, "ms_total": ms},
-        "gsw_same_traps": {str(k): v for k, v in gsw.items()},
+        "metric": "Adam steps/s on -sum log I + 10 var I (1024x1024 px, M=256)",
+        "value": main["library_graph"]["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": base.iters,
+        "warmup": 3, "ms_per_step": main["library_graph"]["ms_per_step"], "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "path": "hot_intensity_loss (forward field; loss and adjoint coefficients; adjoint) + torch fused Adam, "
+                "each step one CUDA graph replay",
+        "config": {"workload": f"{base.name}: {base.W}x{base.H} px, M={base.M} traps, {base.iters} Adam steps on "
+                               f"the phases, {modes[0]} mode", "W": base.W, "H": base.H, "M": base.M,
+                   "steps": base.iters, "precision": modes[0], "seed": 0,
+                   "optimizer": "Adam lr 1.0 (the best of 1e-2, 3e-2, 0.1, 0.3, 1.0 for this loss; torch defaults "
+                                "otherwise)"},
+        "modes": results,
     }
     print(json.dumps(line), flush=True)
-    h.close()
     return 0
 
 

@@ -35,6 +35,7 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kTileW = 32;      // pixels per sub-tile row: one per lane
 constexpr int kRowsMax = 14;    // rows per sub-tile (each lane keeps one field per row)
 constexpr int kYStride = (kRowsMax + 3) & ~3;  // floats per trap in the staged row table (16-byte rows)
+static_assert(kTileW == 32 && kYStride == 16, "16-byte staging of 32 columns and 16 rows per trap");
 constexpr int kChunk = 128;     // traps whose tables are staged in shared memory at once
 constexpr float kTwoPi = 6.283185307179586f;
 constexpr int kModeAccurate = 0, kModeFast = 1, kModeSeparable = 2;  // kernel variants
@@ -53,10 +54,14 @@ struct StepArgs {
   int copies;             // copies of each fixed-point accumulator buffer (a power of two; more than
                           // one in the separable mode only): block b adds into copy b % copies,
                           // spreading the atomics over more addresses
+  int ldy4;               // row stride of Y4 (below)
   const SubTile *sub;     // work schedule: sub-tiles
   const int *first;       // [gridDim.x + 1]: block b processes sub-tiles first[b] .. first[b+1]-1
   const float *X;         // [M][W] column phase parts (turns if accurate, radians if fast)
   const float *Y;         // [M][H] row phase parts (same unit)
+  const float *Y4;        // NULL, or [4][M][ldy4]: copy s holds Y shifted by s rows (Y4[s][m][i + s] =
+                          // Y[m][i], zero elsewhere), so that every sub-tile's rows start 16-byte aligned
+                          // in one of the copies
   const float2 *Xc;       // [M][W] e^{i 2pi X} (separable variant)
   const float2 *Yc;       // [M][H] e^{i 2pi Y} (separable variant)
   float *phi;             // [H*W] pixel phases, radians
@@ -171,6 +176,11 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid
   const int n = valid ? 8 : 0;
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
+// 16 bytes, both addresses 16-byte aligned (through L2 only).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -259,19 +269,39 @@ __device__ __forceinline__ float2 adjoint_coefficient(const StepArgs &a, int m) 
 // (rows y0 .. y0+rows-1) tables of traps [m0, m0+n), plus their coefficients when BACK
 // (GSW coefficients, or adjoint coefficients when ADJ).
 // The caller synchronises the block afterwards.
+// A trap's 32 columns of the X table are copied as 8 16-byte pieces when W is a multiple of 4
+// (rows then start 16-byte aligned; x0 is a multiple of 32) and the strip lies inside the image;
+// otherwise column by column, zero past the right edge.  (Four times fewer copy instructions: the
+// staging of every chunk is on the sub-tile's critical path.)
 template <bool BACK, bool ADJ = false>
 __device__ __forceinline__ void stage_tables(const StepArgs &a, int m0, int n, const SubTile &st,
                                              float *Xs, float *Ys, float2 *Cs, bool xy = true,
                                              float mean = 0.f, bool coef = true) {
-  for (int i = gthread(); xy && i < n * kTileW; i += kThreads) {
-    const int k = i / kTileW, col = st.x0 + (i % kTileW);
-    const bool ok = col < a.W;
-    cp_async4(Xs + i, a.X + (ok ? (size_t)(m0 + k) * a.W + col : 0), ok);
+  if (xy && (a.W & 3) == 0 && st.x0 + kTileW <= a.W) {
+    for (int i = gthread(); i < n * (kTileW / 4); i += kThreads) {
+      const int k = i >> 3, q = i & 7;
+      cp_async16(Xs + k * kTileW + 4 * q, a.X + (size_t)(m0 + k) * a.W + st.x0 + 4 * q);
+    }
+  } else {
+    for (int i = gthread(); xy && i < n * kTileW; i += kThreads) {
+      const int k = i / kTileW, col = st.x0 + (i % kTileW);
+      const bool ok = col < a.W;
+      cp_async4(Xs + i, a.X + (ok ? (size_t)(m0 + k) * a.W + col : 0), ok);
+    }
   }
-  for (int i = gthread(); xy && i < n * kYStride; i += kThreads) {
-    const int k = i / kYStride, r = i % kYStride;
-    const bool ok = r < st.rows;
-    cp_async4(Ys + i, a.Y + (ok ? (size_t)(m0 + k) * a.H + st.y0 + r : 0), ok);
+  if (xy && a.Y4) {  // the trap's kYStride rows from y0 as 4 16-byte pieces of the aligned copy
+    const int s = (4 - (st.y0 & 3)) & 3;
+    const float *src = a.Y4 + ((size_t)s * a.M + m0) * a.ldy4 + st.y0 + s;
+    for (int i = gthread(); i < n * (kYStride / 4); i += kThreads) {
+      const int k = i >> 2, q = i & 3;
+      cp_async16(Ys + k * kYStride + 4 * q, src + (size_t)k * a.ldy4 + 4 * q);
+    }
+  } else {
+    for (int i = gthread(); xy && i < n * kYStride; i += kThreads) {
+      const int k = i / kYStride, r = i % kYStride;
+      const bool ok = r < st.rows;
+      cp_async4(Ys + i, a.Y + (ok ? (size_t)(m0 + k) * a.H + st.y0 + r : 0), ok);
+    }
   }
   if (BACK && coef)
     for (int i = gthread(); i < n; i += kThreads)
@@ -280,6 +310,9 @@ __device__ __forceinline__ void stage_tables(const StepArgs &a, int m0, int n, c
 }
 
 constexpr int kGroup = 8;  // traps reduced together over the lanes of a warp
+// ... in the direct kernels' forward field (4 or 8: the unrolled loop body over a group's traps
+// and the sub-tile's rows is the largest code of the kernel)
+constexpr int kFwdGroup = 8;
 
 // Sums acc[0..7] over the 32 lanes of a warp with 18 shuffles instead of 8 x 5: at each of
 // the first three steps a lane keeps half of its traps and sends the other half to its
@@ -312,6 +345,37 @@ __device__ __forceinline__ float2 warp_reduce8(float2 (&acc)[kGroup], int lane) 
   v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
   return v;
 }
+
+// Sums acc[0..3] over the 32 lanes of a warp with 12 shuffles: at offsets 16 and 8 a lane keeps
+// half of its traps and sends the other half, so that lane l then holds trap (l >> 3) & 3 summed
+// over 4 lanes; three butterfly steps finish the sum (lanes with (lane & 7) == 0 store it).
+__device__ __forceinline__ float2 warp_reduce4(float2 (&acc)[4], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8;
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    const float2 send = b4 ? acc[i] : acc[i + 2], keep = b4 ? acc[i + 2] : acc[i];
+    acc[i].x = keep.x + __shfl_xor_sync(0xffffffffu, send.x, 16);
+    acc[i].y = keep.y + __shfl_xor_sync(0xffffffffu, send.y, 16);
+  }
+  {
+    const float2 send = b3 ? acc[0] : acc[1], keep = b3 ? acc[1] : acc[0];
+    acc[0].x = keep.x + __shfl_xor_sync(0xffffffffu, send.x, 8);
+    acc[0].y = keep.y + __shfl_xor_sync(0xffffffffu, send.y, 8);
+  }
+  float2 v = acc[0];
+#pragma unroll
+  for (int o = 4; o; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// The group reductions by size, and the trap of the group whose total lane `lane` holds.
+__device__ __forceinline__ float2 warp_reduce_group(float2 (&acc)[8], int lane) { return warp_reduce8(acc, lane); }
+__device__ __forceinline__ float2 warp_reduce_group(float2 (&acc)[4], int lane) { return warp_reduce4(acc, lane); }
+template <int NG>
+__device__ __forceinline__ int group_trap(int lane) { return (lane >> (NG == 8 ? 2 : 3)) & (NG - 1); }
 
 // Back-projection of traps [lo, hi) of the staged chunk onto the R rows of this lane:
 // S_r += w_m e^{i (X_m + Y_m(r) + arg V_m)}.  R is a compile-time row count.
@@ -355,10 +419,12 @@ template <bool FAST, int R>
 __device__ __forceinline__ void forward_traps(const float *Xs, const float *Ys, int lo, int hi, int lane,
                                               const float (&ph)[kRowsMax], float msk, const StepArgs &a,
                                               int m0, float2 undo = make_float2(1.f, 0.f)) {
-  for (int g = lo; g < hi; g += kGroup) {
-    float2 acc[kGroup];
+  constexpr int NG = kFwdGroup;
+  static_assert(NG == 4 || NG == 8, "forward group of 4 or 8 traps");
+  for (int g = lo; g < hi; g += NG) {
+    float2 acc[NG];
 #pragma unroll
-    for (int i = 0; i < kGroup; i++) {
+    for (int i = 0; i < NG; i++) {
       acc[i] = make_float2(0.f, 0.f);
       const int k = g + i;
       if (k < hi) {
@@ -381,10 +447,11 @@ __device__ __forceinline__ void forward_traps(const float *Xs, const float *Ys, 
         }
       }
     }
-    float2 v = warp_reduce8(acc, lane);
+    float2 v = warp_reduce_group(acc, lane);
+    const int k = g + group_trap<NG>(lane);
+    const bool store = (lane & (32 / NG - 1)) == 0;
     if (FAST) v = make_float2(fmaf(v.x, undo.x, -v.y * undo.y), fmaf(v.x, undo.y, v.y * undo.x));
-    const int k = g + ((lane >> 2) & 7);
-    if ((lane & 3) == 0 && k < hi) {
+    if (store && k < hi) {
       // |v| <= 32 * kRowsMax, so v * 2^fx_shift is an exact integer far below 2^63
       atomicAdd(a.acc_out + m0 + k, (unsigned long long)__float2ll_rn(v.x * a.fx_scale));
       atomicAdd(a.acc_out + a.M + m0 + k, (unsigned long long)__float2ll_rn(v.y * a.fx_scale));
@@ -1271,8 +1338,11 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)
 // abc: [M][3] = a_m, b_m, c_m in turns (see the file header).  Writes turns and radians.
 // A row band (rows y_off .. y_off+H-1 of a hologram of H_total rows) takes the row parts of
 // its global rows.
+// Y4t, Y4r (optional): the shifted copies of the row parts (StepArgs::Y4), [4][M][ldy4], whose
+// entries outside the shifted rows stay as they are (zero from allocation).
 __global__ void build_tables_kernel(int W, int H, int H_total, int y_off, int M, const double *abc, float *Xt,
-                                    float *Yt, float *Xr, float *Yr, float2 *Xc, float2 *Yc) {
+                                    float *Yt, float *Xr, float *Yr, float2 *Xc, float2 *Yc, float *Y4t = nullptr,
+                                    float *Y4r = nullptr, int ldy4 = 0) {
   const long long total = (long long)M * (W + H);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -1298,6 +1368,11 @@ __global__ void build_tables_kernel(int W, int H, int H_total, int y_off, int M,
     } else {
       Yt[(size_t)m * H + (i - W)] = tf;
       Yr[(size_t)m * H + (i - W)] = rf;
+      if (Y4t)
+        for (int sh = 0; sh < 4; sh++) {
+          Y4t[((size_t)sh * M + m) * ldy4 + (i - W) + sh] = tf;
+          Y4r[((size_t)sh * M + m) * ldy4 + (i - W) + sh] = rf;
+        }
       if (Yc) Yc[(size_t)m * H + (i - W)] = make_float2((float)cs, (float)sn);
     }
   }

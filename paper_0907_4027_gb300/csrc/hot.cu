@@ -79,6 +79,8 @@ struct hot_ctx {
   int M = 0;
   double *abc = nullptr;                                       // [M][3]
   float *Xt = nullptr, *Yt = nullptr, *Xr = nullptr, *Yr = nullptr;  // tables
+  float *Y4t = nullptr, *Y4r = nullptr;  // [4][M][ldy4] shifted row tables (hot::StepArgs::Y4)
+  int ldy4 = 0;
   float2 *Xc = nullptr, *Yc = nullptr;                               // complex tables (separable)
   float *w = nullptr;                                          // [2][M] weights (home: w[0])
   unsigned long long *acc = nullptr;                           // [3][copies][2][M] fixed-point field sums
@@ -159,6 +161,8 @@ void free_traps(hot_ctx *c) {
   dfree(c->Yt);
   dfree(c->Xr);
   dfree(c->Yr);
+  dfree(c->Y4t);
+  dfree(c->Y4r);
   dfree(c->Xc);
   dfree(c->Yc);
   dfree(c->w);
@@ -243,6 +247,8 @@ hot::StepArgs make_step_args(const hot_ctx *c, int k, const float *phi, const fl
   a.first = c->first;
   a.X = fast ? c->Xr : c->Xt;
   a.Y = fast ? c->Yr : c->Yt;
+  a.Y4 = fast ? c->Y4r : c->Y4t;
+  a.ldy4 = c->ldy4;
   a.Xc = c->Xc;
   a.Yc = c->Yc;
   a.phi = c->phi;
@@ -445,7 +451,7 @@ int launch_build_tables(hot_ctx *c) {
   const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
   Probe p(c, HOT_KERNEL_OTHER);
   hot::build_tables_kernel<<<blocks, 256, 0, c->st>>>(c->W, c->H, c->H_total, c->y_off, c->M, c->abc, c->Xt, c->Yt,
-                                                      c->Xr, c->Yr, c->Xc, c->Yc);
+                                                      c->Xr, c->Yr, c->Xc, c->Yc, c->Y4t, c->Y4r, c->ldy4);
   int rc = check_launch(c, "build_tables_kernel");
   if (rc == HOT_OK && c->tc) {  // the tensor-core operands derive from the tables
     cudaError_t e = hot_tc::plan_refresh(c->tc, c->st);
@@ -712,6 +718,13 @@ int hot_set_traps(hot_ctx *c, int M, const double *xyz_m, const double *w0) {
     if (rc == HOT_OK) rc = dalloc(&c->Xr, (size_t)M * c->W);
     if (rc == HOT_OK) rc = dalloc(&c->Yt, (size_t)M * c->H);
     if (rc == HOT_OK) rc = dalloc(&c->Yr, (size_t)M * c->H);
+    // shifted row tables: rows y0 .. y0 + 15 of copy (4 - y0 % 4) % 4 start 16-byte aligned
+    c->ldy4 = (c->H + 18 + 3) & ~3;
+    if (rc == HOT_OK) rc = dalloc(&c->Y4t, 4 * (size_t)M * c->ldy4);
+    if (rc == HOT_OK) rc = dalloc(&c->Y4r, 4 * (size_t)M * c->ldy4);
+    if (rc == HOT_OK && (cudaMemsetAsync(c->Y4t, 0, sizeof(float) * 4 * (size_t)M * c->ldy4, c->st) != cudaSuccess ||
+                         cudaMemsetAsync(c->Y4r, 0, sizeof(float) * 4 * (size_t)M * c->ldy4, c->st) != cudaSuccess))
+      rc = fail(HOT_ECUDA, "hot_set_traps: clearing the shifted row tables failed");
     if (rc == HOT_OK) rc = dalloc(&c->Xc, (size_t)M * c->W);
     if (rc == HOT_OK) rc = dalloc(&c->Yc, (size_t)M * c->H);
     if (rc == HOT_OK) rc = dalloc(&c->w, 2 * (size_t)M);
@@ -1255,6 +1268,8 @@ hot::StepArgs step_args(const hot_ctx *c, int k, int chunk) {
   a.copies = acc_copies(c);
   a.X = fast ? c->Xr : c->Xt;
   a.Y = fast ? c->Yr : c->Yt;
+  a.Y4 = fast ? c->Y4r : c->Y4t;
+  a.ldy4 = c->ldy4;
   a.Xc = c->Xc;
   a.Yc = c->Yc;
   a.phi = c->phi;
