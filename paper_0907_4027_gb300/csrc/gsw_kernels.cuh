@@ -63,7 +63,9 @@ struct StepArgs {
                           // Y[m][i], zero elsewhere), so that every sub-tile's rows start 16-byte aligned
                           // in one of the copies
   const float2 *Xc;       // [M][W] e^{i 2pi X} (separable variant)
-  const float2 *Yc;       // [M][H] e^{i 2pi Y} (separable variant)
+  const float2 *Yc;       // [2][M][ldy4] e^{i 2pi Y} (separable variant), in two copies: copy s holds the
+                          // rows shifted by s (Yc[s][m][i + s] = e^{i 2pi Y_m(i)}, zero elsewhere), so
+                          // that every sub-tile's rows start 16-byte aligned in one of them
   float *phi;             // [H*W] pixel phases, radians
   // BACK: weight update and coefficients from the previous launch's forward field
   const unsigned long long *acc_in;  // [copies][2][M] fixed-point sums of the previous forward: Re, Im
@@ -958,18 +960,28 @@ template <bool BACK, bool ADJ = false>
 __device__ __forceinline__ void stage_sep(const StepArgs &a, int m0, int n, const SubTile &st, const SepSmem &sm,
                                           bool xy = true, float mean = 0.f, bool coef = true) {
   if (xy) {
-    // thread t copies column t % 32 of traps t / 32, t / 32 + 8, ... and row t % 16 of traps
-    // t / 16, t / 16 + 16, ...: fixed column / row, pointers advanced by whole trap strides
-    const int col = gthread() % kTileW, kx = gthread() / kTileW;
-    const bool okx = st.x0 + col < a.W;
-    const float2 *src = a.Xc + (okx ? (size_t)(m0 + kx) * a.W + st.x0 + col : 0);
-    const size_t sx = okx ? (size_t)(kThreads / kTileW) * a.W : 0;
-    for (int k = kx; k < n; k += kThreads / kTileW, src += sx) cp_async8(sm.Xs + k * kTileW + col, src, okx);
-    const int r = gthread() % kYStride, ky = gthread() / kYStride;
-    const bool oky = r < st.rows;
-    const float2 *srcy = a.Yc + (oky ? (size_t)(m0 + ky) * a.H + st.y0 + r : 0);
-    const size_t sy = oky ? (size_t)(kThreads / kYStride) * a.H : 0;
-    for (int k = ky; k < n; k += kThreads / kYStride, srcy += sy) cp_async8(sm.Ys + k * kYStride + r, srcy, oky);
+    if ((a.W & 1) == 0 && st.x0 + kTileW <= a.W) {
+      // thread t copies columns 2 (t % 16), +1 of traps t / 16, t / 16 + 16, ... (16 bytes:
+      // rows start 16-byte aligned for even W)
+      const int q = gthread() % (kTileW / 2), kx = gthread() / (kTileW / 2);
+      const float2 *src = a.Xc + (size_t)(m0 + kx) * a.W + st.x0 + 2 * q;
+      const size_t sx = (size_t)(kThreads / (kTileW / 2)) * a.W;
+      for (int k = kx; k < n; k += kThreads / (kTileW / 2), src += sx) cp_async16(sm.Xs + k * kTileW + 2 * q, src);
+    } else {
+      // thread t copies column t % 32 of traps t / 32, t / 32 + 8, ...: fixed column, pointers
+      // advanced by whole trap strides
+      const int col = gthread() % kTileW, kx = gthread() / kTileW;
+      const bool okx = st.x0 + col < a.W;
+      const float2 *src = a.Xc + (okx ? (size_t)(m0 + kx) * a.W + st.x0 + col : 0);
+      const size_t sx = okx ? (size_t)(kThreads / kTileW) * a.W : 0;
+      for (int k = kx; k < n; k += kThreads / kTileW, src += sx) cp_async8(sm.Xs + k * kTileW + col, src, okx);
+    }
+    // rows y0 .. y0 + 15 of copy y0 % 2 (16-byte aligned): thread t copies rows 2 (t % 8), +1 of
+    // traps t / 8, t / 8 + 32, ...
+    const int s = st.y0 & 1, q = gthread() % (kYStride / 2), ky = gthread() / (kYStride / 2);
+    const float2 *srcy = a.Yc + ((size_t)s * a.M + m0 + ky) * a.ldy4 + st.y0 + s + 2 * q;
+    const size_t sy = (size_t)(kThreads / (kYStride / 2)) * a.ldy4;
+    for (int k = ky; k < n; k += kThreads / (kYStride / 2), srcy += sy) cp_async16(sm.Ys + k * kYStride + 2 * q, srcy);
   }
   if (BACK && coef)
     for (int i = gthread(); i < n; i += kThreads)
@@ -1338,11 +1350,12 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)
 // abc: [M][3] = a_m, b_m, c_m in turns (see the file header).  Writes turns and radians.
 // A row band (rows y_off .. y_off+H-1 of a hologram of H_total rows) takes the row parts of
 // its global rows.
-// Y4t, Y4r (optional): the shifted copies of the row parts (StepArgs::Y4), [4][M][ldy4], whose
-// entries outside the shifted rows stay as they are (zero from allocation).
+// Y4t, Y4r (optional): the shifted copies of the row parts (StepArgs::Y4), [4][M][ldy4], and
+// Yc2 (optional) the two shifted copies of Yc (StepArgs::Yc), [2][M][ldy4], whose entries outside
+// the shifted rows stay as they are (zero from allocation).
 __global__ void build_tables_kernel(int W, int H, int H_total, int y_off, int M, const double *abc, float *Xt,
                                     float *Yt, float *Xr, float *Yr, float2 *Xc, float2 *Yc, float *Y4t = nullptr,
-                                    float *Y4r = nullptr, int ldy4 = 0) {
+                                    float *Y4r = nullptr, int ldy4 = 0, float2 *Yc2 = nullptr) {
   const long long total = (long long)M * (W + H);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -1374,6 +1387,8 @@ __global__ void build_tables_kernel(int W, int H, int H_total, int y_off, int M,
           Y4r[((size_t)sh * M + m) * ldy4 + (i - W) + sh] = rf;
         }
       if (Yc) Yc[(size_t)m * H + (i - W)] = make_float2((float)cs, (float)sn);
+      if (Yc2)
+        for (int sh = 0; sh < 2; sh++) Yc2[((size_t)sh * M + m) * ldy4 + (i - W) + sh] = make_float2((float)cs, (float)sn);
     }
   }
 }

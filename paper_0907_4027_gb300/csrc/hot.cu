@@ -82,6 +82,7 @@ struct hot_ctx {
   float *Y4t = nullptr, *Y4r = nullptr;  // [4][M][ldy4] shifted row tables (hot::StepArgs::Y4)
   int ldy4 = 0;
   float2 *Xc = nullptr, *Yc = nullptr;                               // complex tables (separable)
+  float2 *Yc2 = nullptr;  // [2][M][ldy4] row-shifted copies of Yc (hot::StepArgs::Yc)
   float *w = nullptr;                                          // [2][M] weights (home: w[0])
   unsigned long long *acc = nullptr;                           // [3][copies][2][M] fixed-point field sums
   long long *Vsum = nullptr;                                   // [2][M] sums of the last forward
@@ -165,6 +166,7 @@ void free_traps(hot_ctx *c) {
   dfree(c->Y4r);
   dfree(c->Xc);
   dfree(c->Yc);
+  dfree(c->Yc2);
   dfree(c->w);
   dfree(c->acc);
   dfree(c->Vsum);
@@ -250,7 +252,7 @@ hot::StepArgs make_step_args(const hot_ctx *c, int k, const float *phi, const fl
   a.Y4 = fast ? c->Y4r : c->Y4t;
   a.ldy4 = c->ldy4;
   a.Xc = c->Xc;
-  a.Yc = c->Yc;
+  a.Yc = c->Yc2;
   a.phi = c->phi;
   const size_t M2 = 2 * (size_t)c->M * acc_copies(c);
   a.copies = acc_copies(c);
@@ -451,7 +453,7 @@ int launch_build_tables(hot_ctx *c) {
   const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
   Probe p(c, HOT_KERNEL_OTHER);
   hot::build_tables_kernel<<<blocks, 256, 0, c->st>>>(c->W, c->H, c->H_total, c->y_off, c->M, c->abc, c->Xt, c->Yt,
-                                                      c->Xr, c->Yr, c->Xc, c->Yc, c->Y4t, c->Y4r, c->ldy4);
+                                                      c->Xr, c->Yr, c->Xc, c->Yc, c->Y4t, c->Y4r, c->ldy4, c->Yc2);
   int rc = check_launch(c, "build_tables_kernel");
   if (rc == HOT_OK && c->tc) {  // the tensor-core operands derive from the tables
     cudaError_t e = hot_tc::plan_refresh(c->tc, c->st);
@@ -727,6 +729,9 @@ int hot_set_traps(hot_ctx *c, int M, const double *xyz_m, const double *w0) {
       rc = fail(HOT_ECUDA, "hot_set_traps: clearing the shifted row tables failed");
     if (rc == HOT_OK) rc = dalloc(&c->Xc, (size_t)M * c->W);
     if (rc == HOT_OK) rc = dalloc(&c->Yc, (size_t)M * c->H);
+    if (rc == HOT_OK) rc = dalloc(&c->Yc2, 2 * (size_t)M * c->ldy4);
+    if (rc == HOT_OK && cudaMemsetAsync(c->Yc2, 0, sizeof(float2) * 2 * (size_t)M * c->ldy4, c->st) != cudaSuccess)
+      rc = fail(HOT_ECUDA, "hot_set_traps: clearing the shifted complex row table failed");
     if (rc == HOT_OK) rc = dalloc(&c->w, 2 * (size_t)M);
     if (rc == HOT_OK) rc = dalloc(&c->acc, acc_elems(M));
     if (rc == HOT_OK) rc = dalloc(&c->Vsum, 2 * (size_t)M);
@@ -1271,7 +1276,7 @@ hot::StepArgs step_args(const hot_ctx *c, int k, int chunk) {
   a.Y4 = fast ? c->Y4r : c->Y4t;
   a.ldy4 = c->ldy4;
   a.Xc = c->Xc;
-  a.Yc = c->Yc;
+  a.Yc = c->Yc2;
   a.phi = c->phi;
   a.acc_in = c->acc + M2 * ((k + 2) % 3);
   a.acc_out = c->acc + M2 * (k % 3);
