@@ -268,17 +268,17 @@ int hot_set_tiling(hot_ctx *c, int rows, int blocks_per_sm, int chunk);
 int hot_get_tiling(const hot_ctx *c, int *rows, int *blocks_per_sm, int *chunk);
 
 /* Block merging of the accurate and fast modes' GSW step (no counterpart in the paper): with
- * merge = 1 and 4 blocks per SM (the default count), the step launches one block of 1024
- * threads per SM that holds the schedule's 4 blocks as groups of 256 threads, each with its own
- * shared memory and barrier.  The 4 blocks of an SM then hold consecutive runs of the image,
- * which add up to the SM's equal share to within one 32-pixel row segment (independent blocks
+ * 4 schedule blocks per SM (the default count), merge = 4 launches one block of 1024 threads per
+ * SM that holds 4 schedule blocks as groups of 256 threads (each with its own shared memory and
+ * barrier), merge = 2 two blocks of 512 threads per SM holding 2 each, merge = 1 (default) the
+ * schedule's blocks themselves.  Consecutive schedule blocks hold consecutive runs of the image,
+ * which add up to their equal share to within one 32-pixel row segment, while independent blocks
  * land on SMs in no fixed order, and an SM may get 4 runs that are each one segment longer than
- * average); the next launch's blocks start later, as each SM's whole block must finish first.
- * Measured on GB300 (fast mode): 8 % faster at 1920 x 1152 px with 1000 traps, slower at small
- * sizes (2 % at 512 x 512 px with 100 traps).  The results are the same bits either way.
- * Default 0; hot_autotune searches it.  merge: 0 or 1, else HOT_EINVAL.  Rebuilds the schedule;
- * synchronises the context's stream.  hot_get_block_merge reports the setting and whether the
- * step runs merged (only in the accurate and fast modes with 4 blocks per SM). */
+ * average.  The price of merging is a later start of the next launch's blocks (a launched block's
+ * groups must all finish first).  The results are the same bits either way.  hot_autotune
+ * searches 1, 2 and 4.  merge: 1, 2 or 4, else HOT_EINVAL.  Rebuilds the schedule; synchronises
+ * the context's stream.  hot_get_block_merge reports the setting and the merge in effect (1 where
+ * it does not apply: the separable and tensor modes, fewer than 4 blocks per SM). */
 int hot_set_block_merge(hot_ctx *c, int merge);
 int hot_get_block_merge(const hot_ctx *c, int *requested, int *in_effect);
 

@@ -793,13 +793,14 @@ __device__ __forceinline__ void process_subtile(const StepArgs &a, const SubTile
   }
 }
 
-// GROUPS > 1: one block of GROUPS x kThreads threads per SM, group g of block b acting as
-// virtual block GROUPS b + g of the schedule, with its own shared memory and barrier.  The
-// schedule deals consecutive runs of row segments to consecutive virtual blocks, so the GROUPS
-// runs of an SM add up to its equal share of the image to within one segment, whereas with
-// independent blocks an SM may hold GROUPS runs that are all one segment longer than average.
+// GROUPS > 1: blocks of GROUPS x kThreads threads (4 / GROUPS per SM), group g of block b acting
+// as virtual block GROUPS b + g of the schedule, with its own shared memory and barrier.  The
+// schedule deals consecutive runs of row segments to consecutive virtual blocks, and consecutive
+// runs add up to their equal share to within one segment: with GROUPS = 4 an SM holds its equal
+// share, with GROUPS = 2 each of its two blocks does, whereas with independent blocks an SM may
+// hold four runs that are all one segment longer than average.
 template <bool FAST, bool BACK, bool FWD, bool ADJ = false, int GROUPS = 1>
-__global__ void __launch_bounds__(kThreads * GROUPS, GROUPS == 1 ? 4 : 1) gsw_step_kernel(StepArgs a) {
+__global__ void __launch_bounds__(kThreads * GROUPS, kMaxGroups / GROUPS) gsw_step_kernel(StepArgs a) {
   static_assert(!ADJ || (BACK && !FWD), "the adjoint is a back-projection without forward field");
   static_assert(GROUPS >= 1 && GROUPS <= kMaxGroups, "groups per block");
   extern __shared__ __align__(16) unsigned char smem_raw[];

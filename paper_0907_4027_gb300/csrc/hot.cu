@@ -71,7 +71,7 @@ struct hot_ctx {
   // (0: as many as fit), traps per staged chunk
   int tile_rows = hot::kRowsMax, tile_bps = 0, tile_chunk = hot::kChunk;
   int sched_bps = 0, sched_bps_max = 0;  // resident blocks per SM in the schedule; occupancy limit
-  int tile_merge = 0;  // hot_set_block_merge: the GSW step's 4 blocks per SM as one launched block
+  int tile_merge = 1;  // hot_set_block_merge: schedule blocks per launched block of the GSW step (1, 2, 4)
   int groups = 1;      // schedule blocks per launched block of the direct GSW step (1 or 4)
   int shard_k = -1;                      // last launch of a sharded sequence (hot_sharded_*)
   // state
@@ -282,9 +282,10 @@ int launch_tile(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const f
   const hot::StepArgs a = make_step_args(c, k, phi, G, grad);
   const int smem = hot::step_smem_bytes(c->M, BACK);
   Probe p(c, BACK && FWD ? HOT_KERNEL_STEP : FWD ? HOT_KERNEL_FORWARD : HOT_KERNEL_OTHER);
-  if (BACK && FWD && !ADJ && c->groups == hot::kMaxGroups)  // the GSW step: one block per SM
-    launch(c, hot::gsw_step_kernel<FAST, true, true, false, hot::kMaxGroups>, c->grid / hot::kMaxGroups,
-           hot::kThreads * hot::kMaxGroups, smem * hot::kMaxGroups, pdl, a);
+  if (BACK && FWD && !ADJ && c->groups == 4)  // the GSW step, merged: one block per SM
+    launch(c, hot::gsw_step_kernel<FAST, true, true, false, 4>, c->grid / 4, hot::kThreads * 4, smem * 4, pdl, a);
+  else if (BACK && FWD && !ADJ && c->groups == 2)  // two blocks per SM, two schedule blocks each
+    launch(c, hot::gsw_step_kernel<FAST, true, true, false, 2>, c->grid / 2, hot::kThreads * 2, smem * 2, pdl, a);
   else
     launch(c, hot::gsw_step_kernel<FAST, BACK, FWD, ADJ>, c->grid, hot::kThreads, smem, pdl, a);
   return check_launch(c, "gsw_step_kernel");
@@ -320,9 +321,10 @@ int set_step_smem(int M) {
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd));
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, back));
-  constexpr int G4 = hot::kMaxGroups;
-  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, true, true, false, G4>, cudaFuncAttributeMaxDynamicSharedMemorySize, G4 * back));
-  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, true, true, false, G4>, cudaFuncAttributeMaxDynamicSharedMemorySize, G4 * back));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, true, true, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * back));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, true, true, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * back));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<true, true, true, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * back));
+  HOT_CUDA(cudaFuncSetAttribute(hot::gsw_step_kernel<false, true, true, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * back));
   const int sep = hot::sep_smem_bytes(hot::kChunk);
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_sep_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sep));
   HOT_CUDA(cudaFuncSetAttribute(hot::gsw_sep_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sep));
@@ -370,12 +372,16 @@ int build_schedule(hot_ctx *c) {
   // Merged (hot_set_block_merge), with four schedule blocks per SM the direct modes' GSW step
   // runs one block per SM holding four of them (see gsw_step_kernel), if such a block fits.
   c->groups = 1;
-  if (c->tile_merge && !separable_kernels(c) && per_sm == hot::kMaxGroups) {
+  if (c->tile_merge > 1 && !separable_kernels(c) && per_sm == hot::kMaxGroups) {
     int per_sm_g = 0;
-    HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm_g, hot::gsw_step_kernel<true, true, true, false, hot::kMaxGroups>, hot::kThreads * hot::kMaxGroups,
-        hot::kMaxGroups * hot::step_smem_bytes(c->M, true)));
-    if (per_sm_g >= 1) c->groups = hot::kMaxGroups;
+    const int smem = c->tile_merge * hot::step_smem_bytes(c->M, true);
+    if (c->tile_merge == 4)
+      HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_g, hot::gsw_step_kernel<true, true, true, false, 4>,
+                                                             hot::kThreads * 4, smem));
+    else
+      HOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_g, hot::gsw_step_kernel<true, true, true, false, 2>,
+                                                             hot::kThreads * 2, smem));
+    if (per_sm_g * c->tile_merge >= per_sm) c->groups = c->tile_merge;
   }
   const int strips = (c->W + hot::kTileW - 1) / hot::kTileW;
   const long long U = (long long)strips * c->H;
@@ -1543,7 +1549,8 @@ constexpr int kMaxBlocksPerSm = 4;
 // Coordinate search: each parameter in turn takes the fastest of its candidates with the
 // others fixed; a candidate replaces the incumbent only if it is more than 1 % faster; at
 // most two passes.  apply(t) installs a tiling, time(&us) measures it.  Leaves `best` applied.
-// With merge, the blocks-per-SM candidates include max_bps blocks merged into one (Tiling::merge).
+// With merge, the blocks-per-SM candidates include max_bps blocks merged four and two to a
+// launched block (Tiling::merge: schedule blocks per launched block).
 template <typename Apply, typename Time>
 int tune_tiling(int max_bps, Tiling &best, double &best_us, Apply apply, Time time, bool merge = false) {
   static const int rows_c[] = {14, 12, 10, 8, 6, 4, 2};
@@ -1553,18 +1560,21 @@ int tune_tiling(int max_bps, Tiling &best, double &best_us, Apply apply, Time ti
   for (int pass = 0; rc == HOT_OK && pass < 2; pass++) {
     bool changed = false;
     for (int dim = 0; rc == HOT_OK && dim < 3; dim++) {
-      std::vector<int> cand;  // blocks per SM: -v stands for v blocks merged
+      std::vector<int> cand;  // blocks per SM; -4 and -2: max_bps blocks merged 4 or 2 to a block
       if (dim == 0) cand.assign(std::begin(rows_c), std::end(rows_c));
       if (dim == 1) {
-        if (merge) cand.push_back(-max_bps);
+        if (merge) {
+          cand.push_back(-4);
+          cand.push_back(-2);
+        }
         for (int v = max_bps; v >= 1; v--) cand.push_back(v);
       }
       if (dim == 2) cand.assign(std::begin(chunk_c), std::end(chunk_c));
       for (int v : cand) {
         Tiling t = best;
         if (dim == 1) {
-          t.bps = v < 0 ? -v : v;
-          t.merge = v < 0;
+          t.bps = v < 0 ? max_bps : v;
+          t.merge = v < 0 ? -v : 1;
         } else {
           (dim == 0 ? t.rows : t.chunk) = v;
         }
@@ -1668,7 +1678,7 @@ int hot_get_tiling(const hot_ctx *c, int *rows, int *blocks_per_sm, int *chunk) 
 
 int hot_set_block_merge(hot_ctx *c, int merge) {
   if (!c) return fail(HOT_EINVAL, "hot_set_block_merge: NULL context");
-  if (merge != 0 && merge != 1) return fail(HOT_EINVAL, "hot_set_block_merge: merge = %d is not 0 or 1", merge);
+  if (merge != 1 && merge != 2 && merge != 4) return fail(HOT_EINVAL, "hot_set_block_merge: merge = %d is not 1, 2 or 4", merge);
   HOT_CUDA(cudaStreamSynchronize(c->st));
   c->tile_merge = merge;
   drop_graphs(c);
@@ -1678,7 +1688,7 @@ int hot_set_block_merge(hot_ctx *c, int merge) {
 int hot_get_block_merge(const hot_ctx *c, int *requested, int *in_effect) {
   if (!c) return fail(HOT_EINVAL, "hot_get_block_merge: NULL context");
   if (requested) *requested = c->tile_merge;
-  if (in_effect) *in_effect = c->groups > 1;
+  if (in_effect) *in_effect = c->groups;
   return HOT_OK;
 }
 
@@ -1837,7 +1847,7 @@ int hot_batch_autotune(hot_batch *b, int iters, int *rows, int *blocks_per_sm, i
     }
     return (int)HOT_OK;
   };
-  Tiling best = {b->rows, b->bps > 0 ? std::min(b->bps, b->per_sm_max) : b->per_sm_max, b->chunk, 0};
+  Tiling best = {b->rows, b->bps > 0 ? std::min(b->bps, b->per_sm_max) : b->per_sm_max, b->chunk, 1};
   double best_us = 0;
   const double gp = b->group_pairs;
   rc = tune_tiling(

@@ -267,14 +267,17 @@ def hot_get_tiling(ctx: int) -> dict:
     return {"rows": r.value, "blocks_per_sm": b.value, "chunk": c.value}
 
 
-def hot_set_block_merge(ctx: int, merge: bool) -> None:
-    _ok(lib.hot_set_block_merge(_vp(ctx), int(bool(merge))), "hot_set_block_merge")
+def hot_set_block_merge(ctx: int, merge) -> None:
+    """merge: schedule blocks per launched block of the GSW step, 1, 2 or 4 (True: 4, False: 1)."""
+    if isinstance(merge, bool):
+        merge = 4 if merge else 1
+    _ok(lib.hot_set_block_merge(_vp(ctx), int(merge)), "hot_set_block_merge")
 
 
 def hot_get_block_merge(ctx: int) -> dict:
     req, eff = _c_int(), _c_int()
     _ok(lib.hot_get_block_merge(_vp(ctx), ctypes.byref(req), ctypes.byref(eff)), "hot_get_block_merge")
-    return {"requested": bool(req.value), "in_effect": bool(eff.value)}
+    return {"requested": req.value, "in_effect": eff.value}
 
 
 def hot_autotune(ctx: int, iters: int) -> dict:
@@ -528,7 +531,7 @@ class Hologram:
     def set_tiling(self, rows: int = 0, blocks_per_sm: int = 0, chunk: int = 0):
         hot_set_tiling(self.ctx, rows, blocks_per_sm, chunk)
 
-    def set_block_merge(self, merge: bool = True):
+    def set_block_merge(self, merge=4):
         hot_set_block_merge(self.ctx, merge)
 
     def use_persistent(self, enable: bool = True):

@@ -390,20 +390,20 @@ def test_maximum_trap_count(hot, precision):
 @pytest.mark.parametrize("precision", ["accurate", "fast"])
 @pytest.mark.parametrize("W,H,M", [(600, 300, 300), (100, 37, 13), (512, 512, 100)])
 def test_block_merge_gives_the_same_bits(hot, W, H, M, precision):
-    """hot_set_block_merge: the GSW step as one block per SM holding the schedule's four blocks
-    computes the same bits as four separate blocks (and as the persistent kernel), with several
-    chunks and sub-tiles per block, ragged tiles and the bench's size."""
+    """hot_set_block_merge: the GSW step with the schedule's blocks merged four or two to a
+    launched block computes the same bits as separate blocks (and as the persistent kernel), with
+    several chunks and sub-tiles per block, ragged tiles and the bench's size."""
     w = wl.random_case(W, H, M, seed=W + H, precision=precision)
     out = []
-    for merge, persistent in ((0, False), (1, False), (1, True)):
+    for merge, persistent in ((1, False), (4, False), (2, False), (4, True)):
         with make(hot, w) as h:
             h.set_block_merge(merge)
             h.use_persistent(persistent)
-            assert h.tiling()["merge"] == bool(merge and h.tiling()["blocks_per_sm"] == 4)
+            assert h.tiling()["merge"] == (merge if h.tiling()["blocks_per_sm"] == 4 else 1)
             eu = h.gsw(3)
             out.append((h.phase("f32"), *h.fields(), eu))
     for p, V, wt, eu in out[1:]:
         assert np.array_equal(out[0][0], p) and np.array_equal(out[0][1], V) and np.array_equal(out[0][2], wt)
         assert eu == out[0][3]
     with make(hot, w) as h:
-        assert hot.lib.hot_set_block_merge(h.ctx, 2) == hot.HOT_EINVAL
+        assert hot.lib.hot_set_block_merge(h.ctx, 3) == hot.HOT_EINVAL
