@@ -62,8 +62,8 @@ def parse():
                     help="efficiency and uniformity vs trap count on n x n grids (n = 2..9, 768^2 SLM)")
     ap.add_argument("--single", type=int, default=0, metavar="K",
                     help="run hot_gsw(K) once on the workload and print e, u (no timing; for profilers)")
-    ap.add_argument("--merge", action="store_true",
-                    help="with --single: run the GSW step as one block per SM holding four schedule blocks "
+    ap.add_argument("--merge", type=int, default=1, choices=[1, 2, 4],
+                    help="with --single: schedule blocks per launched block of the GSW step "
                          "(hot_set_block_merge; the timed runs let the autotuner choose)")
     ap.add_argument("--cpu-sample-iters", type=int, default=0,
                     help="GSW iterations of the CPU-baseline sample (0: the workload's own count)")
@@ -880,8 +880,8 @@ def run_single(args):
     if args.precision:
         w.precision = args.precision
     with hot.Hologram.from_workload(w, torch.cuda.current_stream().cuda_stream) as h:
-        if args.merge:
-            h.set_block_merge(True)
+        if args.merge > 1:
+            h.set_block_merge(args.merge)
         e, u = h.gsw(args.single)
         print(json.dumps({"workload": w.name, "precision": w.precision, "iters": args.single, "e": e, "u": u,
                           "kernels": h.launches, "tiling": h.tiling()}), flush=True)
