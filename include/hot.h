@@ -282,10 +282,29 @@ int hot_get_tiling(const hot_ctx *c, int *rows, int *blocks_per_sm, int *chunk);
 int hot_set_block_merge(hot_ctx *c, int merge);
 int hot_get_block_merge(const hot_ctx *c, int *requested, int *in_effect);
 
+/* One-exponential step of the accurate and fast modes (no counterpart in the paper's kernel;
+ * the same sums, Eq. 1 and Sec. 3): with M <= 128 traps the GSW step evaluates each pixel-trap
+ * exponential E = e^{i Delta_j^m} (Eq. 2) once per iteration and keeps it in registers between
+ * the back-projection S_j = sum_m c_m E and the forward field N V_m = sum_j e^{i phi_j} conj(E),
+ * which halves the cos/sin work of an iteration.  Its blocks split the M traps among their warps
+ * (at most 16 traps per warp, so at most 128 traps) and walk sub-tiles of 2 to 8 rows (fixed by
+ * M); its schedule is its own, so the tiling above does not apply to it (it still applies to the
+ * adjoint and the superposition, which keep the direct kernels).  The forward field of given
+ * phases (the first launch of hot_gsw, hot_field) uses the same arithmetic, so resumed
+ * sequences, CUDA graphs and the persistent form give the same bits.  Its results differ from
+ * the direct kernels' by FP32 rounding.  on: 1 (default) or 0, else HOT_EINVAL; it is in effect
+ * where M <= 128 and the mode is HOT_PREC_ACCURATE or HOT_PREC_FAST.  Rebuilds the schedule;
+ * synchronises the context's stream.  hot_get_once reports the setting and whether it is in
+ * effect. */
+int hot_set_once(hot_ctx *c, int on);
+int hot_get_once(const hot_ctx *c, int *requested, int *in_effect);
+
 /* Autotuner: times hot_gsw(iters) (CUDA events, best of 3 graph replays) for candidate tilings
  * by coordinate search over rows, blocks_per_sm (with block merging, hot_set_block_merge, as a
  * candidate in the accurate and fast modes) and chunk, keeps the fastest, and reports it
- * with its time per iteration in microseconds (outputs may be NULL).  The phases and weights
+ * with its time per iteration in microseconds (outputs may be NULL).  Where the one-exponential
+ * step is requested and applies (hot_set_once), it is timed too and kept if it is faster than
+ * the best tiling of the direct kernels; otherwise the setting is turned off (hot_get_once).  The phases and weights
  * are restored afterwards; the fields are stale until the next forward evaluation (HOT_ESTATE
  * from hot_get_fields).  Synchronises.  HOT_ESTATE before hot_set_traps; iters >= 1. */
 int hot_autotune(hot_ctx *c, int iters, int *rows, int *blocks_per_sm, int *chunk, double *us_per_iter);

@@ -9,8 +9,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libhot.so")
-SOURCES = [os.path.join(CSRC, "hot.cu"), os.path.join(CSRC, "tc.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("gsw_kernels.cuh", "tc_kernels.cuh", "tc.h")] + \
+SOURCES = [os.path.join(CSRC, f) for f in ("hot.cu", "tc.cu", "once.cu")]
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("gsw_kernels.cuh", "tc_kernels.cuh", "tc.h", "once.h")] + \
     [os.path.join(ROOT, "include", "hot.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -206,6 +206,11 @@ __device__ __forceinline__ int vgrid() { return gridDim.x * (blockDim.x / kThrea
 __device__ __forceinline__ void group_sync() {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + group_id()), "n"(kThreads) : "memory");
 }
+// The same barrier for warps that reach it at different instructions (code specialised per
+// warp): the non-aligned form, which PTX allows there.
+__device__ __forceinline__ void group_sync_any() {
+  asm volatile("barrier.sync %0, %1;" ::"r"(1 + group_id()), "n"(kThreads) : "memory");
+}
 
 // Traps [lo, hi) of a staged chunk of n that warp `warp` of a group takes.  Warps w and w + 4
 // issue to the same SM sub-partition (warp slot mod 4) and share its special-function unit, so
@@ -237,13 +242,17 @@ __device__ __forceinline__ unsigned long long *block_acc(const StepArgs &a) {
   return a.acc_out + (size_t)((unsigned)vblock() & (unsigned)(a.copies - 1)) * 2 * a.M;
 }
 
+// |v|^2 with its rounding fixed in the source (v.y^2 rounded, then one fused multiply-add), so
+// that every kernel that inlines it computes the same bits whatever the compiler would fuse.
+__device__ __forceinline__ float abs2(float2 v) { return fmaf(v.x, v.x, v.y * v.y); }
+
 // Sec. 3 weight update and back-projection coefficient of a trap with field v and weight w:
 // w <- w <|V|>/|V_m|; if |V_m| < 1e-30 the unit field is 1 and w stays.  Polar form
 // (w', arg V_m in table units: times units, plus eta of itself), or complex form w' V_m/|V_m|
 // (COMPLEX).
 template <bool COMPLEX>
 __device__ __forceinline__ float2 update_from(float2 v, float w, float mean, float units, float eta = 0.f) {
-  const float am = sqrtf(v.x * v.x + v.y * v.y);
+  const float am = sqrtf(abs2(v));
   if (COMPLEX) {
     if (am < 1e-30f) return make_float2(w, 0.f);
     const float s = w * mean / (am * am);
@@ -264,7 +273,7 @@ __device__ __forceinline__ float2 coefficient(const StepArgs &a, int m, float me
 __device__ __forceinline__ float2 adjoint_coefficient(const StepArgs &a, int m) {
   const float2 g = a.G[m];
   const float ang = atan2f(g.y, g.x);
-  return make_float2(sqrtf(g.x * g.x + g.y * g.y), fmaf(ang, a.angle_eta, ang * a.angle_units));
+  return make_float2(sqrtf(abs2(g)), fmaf(ang, a.angle_eta, ang * a.angle_units));
 }
 
 // Stages, with asynchronous copies (all in flight at once), the X (32 columns from x0) and Y
@@ -513,9 +522,9 @@ __device__ __forceinline__ void gsw_prologue(const StepArgs &a, int mc, float2 *
   for (int m = t; m < a.M; m += kThreads) {
     const float2 v = field_from_sums<COMPLEX>(a, m);
     if (m == t) v0 = v;
-    s = ff_add(s, {sqrtf(v.x * v.x + v.y * v.y), 0.f});
+    s = ff_add(s, {sqrtf(abs2(v)), 0.f});
     if (tr) {
-      const float I = v.x * v.x + v.y * v.y;
+      const float I = abs2(v);
       si = ff_add(si, {I, 0.f});
       mx = fmaxf(mx, I);
       mn = fminf(mn, I);
@@ -645,13 +654,13 @@ __device__ __forceinline__ void finalize_block(const FinalizeArgs &a) {
   }
 }
 
-__global__ void __launch_bounds__(kFinalizeThreads) gsw_finalize_kernel(FinalizeArgs a) {
+static __global__ void __launch_bounds__(kFinalizeThreads) gsw_finalize_kernel(FinalizeArgs a) {
   grid_dependency_wait();
   finalize_block(a);
 }
 
 // Batched: block h finalizes hologram h and stamps its completion time.
-__global__ void __launch_bounds__(kFinalizeThreads) gsw_finalize_batch_kernel(const FinalizeArgs *args) {
+static __global__ void __launch_bounds__(kFinalizeThreads) gsw_finalize_batch_kernel(const FinalizeArgs *args) {
   grid_dependency_wait();
   const FinalizeArgs &a = args[blockIdx.x];
   finalize_block(a);
@@ -830,7 +839,7 @@ __global__ void __launch_bounds__(kThreads * GROUPS, kMaxGroups / GROUPS) gsw_st
 }
 
 // Start stamp of a batched sequence (%globaltimer, ns).
-__global__ void stamp_kernel(unsigned long long *t) { *t = global_timer_ns(); }
+static __global__ void stamp_kernel(unsigned long long *t) { *t = global_timer_ns(); }
 
 // The trap-intensity loss of the differentiable form and its adjoint coefficients, from the
 // forward field's fixed-point sums: I_m = |V_m|^2 (the intensities of Eq. 4),
@@ -865,7 +874,7 @@ __device__ __forceinline__ double block_sum(double v, double *part) {
   return t;
 }
 
-__global__ void __launch_bounds__(kLossThreads) intensity_loss_kernel(LossArgs a) {
+static __global__ void __launch_bounds__(kLossThreads) intensity_loss_kernel(LossArgs a) {
   __shared__ double part[kLossThreads / 32];
   __shared__ float ext[2][kLossThreads / 32];
   double sI = 0.0, sLog = 0.0;
@@ -919,6 +928,373 @@ __global__ void __launch_bounds__(kLossThreads) intensity_loss_kernel(LossArgs a
     a.metrics[0] = (float)e;
     a.metrics[1] = (hi + lo > 0.f) ? 1.f - (hi - lo) / (hi + lo) : 0.f;
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// One-exponential step (direct modes, M <= kOnceMaxM traps).  The back-projection and the
+// forward field of an iteration use the same pair exponentials E_j^m = e^{i Delta_j^m}:
+//   S_j = sum_m c_m E_j^m,  c_m = w_m V_m/|V_m|      (back-projection, Sec. 3)
+//   u_j = e^{i arg S_j}                              (the new phase, phi_j = arg S_j)
+//   N V_m = sum_j u_j conj(E_j^m)                    (forward field, Eq. 1).
+// A thread keeps the exponentials of its pixels and traps in registers between the two sums,
+// so each pair costs one cos/sin per iteration instead of two.  The 8 warps of a block split
+// the traps (warp_traps over all M, at most TMAX each, fixed for the launch); lane l holds
+// column x0 + l of a sub-tile of at most R rows.  All M traps' tables of a sub-tile are staged
+// in shared memory at once (the column parts once per 32-pixel strip), one sub-tile ahead.  A thread's forward sums stay in registers
+// over all of the block's sub-tiles; they are summed over the warp and added, in fixed point,
+// once at the end.  The forward-only variant (the field of given phases) evaluates the same
+// expressions in the same order, so a sequence resumed from stored phases gives the same bits.
+constexpr int kOnceMaxM = 128;
+constexpr int kOnceTMax = 16;  // traps per warp at most (8 warps x 16 = kOnceMaxM)
+
+// Floats per trap in a staged block of row parts (R rows, in 16-byte pieces).
+__host__ __device__ constexpr int once_yw(int R) { return (R + 3) & ~3; }
+
+// Shared memory of a block: the coefficients, the row parts of two sub-tiles and the column
+// parts of two strips (the next ones are staged during the current sub-tile), the warps'
+// partial superpositions and the unit phasors u_j.
+__host__ __device__ constexpr int once_smem_bytes(int R) {
+  return kOnceMaxM * 8 + kWarps * kOnceTMax * 8 + 2 * kOnceMaxM * once_yw(R) * 4 + 2 * kOnceMaxM * kTileW * 4 +
+         kWarps * R * kTileW * 8 + R * kTileW * 8;
+}
+
+struct OnceSmem {
+  float2 *C;   // [kOnceMaxM] complex coefficients (gsw_prologue<true>)
+  float2 *Cw;  // [kWarps][kOnceTMax] each warp's coefficients, zero past its traps
+  float *Yb;   // [2][kOnceMaxM][once_yw(R)] row parts of a sub-tile's rows, by trap
+  float *Xb;   // [2][kOnceMaxM][kTileW] column parts of a strip, by trap
+  float2 *Sp;  // [kWarps][R][kTileW] per-warp superpositions
+  float2 *Ps;  // [R][kTileW] unit phasors of the sub-tile's pixels (0 outside the image)
+  int yw;
+  __device__ __forceinline__ OnceSmem(unsigned char *raw, int R) {
+    yw = once_yw(R);
+    C = reinterpret_cast<float2 *>(raw);
+    Cw = C + kOnceMaxM;
+    Yb = reinterpret_cast<float *>(Cw + kWarps * kOnceTMax);
+    Xb = Yb + 2 * kOnceMaxM * yw;
+    Sp = reinterpret_cast<float2 *>(Xb + 2 * kOnceMaxM * kTileW);
+    Ps = Sp + kWarps * R * kTileW;
+  }
+  __device__ __forceinline__ float *rows(int buf) const { return Yb + buf * kOnceMaxM * yw; }
+  __device__ __forceinline__ float *cols(int buf) const { return Xb + buf * kOnceMaxM * kTileW; }
+};
+
+// Issues the asynchronous copies of the column parts X_m(x0 .. x0 + 31) of every trap into Xb
+// (16-byte pieces when the strip lies inside the image and W is a multiple of 4; zero past the
+// right edge otherwise).  Not committed.
+__device__ __forceinline__ void once_stage_columns(const StepArgs &a, int x0, float *Xb) {
+  if ((a.W & 3) == 0 && x0 + kTileW <= a.W) {
+    for (int i = gthread(); i < a.M * (kTileW / 4); i += kThreads) {
+      const int k = i >> 3, q = i & 7;
+      cp_async16(Xb + k * kTileW + 4 * q, a.X + (size_t)k * a.W + x0 + 4 * q);
+    }
+  } else {
+    for (int i = gthread(); i < a.M * kTileW; i += kThreads) {
+      const int k = i / kTileW, col = x0 + (i % kTileW);
+      const bool ok = col < a.W;
+      cp_async4(Xb + i, a.X + (ok ? (size_t)k * a.W + col : 0), ok);
+    }
+  }
+}
+
+// Issues the asynchronous copies of the row parts Y_m(y0 .. y0 + R - 1) of every trap into Yb
+// (once_yw(R) floats per trap, 16-byte pieces of the aligned shifted copy when there is one).
+// Not committed.
+template <int R>
+__device__ __forceinline__ void once_stage_rows(const StepArgs &a, const SubTile &st, float *Yb) {
+  constexpr int YW = once_yw(R), Q = YW / 4;
+  if (a.Y4) {
+    const int s = (4 - (st.y0 & 3)) & 3;
+    const float *src = a.Y4 + (size_t)s * a.M * a.ldy4 + st.y0 + s;
+    for (int i = gthread(); i < a.M * Q; i += kThreads) {
+      const int k = i / Q, q = i % Q;
+      cp_async16(Yb + k * YW + 4 * q, src + (size_t)k * a.ldy4 + 4 * q);
+    }
+  } else {
+    for (int i = gthread(); i < a.M * YW; i += kThreads) {
+      const int k = i / YW, r = i % YW;
+      const bool ok = r < st.rows;
+      cp_async4(Yb + i, a.Y + (ok ? (size_t)k * a.H + st.y0 + r : 0), ok);
+    }
+  }
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// u = e^{i phi} of a phase reduced to one turn in table units: radians in [-pi, pi] (fast,
+// scaled by 1 + kFastEta here like the tables) or turns in [-1/2, 1/2] (accurate).
+template <bool FAST>
+__device__ __forceinline__ float2 unit_phasor(float ph) {
+  float s, c;
+  if (FAST) {
+    const float x = fmaf(ph, kFastEta, ph);
+    s = sin_approx(x);
+    c = cos_approx(x);
+  } else {
+    sincospif(2.0f * ph, &s, &c);
+  }
+  return make_float2(c, s);
+}
+
+// Back-projection of a warp's TV traps (tables and coefficients from Xs, Yb, Cw, trap by trap)
+// onto the lane's R rows: E[k][r] = e^{i (X + Y)} (kept), S[r] += c_k E[k][r].  All R rows are
+// evaluated (no per-row branches): the rows past a short sub-tile's end are staged rows of the
+// next sub-tile or zero padding, and their results are discarded.
+template <bool FAST, int TV, int TMAX, int R>
+__device__ __forceinline__ void once_back(const float *Xs, const float *Yb, const float2 *Cw, int lane,
+                                          float2 (&E)[TMAX][R], float2 (&S)[R]) {
+  constexpr int YW = once_yw(R);
+#pragma unroll
+  for (int k = 0; k < TV; k++) {
+    const float2 c = Cw[k];
+    const float xk = Xs[k * kTileW + lane];
+    const float4 *yq = reinterpret_cast<const float4 *>(Yb + k * YW);
+#pragma unroll
+    for (int q = 0; q < YW / 4; q++) {
+      const float4 y4 = yq[q];
+      const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const int r = 4 * q + j;
+        if (r < R) {
+          float co, si;
+          cis<FAST>(xk + yy[j], co, si);
+          E[k][r] = make_float2(co, si);
+          S[r].x = fmaf(c.x, co, fmaf(-c.y, si, S[r].x));
+          S[r].y = fmaf(c.x, si, fmaf(c.y, co, S[r].y));
+        }
+      }
+    }
+  }
+}
+
+// acc[k] += u_r conj(E[k][r]) over the lane's R rows (u_r = 0 past the sub-tile's end).
+template <int TV, int TMAX, int R>
+__device__ __forceinline__ void once_accumulate(const float2 (&P)[R], const float2 (&E)[TMAX][R],
+                                                float2 (&acc)[TMAX]) {
+#pragma unroll
+  for (int k = 0; k < TV; k++) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      acc[k].x = fmaf(P[r].x, E[k][r].x, fmaf(P[r].y, E[k][r].y, acc[k].x));
+      acc[k].y = fmaf(P[r].y, E[k][r].x, fmaf(-P[r].x, E[k][r].y, acc[k].y));
+    }
+  }
+}
+
+// Forward field of given phases: the exponentials of the back-projection's expression, then the
+// same accumulation (trap by trap, one trap's rows at a time).
+template <bool FAST, int TV, int TMAX, int R>
+__device__ __forceinline__ void once_forward_only(const float *Xs, const float *Yb, const float2 (&P)[R], int lane,
+                                                  float2 (&acc)[TMAX]) {
+  constexpr int YW = once_yw(R);
+#pragma unroll
+  for (int k = 0; k < TV; k++) {
+    float2 E[1][R];
+    const float xk = Xs[k * kTileW + lane];
+    const float4 *yq = reinterpret_cast<const float4 *>(Yb + k * YW);
+#pragma unroll
+    for (int q = 0; q < YW / 4; q++) {
+      const float4 y4 = yq[q];
+      const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const int r = 4 * q + j;
+        if (r < R) cis<FAST>(xk + yy[j], E[0][r].x, E[0][r].y);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      acc[k].x = fmaf(P[r].x, E[0][r].x, fmaf(P[r].y, E[0][r].y, acc[k].x));
+      acc[k].y = fmaf(P[r].y, E[0][r].x, fmaf(-P[r].x, E[0][r].y, acc[k].y));
+    }
+  }
+}
+
+// The sub-tiles of a block, for a warp whose traps lo .. lo + T - 1 are evaluated as TV traps
+// (T <= TV; the rest are padding: zero coefficients, their sums dropped), then the warp's
+// forward sums, totalled over its lanes in a fixed order and added in fixed point.  Warps of
+// one block may run copies of this loop for different TV: its barriers are non-aligned.
+template <bool FAST, bool BACK, int TV, int R>
+__device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm, int t_begin, int t_end, int lo,
+                                          int T) {
+  const int lane = threadIdx.x & 31, warp = gthread() >> 5, t = gthread();
+  constexpr int YW = once_yw(R);
+  float2 acc[TV];
+#pragma unroll
+  for (int k = 0; k < TV; k++) acc[k] = make_float2(0.f, 0.f);
+  int xb = 0;  // the buffer of the current strip's column parts
+  for (int i = t_begin; i < t_end; i++) {
+    const SubTile st = a.sub[i];
+    const int buf = (i - t_begin) & 1;
+    if (!BACK) group_sync_any();  // the previous sub-tile's readers of Ps and of the other buffers are done
+    bool next_strip = false;
+    if (i + 1 < t_end) {  // stage the next sub-tile's tables
+      const SubTile nx = a.sub[i + 1];
+      once_stage_rows<R>(a, nx, sm.rows(buf ^ 1));
+      next_strip = nx.x0 != st.x0;
+      if (next_strip) once_stage_columns(a, nx.x0, sm.cols(xb ^ 1));
+    }
+    cp_async_commit();  // (an empty group after the last sub-tile: uniform waits)
+    const float *Xs = sm.cols(xb) + lo * kTileW, *Yb = sm.rows(buf) + lo * YW;
+    float2 E[TV][R];
+    if (BACK) {
+      float2 S[R];
+#pragma unroll
+      for (int r = 0; r < R; r++) S[r] = make_float2(0.f, 0.f);
+      once_back<FAST, TV, TV, R>(Xs, Yb, sm.Cw + warp * kOnceTMax, lane, E, S);
+#pragma unroll
+      for (int r = 0; r < R; r++)
+        if (r < st.rows) sm.Sp[(warp * R + r) * kTileW + lane] = S[r];
+      group_sync_any();
+      if (t < st.rows * kTileW) {  // one pixel per thread: the 8 warps' sums in warp order
+        const int r = t >> 5, l = t & 31, ix = st.x0 + l;
+        float2 s = sm.Sp[r * kTileW + l];
+#pragma unroll
+        for (int w = 1; w < kWarps; w++) {
+          const float2 q = sm.Sp[(w * R + r) * kTileW + l];
+          s.x += q.x;
+          s.y += q.y;
+        }
+        const float ph = atan2f(s.y, s.x);
+        if (ix < a.W) a.phi[(size_t)(st.y0 + r) * a.W + ix] = ph;
+        sm.Ps[r * kTileW + l] = ix < a.W ? unit_phasor<FAST>(FAST ? ph : phase_turns(ph)) : make_float2(0.f, 0.f);
+      }
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // the next sub-tile's tables
+    } else {
+      if (t < st.rows * kTileW) {
+        const int r = t >> 5, l = t & 31, ix = st.x0 + l;
+        const float ph = ix < a.W ? a.phi[(size_t)(st.y0 + r) * a.W + ix] : 0.f;
+        sm.Ps[r * kTileW + l] =
+            ix < a.W ? unit_phasor<FAST>(FAST ? reduced_radians(ph) : reduced_phase_turns(ph)) : make_float2(0.f, 0.f);
+      }
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this sub-tile's tables
+    }
+    group_sync_any();
+    float2 P[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) P[r] = r < st.rows ? sm.Ps[r * kTileW + lane] : make_float2(0.f, 0.f);
+    if (BACK)
+      once_accumulate<TV, TV, R>(P, E, acc);
+    else
+      once_forward_only<FAST, TV, TV, R>(Xs, Yb, P, lane, acc);
+    if (next_strip) xb ^= 1;
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  unsigned long long *const out = block_acc(a);
+#pragma unroll
+  for (int g = 0; g < TV; g += kGroup) {
+    float2 v8[kGroup];
+#pragma unroll
+    for (int i = 0; i < kGroup; i++) v8[i] = g + i < TV ? acc[g + i] : make_float2(0.f, 0.f);
+    const float2 v = warp_reduce8(v8, lane);
+    const int k = g + ((lane >> 2) & 7);
+    if ((lane & 3) == 0 && k < T) {
+      // |v| <= the block's pixel count <= N, so v * 2^fx_shift is an exact integer below 2^62
+      atomicAdd(out + lo + k, (unsigned long long)__float2ll_rn(v.x * a.fx_scale));
+      atomicAdd(out + a.M + lo + k, (unsigned long long)__float2ll_rn(v.y * a.fx_scale));
+    }
+  }
+}
+
+// The work of one block on its sub-tiles [t_begin, t_end) after the dependency wait and the
+// clearing of the next accumulator.  On entry the first sub-tile's row and column parts are
+// being staged into rows(0) and cols(0) (one committed group).
+// BACK: weight update, back-projection -> a.phi, forward field of the new phases; otherwise
+// the forward field of the phases in a.phi.
+// A warp's trap count T is TMAX or less (warp_traps); it runs the loop compiled for TMAX traps,
+// or for TMAX - 1 traps with any remaining ones as padding, so that no per-trap branch remains.
+template <bool FAST, bool BACK, int TMAX, int R>
+__device__ __forceinline__ void once_block(const StepArgs &a, const OnceSmem &sm, int t_begin, int t_end,
+                                           float *trace) {
+  static_assert(TMAX >= 2 && TMAX <= kOnceTMax, "traps per warp");
+  const int lane = threadIdx.x & 31, warp = gthread() >> 5;
+  int lo, hi;
+  warp_traps(a.M, warp, lo, hi);
+  const int T = hi - lo;
+  if (BACK) {  // the weights are written here, before the sub-tiles: nothing stays live across them
+    LateWeight lw;
+    gsw_prologue<true>(a, a.M, sm.C, vblock(), vgrid(), lw, trace);
+    write_weights<true>(a, lw, vgrid());
+  }
+  // Padding traps read table rows from M on (never staged): zero, in both buffers.
+  for (int i = gthread(); i < 2 * kOnceTMax * (kTileW + sm.yw); i += kThreads) {
+    const int b = i / (kOnceTMax * (kTileW + sm.yw)), j = i % (kOnceTMax * (kTileW + sm.yw));
+    if (j < kOnceTMax * kTileW) {
+      if (a.M * kTileW + j < kOnceMaxM * kTileW) sm.cols(b)[a.M * kTileW + j] = 0.f;
+    } else if (a.M * sm.yw + (j - kOnceTMax * kTileW) < kOnceMaxM * sm.yw) {
+      sm.rows(b)[a.M * sm.yw + (j - kOnceTMax * kTileW)] = 0.f;
+    }
+  }
+  if (BACK) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    group_sync();  // coefficients, padding and the first tables are in place
+    if (lane < kOnceTMax) sm.Cw[warp * kOnceTMax + lane] = lane < T ? sm.C[lo + lane] : make_float2(0.f, 0.f);
+    __syncwarp();
+  }
+  if (T == TMAX)
+    once_loop<FAST, BACK, TMAX, R>(a, sm, t_begin, t_end, lo, T);
+  else
+    once_loop<FAST, BACK, TMAX - 1, R>(a, sm, t_begin, t_end, lo, T);
+}
+
+// Stages the first sub-tile's tables of a block (one committed group; empty without work).
+template <int R>
+__device__ __forceinline__ void once_stage_first(const StepArgs &a, const OnceSmem &sm, int t_begin, int t_end) {
+  if (t_begin < t_end) {
+    const SubTile st0 = a.sub[t_begin];
+    once_stage_rows<R>(a, st0, sm.rows(0));
+    once_stage_columns(a, st0.x0, sm.cols(0));
+  }
+  cp_async_commit();
+}
+
+// Calls BODY with compile-time TMAX (traps per warp at most) and R (rows per sub-tile) of a
+// shape index (once_shape): a warp holds 2 TMAX R floats of exponentials and 2 TMAX of sums.
+#define HOT_WITH_ONCE_SHAPE(shape, BODY)                     \
+  switch (shape) {                                           \
+    case 1: { constexpr int TMAX = 2, R = 8; BODY; } break;  \
+    case 2: { constexpr int TMAX = 4, R = 8; BODY; } break;  \
+    case 3: { constexpr int TMAX = 6, R = 6; BODY; } break;  \
+    case 4: { constexpr int TMAX = 8, R = 4; BODY; } break;  \
+    case 5: { constexpr int TMAX = 10, R = 4; BODY; } break; \
+    case 6: { constexpr int TMAX = 12, R = 3; BODY; } break; \
+    case 7: { constexpr int TMAX = 13, R = 3; BODY; } break; \
+    case 8: { constexpr int TMAX = 14, R = 2; BODY; } break; \
+    default: { constexpr int TMAX = 16, R = 2; BODY; } break; \
+  }
+
+// The shape for M traps (0: none, M > kOnceMaxM): the smallest TMAX >= ceil(M / 8), so that a
+// warp's count (floor(M / 8) or ceil(M / 8), warp_traps) is TMAX, TMAX - 1 or TMAX - 2.
+__host__ __device__ constexpr int once_shape(int M) {
+  return M <= 0 || M > kOnceMaxM ? 0
+         : M <= 16              ? 1
+         : M <= 32              ? 2
+         : M <= 48              ? 3
+         : M <= 64              ? 4
+         : M <= 80              ? 5
+         : M <= 96              ? 6
+         : M <= 104             ? 7
+         : M <= 112             ? 8
+                                : 9;
+}
+__host__ __device__ constexpr int once_rows(int shape) {
+  return shape <= 2 ? 8 : shape == 3 ? 6 : shape <= 5 ? 4 : shape <= 7 ? 3 : 2;
+}
+
+// The per-launch form.  The tables are constant during hot_gsw: the first sub-tile's are
+// staged before waiting for the previous launch.
+template <bool FAST, bool BACK, int TMAX, int R>
+__global__ void __launch_bounds__(kThreads, 2) gsw_once_kernel(StepArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const OnceSmem sm(smem_raw, R);
+  const int vb = vblock(), vg = vgrid();
+  const int t_begin = a.first[vb], t_end = a.first[vb + 1];
+  allow_dependents();
+  once_stage_first<R>(a, sm, t_begin, t_end);
+  grid_dependency_wait();
+  for (int i = vb * kThreads + gthread(); i < 2 * a.M * a.copies; i += vg * kThreads) a.acc_clear[i] = 0ull;
+  once_block<FAST, BACK, TMAX, R>(a, sm, t_begin, t_end, a.trace);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1347,6 +1723,26 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)
   }
 }
 
+// The persistent form of the one-exponential step (same schedule, same arithmetic, same bits).
+template <bool FAST, int TMAX, int R>
+__global__ void __launch_bounds__(kThreads, 2) gsw_once_persistent_kernel(const __grid_constant__ PersistArgs p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const OnceSmem sm(smem_raw, R);
+  const StepArgs &a0 = p.step[0];
+  const int t_begin = a0.first[blockIdx.x], t_end = a0.first[blockIdx.x + 1];
+  unsigned int epoch = 0u;
+  for (int k = 0; k <= p.iters; k++) {
+    const StepArgs &a = p.step[k % 6];
+    if (k > 0 && !grid_sync(p.sync, epoch)) return;
+    once_stage_first<R>(a, sm, t_begin, t_end);
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M * a.copies; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
+    if (k == 0)
+      once_block<FAST, false, TMAX, R>(a, sm, t_begin, t_end, nullptr);
+    else
+      once_block<FAST, true, TMAX, R>(a, sm, t_begin, t_end, p.trace ? p.trace + 2 * (k - 1) : nullptr);
+  }
+}
+
 // Per (trap, column) and (trap, row) phase parts of Eq. 2 reduced modulo one turn in FP64.
 // abc: [M][3] = a_m, b_m, c_m in turns (see the file header).  Writes turns and radians.
 // A row band (rows y_off .. y_off+H-1 of a hologram of H_total rows) takes the row parts of
@@ -1354,7 +1750,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeSeparable ? 2 : 4)
 // Y4t, Y4r (optional): the shifted copies of the row parts (StepArgs::Y4), [4][M][ldy4], and
 // Yc2 (optional) the two shifted copies of Yc (StepArgs::Yc), [2][M][ldy4], whose entries outside
 // the shifted rows stay as they are (zero from allocation).
-__global__ void build_tables_kernel(int W, int H, int H_total, int y_off, int M, const double *abc, float *Xt,
+static __global__ void build_tables_kernel(int W, int H, int H_total, int y_off, int M, const double *abc, float *Xt,
                                     float *Yt, float *Xr, float *Yr, float2 *Xc, float2 *Yc, float *Y4t = nullptr,
                                     float *Y4r = nullptr, int ldy4 = 0, float2 *Yc2 = nullptr) {
   const long long total = (long long)M * (W + H);
@@ -1395,13 +1791,13 @@ __global__ void build_tables_kernel(int W, int H, int H_total, int y_off, int M,
 }
 
 // Fixed-point field sums -> float32 complex fields V_m (for callers of hot_field).
-__global__ void sums_to_fields_kernel(int M, const long long *Vsum, double inv, float2 *V) {
+static __global__ void sums_to_fields_kernel(int M, const long long *Vsum, double inv, float2 *V) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m < M) V[m] = make_float2((float)((double)Vsum[m] * inv), (float)((double)Vsum[M + m] * inv));
 }
 
 // Sec. 5 encoding of the phases: uint8 g = rint(phi 256 / 2pi) mod 256 (FP32 decision).
-__global__ void quantize_kernel(const float *phi, unsigned char *g, long long n) {
+static __global__ void quantize_kernel(const float *phi, unsigned char *g, long long n) {
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
        j += (long long)gridDim.x * blockDim.x) {
     const float q = rintf(phi[j] * (256.0f / kTwoPi));

@@ -12,6 +12,7 @@
 
 #include "../../include/hot.h"
 #include "gsw_kernels.cuh"
+#include "once.h"
 #include "tc.h"
 
 namespace {
@@ -73,6 +74,13 @@ struct hot_ctx {
   int sched_bps = 0, sched_bps_max = 0;  // resident blocks per SM in the schedule; occupancy limit
   int tile_merge = 1;  // hot_set_block_merge: schedule blocks per launched block of the GSW step (1, 2, 4)
   int groups = 1;      // schedule blocks per launched block of the direct GSW step (1 or 4)
+  // one-exponential step of the direct modes (hot_set_once; M <= hot::kOnceMaxM): requested,
+  // shape in effect (hot::once_shape; 0: the direct step kernels) and its own schedule
+  bool once_req = true;
+  int once = 0;
+  hot::SubTile *osub = nullptr;  // [on_sub]
+  int *ofirst = nullptr;         // [ogrid + 1]
+  int ogrid = 0, on_sub = 0;
   int shard_k = -1;                      // last launch of a sharded sequence (hot_sharded_*)
   // state
   float *phi = nullptr;  // [N]
@@ -301,11 +309,34 @@ int launch_sep(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const fl
   return check_launch(c, "gsw_sep_kernel");
 }
 
+// The one-exponential step (BACK: weight update, back-projection and forward field) or its
+// forward field of given phases, on the context's one-exponential schedule.
+template <bool BACK>
+int launch_once(hot_ctx *c, bool pdl, int k, const float *phi) {
+  hot::StepArgs a = make_step_args(c, k, phi, nullptr, nullptr);
+  a.sub = c->osub;
+  a.first = c->ofirst;
+  a.chunk = c->M;
+  Probe p(c, BACK ? HOT_KERNEL_STEP : HOT_KERNEL_FORWARD);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c->ogrid);
+  cfg.blockDim = dim3(hot::kThreads);
+  cfg.stream = c->st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  hot_once::launch_step(c->once, c->precision == HOT_PREC_FAST, BACK, cfg, a);
+  return check_launch(c, "gsw_once_kernel");
+}
+
 // The step kernel of the context's mode (accurate / fast direct evaluation, or separable).
 template <bool BACK, bool FWD, bool ADJ = false>
 int launch_mode(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const float2 *G = nullptr,
                 float *grad = nullptr) {
   if (separable_kernels(c)) return launch_sep<BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
+  if (c->once && FWD && !ADJ && !G) return launch_once<BACK>(c, pdl, k, phi);
   if (c->precision == HOT_PREC_FAST) return launch_tile<true, BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
   return launch_tile<false, BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
 }
@@ -336,9 +367,68 @@ int set_step_smem(int M) {
   return HOT_OK;
 }
 
+// The W/32 x H row segments dealt out to G blocks in equal contiguous runs (to within one
+// segment), each run cut into sub-tiles of at most `rows` rows -- evenly, or (full) into
+// sub-tiles of exactly `rows` rows and one shorter remainder; block b walks sub-tiles
+// first[b] .. first[b + 1] - 1.
+void cut_schedule(int W, int H, int G, int rows, std::vector<hot::SubTile> &sub, std::vector<int> &first,
+                  bool full = false) {
+  const int strips = (W + hot::kTileW - 1) / hot::kTileW;
+  const long long U = (long long)strips * H;
+  sub.clear();
+  first.assign(G + 1, 0);
+  for (int b = 0; b < G; b++) {
+    first[b] = (int)sub.size();
+    long long s = U * b / G;
+    const long long s1 = U * (b + 1) / G;
+    while (s < s1) {
+      const int strip = (int)(s / H), row = (int)(s % H);
+      const long long run_end = std::min<long long>(s1, (long long)(strip + 1) * H);
+      const int L = (int)(run_end - s);
+      const int nsub = (L + rows - 1) / rows;
+      for (int i = 0; i < nsub; i++) {
+        const int r0 = row + (full ? i * rows : (int)((long long)L * i / nsub));
+        const int r1 = full ? std::min(r0 + rows, row + L) : row + (int)((long long)L * (i + 1) / nsub);
+        sub.push_back({strip * hot::kTileW, r0, r1 - r0, 0});
+      }
+      s = run_end;
+    }
+  }
+  first[G] = (int)sub.size();
+}
+
+// The one-exponential step's schedule (one wave of its blocks, sub-tiles of its R rows), when
+// the context's mode and trap count allow it and it is requested; otherwise c->once = 0.
+int build_once_schedule(hot_ctx *c, int sms) {
+  c->once = 0;
+  c->ogrid = 0;
+  c->on_sub = 0;
+  dfree(c->osub);
+  dfree(c->ofirst);
+  const int shape = hot::once_shape(c->M);
+  if (!c->once_req || !shape || (c->precision != HOT_PREC_FAST && c->precision != HOT_PREC_ACCURATE)) return HOT_OK;
+  int per_sm = 0, rc = HOT_OK;
+  HOT_CUDA(hot_once::occupancy(shape, &per_sm));
+  if (per_sm < 1) return HOT_OK;  // no room: the direct kernels
+  const long long U = (long long)((c->W + hot::kTileW - 1) / hot::kTileW) * c->H;
+  const int G = (int)std::min<long long>((long long)sms * per_sm, U);
+  std::vector<hot::SubTile> sub;
+  std::vector<int> first;
+  cut_schedule(c->W, c->H, G, hot::once_rows(shape), sub, first, true);
+  rc = dalloc(&c->osub, sub.size());
+  if (rc == HOT_OK) rc = dalloc(&c->ofirst, first.size());
+  if (rc != HOT_OK) return rc;
+  HOT_CUDA(cudaMemcpy(c->osub, sub.data(), sizeof(hot::SubTile) * sub.size(), cudaMemcpyHostToDevice));
+  HOT_CUDA(cudaMemcpy(c->ofirst, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice));
+  c->ogrid = G;
+  c->on_sub = (int)sub.size();
+  c->once = shape;
+  return HOT_OK;
+}
+
 // One wave of persistent blocks (SMs x resident blocks per SM: as many as fit, at most
 // tile_bps); the W/32 x H row segments are dealt out in equal contiguous runs, cut into
-// sub-tiles of <= tile_rows rows.
+// sub-tiles of <= tile_rows rows.  Also the one-exponential step's schedule.
 int build_schedule(hot_ctx *c) {
   drop_graphs(c);  // graphs hold the old schedule
   int rc = set_step_smem(c->M);
@@ -390,24 +480,8 @@ int build_schedule(hot_ctx *c) {
   // (and with it the bits of the results)
   if (!separable_kernels(c) && per_sm == hot::kMaxGroups) G = (G + hot::kMaxGroups - 1) / hot::kMaxGroups * hot::kMaxGroups;
   std::vector<hot::SubTile> sub;
-  std::vector<int> first(G + 1);
-  for (int b = 0; b < G; b++) {
-    first[b] = (int)sub.size();
-    long long s = U * b / G;
-    const long long s1 = U * (b + 1) / G;
-    while (s < s1) {
-      const int strip = (int)(s / c->H), row = (int)(s % c->H);
-      const long long run_end = std::min<long long>(s1, (long long)(strip + 1) * c->H);
-      const int L = (int)(run_end - s);
-      const int nsub = (L + c->tile_rows - 1) / c->tile_rows;
-      for (int i = 0; i < nsub; i++) {
-        const int r0 = row + (int)((long long)L * i / nsub), r1 = row + (int)((long long)L * (i + 1) / nsub);
-        sub.push_back({strip * hot::kTileW, r0, r1 - r0, 0});
-      }
-      s = run_end;
-    }
-  }
-  first[G] = (int)sub.size();
+  std::vector<int> first;
+  cut_schedule(c->W, c->H, G, c->tile_rows, sub, first);
   HOT_CUDA(cudaStreamSynchronize(c->st));
   dfree(c->sub);
   dfree(c->first);
@@ -420,7 +494,7 @@ int build_schedule(hot_ctx *c) {
   HOT_CUDA(cudaMemcpy(c->first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice));
   c->grid = G;
   c->n_sub = (int)sub.size();
-  return HOT_OK;
+  return build_once_schedule(c, sms);
 }
 
 // One step-kernel launch (launch k of the sequence): weight update + back-projection and/or
@@ -534,7 +608,15 @@ int launch_persistent(hot_ctx *c, int iters) {
   cfg.numAttrs = 1;
   HOT_CUDA(cudaMemsetAsync(c->sync, 0, sizeof(unsigned int), c->st));  // arrival count
   Probe probe(c, HOT_KERNEL_STEP);
-  if (c->precision == HOT_PREC_SEPARABLE) {
+  if (c->once) {
+    for (int j = 0; j < 6; j++) {
+      p.step[j].sub = c->osub;
+      p.step[j].first = c->ofirst;
+      p.step[j].chunk = c->M;
+    }
+    cfg.gridDim = dim3(c->ogrid);
+    hot_once::launch_persistent(c->once, c->precision == HOT_PREC_FAST, cfg, p);
+  } else if (c->precision == HOT_PREC_SEPARABLE) {
     cfg.dynamicSmemBytes = hot::sep_smem_bytes(sep_chunk(c));
     cudaLaunchKernelEx(&cfg, hot::gsw_persistent_kernel<hot::kModeSeparable>, p);
   } else if (c->precision == HOT_PREC_FAST) {
@@ -677,6 +759,8 @@ void hot_destroy(hot_ctx *c) {
   dfree(c->phi);
   dfree(c->sub);
   dfree(c->first);
+  dfree(c->osub);
+  dfree(c->ofirst);
   dfree(c->metrics);
   dfree(c->u8);
   dfree(c->sync);
@@ -1692,6 +1776,22 @@ int hot_get_block_merge(const hot_ctx *c, int *requested, int *in_effect) {
   return HOT_OK;
 }
 
+int hot_set_once(hot_ctx *c, int on) {
+  if (!c) return fail(HOT_EINVAL, "hot_set_once: NULL context");
+  if (on != 0 && on != 1) return fail(HOT_EINVAL, "hot_set_once: on = %d is not 0 or 1", on);
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  c->once_req = on != 0;
+  drop_graphs(c);
+  return c->M ? build_schedule(c) : HOT_OK;
+}
+
+int hot_get_once(const hot_ctx *c, int *requested, int *in_effect) {
+  if (!c) return fail(HOT_EINVAL, "hot_get_once: NULL context");
+  if (requested) *requested = c->once_req ? 1 : 0;
+  if (in_effect) *in_effect = c->once ? 1 : 0;
+  return HOT_OK;
+}
+
 int hot_autotune(hot_ctx *c, int iters, int *rows, int *blocks_per_sm, int *chunk, double *us_per_iter) {
   if (!c) return fail(HOT_EINVAL, "hot_autotune: NULL context");
   if (!c->M) return fail(HOT_ESTATE, "hot_autotune: no traps set");
@@ -1703,19 +1803,35 @@ int hot_autotune(hot_ctx *c, int iters, int *rows, int *blocks_per_sm, int *chun
   if (rc != HOT_OK) return rc;
   const bool profiling = c->profiling;
   c->profiling = false;
+  auto timed_gsw = [&](double *us) {
+    return time_runs(c->st, iters, us, [&]() { return restore_state(c, saved, c->st); },
+                     [&]() { return hot_gsw(c, iters, nullptr, nullptr); });
+  };
+  // The one-exponential step, where it applies, against the best tiling of the direct kernels
+  // (which also serve the adjoint and the superposition).
+  const bool once_req = c->once_req;
+  double once_us = 0;
+  if (once_req && c->once) {
+    rc = timed_gsw(&once_us);
+    if (rc == HOT_OK) rc = hot_set_once(c, 0);
+  }
   Tiling best = {c->tile_rows, c->sched_bps, c->tile_chunk, c->tile_merge};
   double best_us = 0;
-  rc = tune_tiling(
+  if (rc == HOT_OK) rc = tune_tiling(
       kMaxBlocksPerSm, best, best_us,
       [&](const Tiling &t) {
         c->tile_merge = t.merge;  // applied by the schedule that hot_set_tiling rebuilds
         return hot_set_tiling(c, t.rows, t.bps, t.chunk);
       },
-      [&](double *us) {
-        return time_runs(c->st, iters, us, [&]() { return restore_state(c, saved, c->st); },
-                         [&]() { return hot_gsw(c, iters, nullptr, nullptr); });
-      },
-      !separable_kernels(c));
+      timed_gsw, !separable_kernels(c));
+  if (rc == HOT_OK && once_req && once_us > 0 && once_us < best_us) {
+    rc = hot_set_once(c, 1);
+    best_us = once_us;
+  } else if (once_req && once_us > 0) {
+    c->once_req = false;  // the direct kernels were faster (hot_get_once reports it)
+  } else if (rc != HOT_OK) {
+    c->once_req = once_req;
+  }
   c->profiling = profiling;
   const int rc2 = restore_state(c, saved, c->st);
   cudaStreamSynchronize(c->st);

@@ -62,6 +62,8 @@ SIGNATURES = {
     "hot_get_tiling": (_c_int, [_vp, _ip, _ip, _ip]),
     "hot_set_block_merge": (_c_int, [_vp, _c_int]),
     "hot_get_block_merge": (_c_int, [_vp, _ip, _ip]),
+    "hot_set_once": (_c_int, [_vp, _c_int]),
+    "hot_get_once": (_c_int, [_vp, _ip, _ip]),
     "hot_autotune": (_c_int, [_vp, _c_int, _ip, _ip, _ip, _dp]),
     "hot_field": (_c_int, [_vp, _vp, _vp]),
     "hot_superposition": (_c_int, [_vp, _vp]),
@@ -280,12 +282,23 @@ def hot_get_block_merge(ctx: int) -> dict:
     return {"requested": req.value, "in_effect": eff.value}
 
 
+def hot_set_once(ctx: int, on: bool) -> None:
+    """The one-exponential GSW step of the accurate and fast modes (M <= 128): on (default) or off."""
+    _ok(lib.hot_set_once(_vp(ctx), 1 if on else 0), "hot_set_once")
+
+
+def hot_get_once(ctx: int) -> dict:
+    req, eff = _c_int(), _c_int()
+    _ok(lib.hot_get_once(_vp(ctx), ctypes.byref(req), ctypes.byref(eff)), "hot_get_once")
+    return {"requested": bool(req.value), "in_effect": bool(eff.value)}
+
+
 def hot_autotune(ctx: int, iters: int) -> dict:
     r, b, c, us = _c_int(), _c_int(), _c_int(), ctypes.c_double()
     _ok(lib.hot_autotune(_vp(ctx), int(iters), ctypes.byref(r), ctypes.byref(b), ctypes.byref(c),
                          ctypes.byref(us)), "hot_autotune")
     return {"rows": r.value, "blocks_per_sm": b.value, "chunk": c.value, "us_per_iter": us.value,
-            "merge": hot_get_block_merge(ctx)["in_effect"]}
+            "merge": hot_get_block_merge(ctx)["in_effect"], "once": hot_get_once(ctx)["in_effect"]}
 
 
 def hot_batch_set_tiling(batch: int, rows: int = 0, blocks_per_sm: int = 0, chunk: int = 0,
@@ -534,6 +547,9 @@ class Hologram:
     def set_block_merge(self, merge=4):
         hot_set_block_merge(self.ctx, merge)
 
+    def set_once(self, on: bool = True):
+        hot_set_once(self.ctx, on)
+
     def use_persistent(self, enable: bool = True):
         hot_use_persistent(self.ctx, enable)
 
@@ -575,7 +591,8 @@ class Hologram:
         return hot_sharded_end(self.ctx, iters)
 
     def tiling(self) -> dict:
-        return dict(hot_get_tiling(self.ctx), merge=hot_get_block_merge(self.ctx)["in_effect"])
+        return dict(hot_get_tiling(self.ctx), merge=hot_get_block_merge(self.ctx)["in_effect"],
+                    once=hot_get_once(self.ctx)["in_effect"])
 
     def autotune(self, iters: int) -> dict:
         """Picks the fastest tiling for hot_gsw(iters); phases and weights are kept."""

@@ -155,7 +155,7 @@ def test_autotune_keeps_state(hot):
         t = h.autotune(4)
         assert 1 <= t["rows"] <= 14 and 1 <= t["blocks_per_sm"] <= 4 and 1 <= t["chunk"] <= 128
         assert t["us_per_iter"] > 0
-        assert h.tiling() == {k: t[k] for k in ("rows", "blocks_per_sm", "chunk", "merge")}
+        assert h.tiling() == {k: t[k] for k in ("rows", "blocks_per_sm", "chunk", "merge", "once")}
         assert np.array_equal(h.phase("f32"), phi_before)
         with pytest.raises(hot.HotError, match="HOT_ESTATE"):
             h.fields()

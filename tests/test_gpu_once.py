@@ -1,0 +1,114 @@
+"""GPU: the one-exponential GSW step (hot_set_once) -- each pixel-trap exponential evaluated once
+per iteration and kept in registers between the back-projection and the forward field.  Checked
+against the FP64 oracle (Eq. 1, Sec. 3; tolerances as in test_gpu_parity) and against the direct
+kernels, on shapes that cover every trap-count shape of the kernel, ragged strips, both column
+staging paths and runs of a block that cross from one 32-pixel strip into the next."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0907_4027_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+REL_V = 1e-4
+ABS_EU = 1e-3
+TOL_S = {"accurate": 2e-6, "fast": 2e-5}
+
+
+@pytest.fixture(scope="module")
+def hot():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0907_4027_gb300 import _build
+    _build.build()
+    from paper_0907_4027_gb300 import hot as h
+    return h
+
+
+def rel_err(a, b):
+    return np.max(np.abs(np.abs(a) - np.abs(b)) / np.maximum(np.abs(b), 1e-300))
+
+
+@pytest.mark.parametrize("precision", ["accurate", "fast"])
+@pytest.mark.parametrize("W,H,M", [
+    (96, 64, 32),     # 8 rows per sub-tile, 4 traps per warp
+    (70, 45, 64),     # W not a multiple of 4: column parts copied one by one
+    (1024, 40, 100),  # runs of 4-5 row segments that cross strip boundaries; 13 traps per warp
+    (300, 60, 104),   # a ragged last strip (12 columns), runs cut into 3-row sub-tiles and a remainder
+    (128, 30, 128),   # 2 rows per sub-tile, 16 traps per warp
+    (37, 29, 9),      # one ragged strip, fewer traps than warps
+])
+def test_once_matches_oracle_and_direct_kernels(hot, W, H, M, precision):
+    w = wl.random_case(W, H, M, seed=W * 7 + H + M, precision=precision)
+    out = {}
+    for once in (True, False):
+        with hot.Hologram.from_workload(w) as h:
+            h.set_once(once)
+            assert h.tiling()["once"] == once
+            h.gsw(0)
+            V0, _ = h.fields()
+            h.gsw(1)
+            V1, w1 = h.fields()
+            phi1 = h.phase("f32")
+            eu3 = h.gsw(2)  # resumes: three iterations in all
+            out[once] = (V0, V1, w1, phi1, eu3)
+    V0, V1, w1, phi1, (e3, u3) = out[True]
+    assert rel_err(V0, oracle.forward(w.geom, w.xyz, w.phi0)) < REL_V
+    r1 = oracle.gsw(w.geom, w.xyz, 1, w.phi0)
+    assert rel_err(V1, r1["V"]) < REL_V
+    np.testing.assert_allclose(w1, r1["w"], rtol=REL_V)
+    r3 = oracle.gsw(w.geom, w.xyz, 3, w.phi0)
+    assert abs(e3 - r3["e"]) < ABS_EU and abs(u3 - r3["u"]) < ABS_EU
+    # the phases of the first iteration from the oracle's coefficients (conditioning-aware)
+    _, coef = oracle.update_weights(oracle.forward(w.geom, w.xyz, w.phi0), np.ones(M))
+    ophi, S = oracle.backproject(w.geom, w.xyz, coef, want_S=True)
+    d = np.abs(np.angle(np.exp(1j * (phi1.astype(np.float64) - ophi))))
+    assert not (np.abs(S) * d > TOL_S[precision] * np.sum(np.abs(coef))).any()
+    # and the direct kernels agree to the same tolerance
+    assert rel_err(V1, out[False][1]) < REL_V and rel_err(out[False][1], r1["V"]) < REL_V
+
+
+@pytest.mark.parametrize("precision", ["accurate", "fast"])
+def test_once_bits_resume_graphs_persistent(hot, precision):
+    """Resumed calls, launches without graphs and the persistent form give the bits of one
+    graph-replayed call (the forward field of stored phases is the step's own arithmetic)."""
+    w = wl.random_case(200, 90, 100, seed=11, precision=precision)
+    res = []
+    for mode in ("one", "split", "nographs", "persistent"):
+        with hot.Hologram.from_workload(w) as h:
+            assert h.tiling()["once"]
+            if mode == "nographs":
+                h.use_graphs(False)
+            if mode == "persistent":
+                h.use_persistent(True)
+            if mode == "split":
+                h.gsw(2)
+                eu = h.gsw(3)
+            else:
+                eu = h.gsw(5)
+            res.append((h.phase("f32"), *h.fields(), eu))
+    for p, V, wt, eu in res[1:]:
+        assert np.array_equal(res[0][0], p) and np.array_equal(res[0][1], V) and np.array_equal(res[0][2], wt)
+        assert eu == res[0][3]
+
+
+def test_once_applies_where_it_can(hot):
+    w = wl.random_case(64, 32, 128, seed=3, precision="fast")
+    with hot.Hologram.from_workload(w) as h:
+        assert h.tiling()["once"]
+        h.set_precision("accurate")
+        assert h.tiling()["once"]
+        h.set_precision("separable")
+        assert not h.tiling()["once"]
+        h.set_precision("fast")
+        assert h.tiling()["once"]
+        h.set_once(False)
+        assert not h.tiling()["once"] and not hot.hot_get_once(h.ctx)["requested"]
+        h.set_once(True)
+        assert h.tiling()["once"]
+        assert hot.lib.hot_set_once(h.ctx, 2) == hot.HOT_EINVAL
+    w = wl.random_case(64, 32, 129, seed=3, precision="fast")
+    with hot.Hologram.from_workload(w) as h:
+        assert not h.tiling()["once"] and hot.hot_get_once(h.ctx)["requested"]
