@@ -36,6 +36,7 @@ METRIC = "GSW pixel-trap updates/s (512x512 px, M=100, 30 iterations)"
 UNIT = "updates/s"
 SFU_LANES_PER_SM = 16          # sin.approx / cos.approx results per clock per SM (sm_103a)
 SFU_OPS_PER_UPDATE = 4         # one sin + one cos in the forward field, one each in back-projection
+SFU_OPS_PER_UPDATE_ONCE = 2    # one-exponential step: one sin + one cos per pair and iteration
 FMA_LANES_PER_SM = 128         # FP32 FMA results per clock per SM (sm_103a)
 FMA_OPS_PER_UPDATE = 8         # separable mode: one complex multiply-add (4 FMA) in each step
 TC_FLOPS_PER_UPDATE = 48       # tensor mode: 2 complex MACs (16 flops) x 3 MMAs per product (hi/lo split)
@@ -65,6 +66,9 @@ def parse():
     ap.add_argument("--merge", type=int, default=1, choices=[1, 2, 4],
                     help="with --single: schedule blocks per launched block of the GSW step "
                          "(hot_set_block_merge; the timed runs let the autotuner choose)")
+    ap.add_argument("--direct", action="store_true",
+                    help="with --single: the direct step kernels even where the one-exponential step "
+                         "applies (hot_set_once(0))")
     ap.add_argument("--cpu-sample-iters", type=int, default=0,
                     help="GSW iterations of the CPU-baseline sample (0: the workload's own count)")
     return ap.parse_args()
@@ -255,7 +259,8 @@ def run_engine(args):
     h.set_phase(phi0)
     t_tune = time.perf_counter()
     if tensor:  # fixed tiles: nothing to tune
-        tuned = {"rows": None, "blocks_per_sm": None, "chunk": None, "merge": None, "us_per_iter": None}
+        tuned = {"rows": None, "blocks_per_sm": None, "chunk": None, "merge": None, "once": False,
+                 "us_per_iter": None}
     else:
         tuned = h.autotune(w.iters)
     tuned["seconds"] = time.perf_counter() - t_tune
@@ -331,13 +336,15 @@ def run_engine(args):
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks_path):
         sm_max_mhz = float(json.load(open(peaks_path)).get("sm_max_mhz", sm_max_mhz))
+    once = bool(tuned.get("once"))  # the one-exponential step (hot_set_once), if the autotuner kept it
     if sep or tensor:
         lanes, ops, pipe = FMA_LANES_PER_SM, FMA_OPS_PER_UPDATE, "FP32 FMA"
     else:
-        lanes, ops, pipe = SFU_LANES_PER_SM, SFU_OPS_PER_UPDATE, "SFU"
+        lanes, ops, pipe = SFU_LANES_PER_SM, SFU_OPS_PER_UPDATE_ONCE if once else SFU_OPS_PER_UPDATE, "SFU"
     peak = dev.multi_processor_count * lanes * sm_max_mhz * 1e6 / ops
+    peak_direct = dev.multi_processor_count * SFU_LANES_PER_SM * sm_max_mhz * 1e6 / SFU_OPS_PER_UPDATE
     lanes_measured = hot.hot_sfu_rate(3 if sep or tensor else 0)[0]
-    traffic = profiled_traffic(args.workload, "tc" if tensor else "sep" if sep else "step")
+    traffic = profiled_traffic(args.workload, "tc" if tensor else "sep" if sep else "once" if once else "step")
     kernel_share = {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4)
                     for k, v in prof.items()}
 
@@ -395,11 +402,18 @@ def run_engine(args):
                     "frac_of_value_note": "the bench value (whole step: forward of the starting phases, "
                                           "iterations, finalize, 8-bit encoding) over the same peak",
                     "kernel": ("gsw_sep_kernel<back, fwd>" if sep else
+                               f"gsw_once_kernel<{w.precision}, back>" if once else
                                f"gsw_step_kernel<{w.precision}, back, fwd>") + " (one GSW iteration per launch)",
                     "peak_basis": f"{dev.multi_processor_count} SMs x {lanes} {pipe} "
                                   f"lanes/clk x {sm_max_mhz:.0f} MHz / {ops} "
                                   f"{pipe} ops per update",
                     "lanes_per_clk_per_sm_measured": round(lanes_measured, 2),
+                    **({"frac_direct_form": achieved / peak_direct,
+                        "frac_direct_form_note": "the same rate over the direct method's bound (two "
+                                                 "exponentials per pair and iteration, 4 SFU ops per update); "
+                                                 "the one-exponential step evaluates each pair's exponential "
+                                                 "once, so its own bound is half as many SFU ops"}
+                       if once else {}),
                     "avg_launch_us": avg_launch_s * 1e6,
                     "units_per_launch": units_per_launch,
                     "launch_timing": launch_timing,
@@ -414,9 +428,10 @@ def run_engine(args):
             "config": workload_config(w, {
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                 "l2": "flushed between steps (256 MB write outside the step events)",
-                "tiling": {k: tuned[k] for k in ("rows", "blocks_per_sm", "chunk", "merge")},
+                "tiling": {k: tuned[k] for k in ("rows", "blocks_per_sm", "chunk", "merge", "once")},
                 "autotune": {"us_per_iter": tuned["us_per_iter"], "seconds": round(tuned["seconds"], 3),
-                             "search": "coordinate search over rows/blocks_per_sm/chunk, best of 3 graph replays"},
+                             "search": "the one-exponential step against a coordinate search over "
+                                       "rows/blocks_per_sm/chunk/merge of the direct kernels, best of 3 graph replays"},
                 "timing": "CUDA events per step on the launching stream, summed; hot_gsw replays "
                           "one CUDA graph per call; roofline kernel times from a second pass of "
                           "the same steps with per-launch events"}),
@@ -882,6 +897,8 @@ def run_single(args):
     with hot.Hologram.from_workload(w, torch.cuda.current_stream().cuda_stream) as h:
         if args.merge > 1:
             h.set_block_merge(args.merge)
+        if args.direct:
+            h.set_once(False)
         e, u = h.gsw(args.single)
         print(json.dumps({"workload": w.name, "precision": w.precision, "iters": args.single, "e": e, "u": u,
                           "kernels": h.launches, "tiling": h.tiling()}), flush=True)

@@ -1021,6 +1021,29 @@ __device__ __forceinline__ void once_stage_rows(const StepArgs &a, const SubTile
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 
+// Two FP32 values in one 64-bit register for the packed FP32 instructions of sm_100 and later
+// (add / fma .f32x2): one instruction does both lanes, each rounded as the scalar operation.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // u = e^{i phi} of a phase reduced to one turn in table units: radians in [-pi, pi] (fast,
 // scaled by 1 + kFastEta here like the tables) or turns in [-1/2, 1/2] (accurate).
 template <bool FAST>
@@ -1037,34 +1060,48 @@ __device__ __forceinline__ float2 unit_phasor(float ph) {
 }
 
 // Back-projection of a warp's TV traps (tables and coefficients from Xs, Yb, Cw, trap by trap)
-// onto the lane's R rows: E[k][r] = e^{i (X + Y)} (kept), S[r] += c_k E[k][r].  All R rows are
-// evaluated (no per-row branches): the rows past a short sub-tile's end are staged rows of the
-// next sub-tile or zero padding, and their results are discarded.
+// onto the lane's R rows: E[k][r] = e^{i (X + Y)} (kept), S[r] = sum_k c_k E[k][r], accumulated
+// as U[r] = sum_k Re(c_k) E[k][r] and W[r] = sum_k Im(c_k) E[k][r] (S = U + i W) with packed FP32
+// multiply-adds on E's (cos, sin) pair; the arguments X + Y of two rows are one packed add.  All
+// R rows are evaluated (no per-row branches): the rows past a short sub-tile's end are staged
+// rows of the next sub-tile or zero padding, and their results are discarded.
 template <bool FAST, int TV, int TMAX, int R>
 __device__ __forceinline__ void once_back(const float *Xs, const float *Yb, const float2 *Cw, int lane,
                                           float2 (&E)[TMAX][R], float2 (&S)[R]) {
   constexpr int YW = once_yw(R);
+  unsigned long long U[R], Wp[R];
+#pragma unroll
+  for (int r = 0; r < R; r++) U[r] = Wp[r] = 0ull;  // (+0, +0)
 #pragma unroll
   for (int k = 0; k < TV; k++) {
     const float2 c = Cw[k];
+    const unsigned long long cx = pack2(c.x, c.x), cy = pack2(c.y, c.y);
     const float xk = Xs[k * kTileW + lane];
-    const float4 *yq = reinterpret_cast<const float4 *>(Yb + k * YW);
+    const unsigned long long xx = pack2(xk, xk);
+    const ulonglong2 *yq = reinterpret_cast<const ulonglong2 *>(Yb + k * YW);
 #pragma unroll
-    for (int q = 0; q < YW / 4; q++) {
-      const float4 y4 = yq[q];
-      const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+    for (int h = 0; h < (R + 1) / 2; h++) {
+      const ulonglong2 y4 = yq[h / 2];  // rows 4 (h / 2) .. + 3, one 16-byte load
+      const float2 arg = unpack2(add2(xx, (h & 1) ? y4.y : y4.x));  // rows 2h and 2h + 1
+      const float a2[2] = {arg.x, arg.y};
 #pragma unroll
-      for (int j = 0; j < 4; j++) {
-        const int r = 4 * q + j;
+      for (int j = 0; j < 2; j++) {
+        const int r = 2 * h + j;
         if (r < R) {
           float co, si;
-          cis<FAST>(xk + yy[j], co, si);
+          cis<FAST>(a2[j], co, si);
           E[k][r] = make_float2(co, si);
-          S[r].x = fmaf(c.x, co, fmaf(-c.y, si, S[r].x));
-          S[r].y = fmaf(c.x, si, fmaf(c.y, co, S[r].y));
+          const unsigned long long e = pack2(co, si);
+          U[r] = fma2(cx, e, U[r]);
+          Wp[r] = fma2(cy, e, Wp[r]);
         }
       }
     }
+  }
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const float2 u = unpack2(U[r]), w = unpack2(Wp[r]);
+    S[r] = make_float2(u.x - w.y, u.y + w.x);
   }
 }
 
