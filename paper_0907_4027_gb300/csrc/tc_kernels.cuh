@@ -629,20 +629,35 @@ __device__ __forceinline__ ffp ffp_add(ffp a, ffp b) {  // TwoSum (Knuth) + reno
 }
 
 constexpr int kPrepThreads = 256;
+constexpr int kPrepPrefetch = 16;  // row-table elements a thread of tc_prep_kernel fetches before the wait
 
 // Sec. 3 weight update and the back-projection operand of one iteration: every block reads the
 // field sums, forms V_m, <|V|> (float-float sum in one fixed order, so every block obtains the
 // same bits) and the coefficients c_m = w_m' V_m/|V_m| with w_m' = w_m <|V|>/|V_m| (|V_m| < 1e-30:
 // c_m = w_m, w kept) in shared memory, then writes its share of P[iy][2m..2m+1] = c_m Y_m(iy),
 // split.  Block 0 writes the new weights (and the trace); the blocks clear the next buffer.
+// The row table is constant during hot_gsw: a thread's first kPrepPrefetch elements of it are
+// fetched before the wait for the previous kernel (they come from HBM: the GEMMs' operands have
+// pushed the table out of L2).
 template <int OP>
 __global__ void __launch_bounds__(kPrepThreads) tc_prep_kernel(PrepArgs a) {
   extern __shared__ float2 cs[];  // [M]
   __shared__ ffp part[2][kPrepThreads / 32];
   __shared__ float ext[2][kPrepThreads / 32];
   __shared__ float cmx[kPrepThreads / 32];
-  grid_wait();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  // this block's rows of P: an even share of the H rows, all Kb/2 (padded) traps of each
+  const int half = a.Kb / 2;
+  const int r0 = (int)((long long)a.H * blockIdx.x / gridDim.x);
+  const int r1 = (int)((long long)a.H * (blockIdx.x + 1) / gridDim.x);
+  const int n = (r1 - r0) * half;
+  float2 ypre[kPrepPrefetch];
+#pragma unroll
+  for (int j = 0; j < kPrepPrefetch; j++) {
+    const int i = t + j * kPrepThreads;
+    ypre[j] = i < n ? __ldg(a.YT + (size_t)r0 * half + i) : make_float2(0.f, 0.f);
+  }
+  grid_wait();
   ffp s = {0.f, 0.f}, si = {0.f, 0.f};
   float mx = -1.f, mn = 3.0e38f;
   for (int m = t; m < a.M; m += kPrepThreads) {
@@ -712,18 +727,16 @@ __global__ void __launch_bounds__(kPrepThreads) tc_prep_kernel(PrepArgs a) {
   float top = cmx[0];
   for (int i = 1; i < kPrepThreads / 32; i++) top = fmaxf(top, cmx[i]);
   const float scale = top > 0.f ? 1.f / top : 1.f;
-  // this block's rows: an even share of the H rows, all Kb/2 (padded) traps of each
-  const int half = a.Kb / 2;
-  const int r0 = (int)((long long)a.H * blockIdx.x / gridDim.x);
-  const int r1 = (int)((long long)a.H * (blockIdx.x + 1) / gridDim.x);
-  const int n = (r1 - r0) * half;
-  for (int i = t; i < n; i += kPrepThreads) {
-    const int iy = r0 + i / half, m = i - (i / half) * half;
+  // element i of the block's rows is P[r0 + i / half][m = i % half], at i of the row-major table
+  auto put = [&](int i, float2 y) {
+    const int m = i % half;
     const float2 c = m < a.M ? make_float2(cs[m].x * scale, cs[m].y * scale) : make_float2(0.f, 0.f);
-    const size_t j = (size_t)iy * half + m;
-    const float2 y = __ldg(a.YT + j);
-    store_split<OP>(a.p_hi, a.p_lo, 2 * j, c.x * y.x - c.y * y.y, c.x * y.y + c.y * y.x);
-  }
+    store_split<OP>(a.p_hi, a.p_lo, 2 * ((size_t)r0 * half + i), c.x * y.x - c.y * y.y, c.x * y.y + c.y * y.x);
+  };
+#pragma unroll
+  for (int j = 0; j < kPrepPrefetch; j++)
+    if (t + j * kPrepThreads < n) put(t + j * kPrepThreads, ypre[j]);
+  for (int i = t + kPrepPrefetch * kPrepThreads; i < n; i += kPrepThreads) put(i, __ldg(a.YT + (size_t)r0 * half + i));
   grid_release();
 }
 
