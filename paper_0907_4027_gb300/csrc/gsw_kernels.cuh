@@ -940,10 +940,11 @@ static __global__ void __launch_bounds__(kLossThreads) intensity_loss_kernel(Los
 // so each pair costs one cos/sin per iteration instead of two.  The 8 warps of a block split
 // the traps (warp_traps over all M, at most TMAX each, fixed for the launch); lane l holds
 // column x0 + l of a sub-tile of at most R rows.  All M traps' tables of a sub-tile are staged
-// in shared memory at once (the column parts once per 32-pixel strip), one sub-tile ahead.  A thread's forward sums stay in registers
-// over all of the block's sub-tiles; they are summed over the warp and added, in fixed point,
-// once at the end.  The forward-only variant (the field of given phases) evaluates the same
-// expressions in the same order, so a sequence resumed from stored phases gives the same bits.
+// in shared memory at once (the column parts once per 32-pixel strip), one sub-tile ahead.  A
+// thread's forward sums stay in registers over all of the block's sub-tiles; they are summed
+// over the warp and added, in fixed point, once at the end.  The forward-only variant (the
+// field of given phases) evaluates the same expressions in the same order, so a sequence
+// resumed from stored phases gives the same bits.
 constexpr int kOnceMaxM = 128;
 constexpr int kOnceTMax = 16;  // traps per warp at most (8 warps x 16 = kOnceMaxM)
 
@@ -1065,9 +1066,9 @@ __device__ __forceinline__ float2 unit_phasor(float ph) {
 // multiply-adds on E's (cos, sin) pair; the arguments X + Y of two rows are one packed add.  All
 // R rows are evaluated (no per-row branches): the rows past a short sub-tile's end are staged
 // rows of the next sub-tile or zero padding, and their results are discarded.
-template <bool FAST, int TV, int TMAX, int R>
+template <bool FAST, int TV, int R>
 __device__ __forceinline__ void once_back(const float *Xs, const float *Yb, const float2 *Cw, int lane,
-                                          float2 (&E)[TMAX][R], float2 (&S)[R]) {
+                                          float2 (&E)[TV][R], float2 (&S)[R]) {
   constexpr int YW = once_yw(R);
   unsigned long long U[R], Wp[R];
 #pragma unroll
@@ -1106,9 +1107,8 @@ __device__ __forceinline__ void once_back(const float *Xs, const float *Yb, cons
 }
 
 // acc[k] += u_r conj(E[k][r]) over the lane's R rows (u_r = 0 past the sub-tile's end).
-template <int TV, int TMAX, int R>
-__device__ __forceinline__ void once_accumulate(const float2 (&P)[R], const float2 (&E)[TMAX][R],
-                                                float2 (&acc)[TMAX]) {
+template <int TV, int R>
+__device__ __forceinline__ void once_accumulate(const float2 (&P)[R], const float2 (&E)[TV][R], float2 (&acc)[TV]) {
 #pragma unroll
   for (int k = 0; k < TV; k++) {
 #pragma unroll
@@ -1121,9 +1121,9 @@ __device__ __forceinline__ void once_accumulate(const float2 (&P)[R], const floa
 
 // Forward field of given phases: the exponentials of the back-projection's expression, then the
 // same accumulation (trap by trap, one trap's rows at a time).
-template <bool FAST, int TV, int TMAX, int R>
+template <bool FAST, int TV, int R>
 __device__ __forceinline__ void once_forward_only(const float *Xs, const float *Yb, const float2 (&P)[R], int lane,
-                                                  float2 (&acc)[TMAX]) {
+                                                  float2 (&acc)[TV]) {
   constexpr int YW = once_yw(R);
 #pragma unroll
   for (int k = 0; k < TV; k++) {
@@ -1179,7 +1179,7 @@ __device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm,
       float2 S[R];
 #pragma unroll
       for (int r = 0; r < R; r++) S[r] = make_float2(0.f, 0.f);
-      once_back<FAST, TV, TV, R>(Xs, Yb, sm.Cw + warp * kOnceTMax, lane, E, S);
+      once_back<FAST, TV, R>(Xs, Yb, sm.Cw + warp * kOnceTMax, lane, E, S);
 #pragma unroll
       for (int r = 0; r < R; r++)
         if (r < st.rows) sm.Sp[(warp * R + r) * kTileW + lane] = S[r];
@@ -1212,9 +1212,9 @@ __device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm,
 #pragma unroll
     for (int r = 0; r < R; r++) P[r] = r < st.rows ? sm.Ps[r * kTileW + lane] : make_float2(0.f, 0.f);
     if (BACK)
-      once_accumulate<TV, TV, R>(P, E, acc);
+      once_accumulate<TV, R>(P, E, acc);
     else
-      once_forward_only<FAST, TV, TV, R>(Xs, Yb, P, lane, acc);
+      once_forward_only<FAST, TV, R>(Xs, Yb, P, lane, acc);
     if (next_strip) xb ^= 1;
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
