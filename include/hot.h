@@ -55,16 +55,19 @@ typedef enum {
  * over a factor ~400, so that the superposition cancels at some pixels and amplifies each term's
  * error.  There the |V_m| error after one iteration is bounded by 2e-4 in the fast mode (1.2e-4
  * measured; accurate 7.6e-5) and by 5e-4 in the tensor mode (3.3e-4 measured).  Measured
- * elsewhere: 512 x 512 px with 100 traps, 4.1e-6 fast, 6.0e-6 accurate; 1920 x 1152 px with
- * 1000 traps, 8.8e-6 fast. */
+ * elsewhere: 512 x 512 px with 100 traps, 2.5e-6 fast, 2.4e-6 accurate (the one-exponential step,
+ * hot_set_once; the direct kernels: 4.1e-6, 6.0e-6); 1920 x 1152 px with 1000 traps, 8.8e-6 fast. */
 typedef enum {
   HOT_PREC_ACCURATE = 0, /* sincospif on the exactly reduced phase (FP32, ~1 ulp) */
   HOT_PREC_FAST = 1,     /* the direct evaluation on the special-function unit: sin.approx /
                              cos.approx of the reduced phase (arguments pre-scaled by 1 + 8.17e-8
-                             against the unit's mean argument shrink); the forward field rotates the
-                             phases of each pixel sub-tile by a fixed pseudo-random angle and its
-                             sums back, so that the unit's systematic error does not add up over
-                             the pixels */
+                             against the unit's mean argument shrink); the direct step's forward
+                             field rotates the phases of each pixel sub-tile by a fixed
+                             pseudo-random angle and its sums back, so that the unit's systematic
+                             error does not add up over the pixels (the one-exponential step,
+                             M <= 128, forms the forward terms as e^{i phi_j} conj(e^{i Delta}),
+                             where a constant error of the unit only meets the small zero-order
+                             sum of e^{i phi_j}) */
   HOT_PREC_SEPARABLE = 2, /* Eq. 2 factorised: e^{i Delta} = e^{i X_m(ix)} e^{i Y_m(iy)} from FP32
                              complex tables (FP64 cos/sin once per entry); per pair one complex
                              multiply-add in each step, no transcendental function */
