@@ -112,3 +112,20 @@ def test_once_applies_where_it_can(hot):
     w = wl.random_case(64, 32, 129, seed=3, precision="fast")
     with hot.Hologram.from_workload(w) as h:
         assert not h.tiling()["once"] and hot.hot_get_once(h.ctx)["requested"]
+
+
+@pytest.mark.parametrize("precision", ["accurate", "fast"])
+def test_once_full_hd_slm_against_oracle(hot, precision):
+    """A 1920 x 1152 SLM with 100 traps: about 76 sub-tiles per block and runs that change strips,
+    against the oracle (|V| after one iteration, weights, e and u after two)."""
+    w = wl.random_case(1920, 1152, 100, seed=17, precision=precision)
+    with hot.Hologram.from_workload(w) as h:
+        assert h.tiling()["once"]
+        h.gsw(1)
+        V1, w1 = h.fields()
+        e2, u2 = h.gsw(1)
+    r1 = oracle.gsw(w.geom, w.xyz, 1, w.phi0)
+    assert rel_err(V1, r1["V"]) < REL_V
+    np.testing.assert_allclose(w1, r1["w"], rtol=REL_V)
+    r2 = oracle.gsw(w.geom, w.xyz, 2, w.phi0)
+    assert abs(e2 - r2["e"]) < ABS_EU and abs(u2 - r2["u"]) < ABS_EU
