@@ -1066,9 +1066,14 @@ __device__ __forceinline__ float2 unit_phasor(float ph) {
 // multiply-adds on E's (cos, sin) pair; the arguments X + Y of two rows are one packed add.  All
 // R rows are evaluated (no per-row branches): the rows past a short sub-tile's end are staged
 // rows of the next sub-tile or zero padding, and their results are discarded.
-template <bool FAST, int TV, int R>
+// PIPE: the forward field of the previous sub-tile is fused in -- each of its exponentials is
+// used for acc[k] += Pp[r] conj(E[k][r]) just before it is replaced -- so that its FP32 work
+// overlaps this sub-tile's cos/sin (per trap the rows and sub-tiles are added in the same order
+// as by once_accumulate, so the sums are the same bits).
+template <bool FAST, int TV, int R, bool PIPE>
 __device__ __forceinline__ void once_back(const float *Xs, const float *Yb, const float2 *Cw, int lane,
-                                          float2 (&E)[TV][R], float2 (&S)[R]) {
+                                          float2 (&E)[TV][R], float2 (&S)[R], const float2 (&Pp)[R],
+                                          float2 (&acc)[TV]) {
   constexpr int YW = once_yw(R);
   unsigned long long U[R], Wp[R];
 #pragma unroll
@@ -1089,6 +1094,10 @@ __device__ __forceinline__ void once_back(const float *Xs, const float *Yb, cons
       for (int j = 0; j < 2; j++) {
         const int r = 2 * h + j;
         if (r < R) {
+          if (PIPE) {
+            acc[k].x = fmaf(Pp[r].x, E[k][r].x, fmaf(Pp[r].y, E[k][r].y, acc[k].x));
+            acc[k].y = fmaf(Pp[r].y, E[k][r].x, fmaf(-Pp[r].x, E[k][r].y, acc[k].y));
+          }
           float co, si;
           cis<FAST>(a2[j], co, si);
           E[k][r] = make_float2(co, si);
@@ -1152,7 +1161,9 @@ __device__ __forceinline__ void once_forward_only(const float *Xs, const float *
 // (T <= TV; the rest are padding: zero coefficients, their sums dropped), then the warp's
 // forward sums, totalled over its lanes in a fixed order and added in fixed point.  Warps of
 // one block may run copies of this loop for different TV: its barriers are non-aligned.
-template <bool FAST, bool BACK, int TV, int R>
+// PIPE: the forward field of each sub-tile runs inside the next sub-tile's back-projection
+// (once_back), the last one's after the loop.
+template <bool FAST, bool BACK, int TV, int R, bool PIPE>
 __device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm, int t_begin, int t_end, int lo,
                                           int T) {
   const int lane = threadIdx.x & 31, warp = gthread() >> 5, t = gthread();
@@ -1160,6 +1171,15 @@ __device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm,
   float2 acc[TV];
 #pragma unroll
   for (int k = 0; k < TV; k++) acc[k] = make_float2(0.f, 0.f);
+  // the sub-tile's exponentials and unit phasors (PIPE: the previous sub-tile's until replaced;
+  // zero before the first, which adds nothing)
+  float2 E[TV][R], P[R];
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    P[r] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < TV; k++) E[k][r] = make_float2(0.f, 0.f);
+  }
   int xb = 0;  // the buffer of the current strip's column parts
   for (int i = t_begin; i < t_end; i++) {
     const SubTile st = a.sub[i];
@@ -1174,12 +1194,11 @@ __device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm,
     }
     cp_async_commit();  // (an empty group after the last sub-tile: uniform waits)
     const float *Xs = sm.cols(xb) + lo * kTileW, *Yb = sm.rows(buf) + lo * YW;
-    float2 E[TV][R];
     if (BACK) {
       float2 S[R];
 #pragma unroll
       for (int r = 0; r < R; r++) S[r] = make_float2(0.f, 0.f);
-      once_back<FAST, TV, R>(Xs, Yb, sm.Cw + warp * kOnceTMax, lane, E, S);
+      once_back<FAST, TV, R, PIPE>(Xs, Yb, sm.Cw + warp * kOnceTMax, lane, E, S, P, acc);
 #pragma unroll
       for (int r = 0; r < R; r++)
         if (r < st.rows) sm.Sp[(warp * R + r) * kTileW + lane] = S[r];
@@ -1208,15 +1227,15 @@ __device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm,
       asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this sub-tile's tables
     }
     group_sync_any();
-    float2 P[R];
 #pragma unroll
     for (int r = 0; r < R; r++) P[r] = r < st.rows ? sm.Ps[r * kTileW + lane] : make_float2(0.f, 0.f);
-    if (BACK)
-      once_accumulate<TV, R>(P, E, acc);
-    else
+    if (!BACK)
       once_forward_only<FAST, TV, R>(Xs, Yb, P, lane, acc);
+    else if (!PIPE)
+      once_accumulate<TV, R>(P, E, acc);
     if (next_strip) xb ^= 1;
   }
+  if (BACK && PIPE) once_accumulate<TV, R>(P, E, acc);  // the forward field of the last sub-tile
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   unsigned long long *const out = block_acc(a);
 #pragma unroll
@@ -1241,6 +1260,9 @@ __device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm,
 // the forward field of the phases in a.phi.
 // A warp's trap count T is TMAX or less (warp_traps); it runs the loop compiled for TMAX traps,
 // or for TMAX - 1 traps with any remaining ones as padding, so that no per-trap branch remains.
+// Shapes of 4 to 16 traps per warp with at most 32 exponentials per thread (TMAX R <= 32) fuse
+// each sub-tile's forward field into the next sub-tile's back-projection (faster there: 8.5 % at
+// M = 64; larger shapes then spill registers, and with 2 traps per warp it does not pay).
 template <bool FAST, bool BACK, int TMAX, int R>
 __device__ __forceinline__ void once_block(const StepArgs &a, const OnceSmem &sm, int t_begin, int t_end,
                                            float *trace) {
@@ -1269,10 +1291,11 @@ __device__ __forceinline__ void once_block(const StepArgs &a, const OnceSmem &sm
     if (lane < kOnceTMax) sm.Cw[warp * kOnceTMax + lane] = lane < T ? sm.C[lo + lane] : make_float2(0.f, 0.f);
     __syncwarp();
   }
+  constexpr bool PIPE = TMAX >= 4 && TMAX * R <= 32;
   if (T == TMAX)
-    once_loop<FAST, BACK, TMAX, R>(a, sm, t_begin, t_end, lo, T);
+    once_loop<FAST, BACK, TMAX, R, PIPE>(a, sm, t_begin, t_end, lo, T);
   else
-    once_loop<FAST, BACK, TMAX - 1, R>(a, sm, t_begin, t_end, lo, T);
+    once_loop<FAST, BACK, TMAX - 1, R, PIPE>(a, sm, t_begin, t_end, lo, T);
 }
 
 // Stages the first sub-tile's tables of a block (one committed group; empty without work).
