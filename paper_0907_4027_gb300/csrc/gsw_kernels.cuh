@@ -206,11 +206,6 @@ __device__ __forceinline__ int vgrid() { return gridDim.x * (blockDim.x / kThrea
 __device__ __forceinline__ void group_sync() {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + group_id()), "n"(kThreads) : "memory");
 }
-// The same barrier for warps that reach it at different instructions (code specialised per
-// warp): the non-aligned form, which PTX allows there.
-__device__ __forceinline__ void group_sync_any() {
-  asm volatile("barrier.sync %0, %1;" ::"r"(1 + group_id()), "n"(kThreads) : "memory");
-}
 
 // Traps [lo, hi) of a staged chunk of n that warp `warp` of a group takes.  Warps w and w + 4
 // issue to the same SM sub-partition (warp slot mod 4) and share its special-function unit, so
@@ -1159,8 +1154,7 @@ __device__ __forceinline__ void once_forward_only(const float *Xs, const float *
 
 // The sub-tiles of a block, for a warp whose traps lo .. lo + T - 1 are evaluated as TV traps
 // (T <= TV; the rest are padding: zero coefficients, their sums dropped), then the warp's
-// forward sums, totalled over its lanes in a fixed order and added in fixed point.  Warps of
-// one block may run copies of this loop for different TV: its barriers are non-aligned.
+// forward sums, totalled over its lanes in a fixed order and added in fixed point.
 // PIPE: the forward field of each sub-tile runs inside the next sub-tile's back-projection
 // (once_back), the last one's after the loop.
 template <bool FAST, bool BACK, int TV, int R, bool PIPE>
@@ -1184,7 +1178,7 @@ __device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm,
   for (int i = t_begin; i < t_end; i++) {
     const SubTile st = a.sub[i];
     const int buf = (i - t_begin) & 1;
-    if (!BACK) group_sync_any();  // the previous sub-tile's readers of Ps and of the other buffers are done
+    if (!BACK) group_sync();  // the previous sub-tile's readers of Ps and of the other buffers are done
     bool next_strip = false;
     if (i + 1 < t_end) {  // stage the next sub-tile's tables
       const SubTile nx = a.sub[i + 1];
@@ -1202,7 +1196,7 @@ __device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm,
 #pragma unroll
       for (int r = 0; r < R; r++)
         if (r < st.rows) sm.Sp[(warp * R + r) * kTileW + lane] = S[r];
-      group_sync_any();
+      group_sync();
       if (t < st.rows * kTileW) {  // one pixel per thread: the 8 warps' sums in warp order
         const int r = t >> 5, l = t & 31, ix = st.x0 + l;
         float2 s = sm.Sp[r * kTileW + l];
@@ -1226,7 +1220,7 @@ __device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm,
       }
       asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this sub-tile's tables
     }
-    group_sync_any();
+    group_sync();
 #pragma unroll
     for (int r = 0; r < R; r++) P[r] = r < st.rows ? sm.Ps[r * kTileW + lane] : make_float2(0.f, 0.f);
     if (!BACK)
@@ -1258,15 +1252,16 @@ __device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm,
 // being staged into rows(0) and cols(0) (one committed group).
 // BACK: weight update, back-projection -> a.phi, forward field of the new phases; otherwise
 // the forward field of the phases in a.phi.
-// A warp's trap count T is TMAX or less (warp_traps); it runs the loop compiled for TMAX traps,
-// or for TMAX - 1 traps with any remaining ones as padding, so that no per-trap branch remains.
-// Shapes of 4 to 16 traps per warp with at most 32 exponentials per thread (TMAX R <= 32) fuse
-// each sub-tile's forward field into the next sub-tile's back-projection (faster there: 8.5 % at
-// M = 64; larger shapes then spill registers, and with 2 traps per warp it does not pay).
+// A warp's trap count T is TMAX, TMAX - 1 or TMAX - 2 (warp_traps); every warp runs the loop
+// compiled for TMAX traps, the ones past T as padding, so that no per-trap branch remains and
+// one copy of the unrolled loop serves the block (with the fused forward field, copies for T
+// and T - 1 ran slower).  From 4 traps per warp, with at most 32 exponentials per thread, each
+// sub-tile's forward field is fused into the next sub-tile's back-projection (with more the
+// registers spill; with 2 traps per warp it does not pay).
 template <bool FAST, bool BACK, int TMAX, int R>
 __device__ __forceinline__ void once_block(const StepArgs &a, const OnceSmem &sm, int t_begin, int t_end,
                                            float *trace) {
-  static_assert(TMAX >= 2 && TMAX <= kOnceTMax, "traps per warp");
+  static_assert(TMAX >= 1 && TMAX <= kOnceTMax, "traps per warp");
   const int lane = threadIdx.x & 31, warp = gthread() >> 5;
   int lo, hi;
   warp_traps(a.M, warp, lo, hi);
@@ -1292,10 +1287,7 @@ __device__ __forceinline__ void once_block(const StepArgs &a, const OnceSmem &sm
     __syncwarp();
   }
   constexpr bool PIPE = TMAX >= 4 && TMAX * R <= 32;
-  if (T == TMAX)
-    once_loop<FAST, BACK, TMAX, R, PIPE>(a, sm, t_begin, t_end, lo, T);
-  else
-    once_loop<FAST, BACK, TMAX - 1, R, PIPE>(a, sm, t_begin, t_end, lo, T);
+  once_loop<FAST, BACK, TMAX, R, PIPE>(a, sm, t_begin, t_end, lo, T);
 }
 
 // Stages the first sub-tile's tables of a block (one committed group; empty without work).
@@ -1309,38 +1301,25 @@ __device__ __forceinline__ void once_stage_first(const StepArgs &a, const OnceSm
   cp_async_commit();
 }
 
-// Calls BODY with compile-time TMAX (traps per warp at most) and R (rows per sub-tile) of a
-// shape index (once_shape): a warp holds 2 TMAX R floats of exponentials and 2 TMAX of sums.
-#define HOT_WITH_ONCE_SHAPE(shape, BODY)                     \
-  switch (shape) {                                           \
-    case 1: { constexpr int TMAX = 2, R = 8; BODY; } break;  \
-    case 2: { constexpr int TMAX = 4, R = 8; BODY; } break;  \
-    case 3: { constexpr int TMAX = 6, R = 6; BODY; } break;  \
-    case 4: { constexpr int TMAX = 8, R = 4; BODY; } break;  \
-    case 5: { constexpr int TMAX = 10, R = 4; BODY; } break; \
-    case 6: { constexpr int TMAX = 12, R = 3; BODY; } break; \
-    case 7: { constexpr int TMAX = 13, R = 3; BODY; } break; \
-    case 8: { constexpr int TMAX = 14, R = 2; BODY; } break; \
-    default: { constexpr int TMAX = 16, R = 2; BODY; } break; \
-  }
-
-// The shape for M traps (0: none, M > kOnceMaxM): the smallest TMAX >= ceil(M / 8), so that a
-// warp's count (floor(M / 8) or ceil(M / 8), warp_traps) is TMAX, TMAX - 1 or TMAX - 2.
-__host__ __device__ constexpr int once_shape(int M) {
-  return M <= 0 || M > kOnceMaxM ? 0
-         : M <= 16              ? 1
-         : M <= 32              ? 2
-         : M <= 48              ? 3
-         : M <= 64              ? 4
-         : M <= 80              ? 5
-         : M <= 96              ? 6
-         : M <= 104             ? 7
-         : M <= 112             ? 8
-                                : 9;
-}
+// The shape of M traps (0: none, M > kOnceMaxM): TMAX = ceil(M / 8) traps per warp at most.
+__host__ __device__ constexpr int once_shape(int M) { return M <= 0 || M > kOnceMaxM ? 0 : (M + kWarps - 1) / kWarps; }
+// R, the rows per sub-tile of a shape: 8 up to 4 traps per warp, 3 for 11 (faster there than 2),
+// otherwise the largest R with TMAX R <= 32 (the fused forward field, once_block).
 __host__ __device__ constexpr int once_rows(int shape) {
-  return shape <= 2 ? 8 : shape == 3 ? 6 : shape <= 5 ? 4 : shape <= 7 ? 3 : 2;
+  return shape <= 4 ? 8 : shape == 11 ? 3 : 32 / shape < 8 ? 32 / shape : 8;
 }
+
+// Calls BODY (parenthesised) with compile-time TMAX and R of a shape (once_shape).
+#define HOT_ONCE_CASE(k, BODY) \
+  case k: { constexpr int TMAX = k, R = ::hot::once_rows(k); BODY; } break;
+#define HOT_WITH_ONCE_SHAPE(shape, BODY)                                                        \
+  switch (shape) {                                                                              \
+    HOT_ONCE_CASE(1, BODY) HOT_ONCE_CASE(2, BODY) HOT_ONCE_CASE(3, BODY) HOT_ONCE_CASE(4, BODY)   \
+    HOT_ONCE_CASE(5, BODY) HOT_ONCE_CASE(6, BODY) HOT_ONCE_CASE(7, BODY) HOT_ONCE_CASE(8, BODY)   \
+    HOT_ONCE_CASE(9, BODY) HOT_ONCE_CASE(10, BODY) HOT_ONCE_CASE(11, BODY) HOT_ONCE_CASE(12, BODY) \
+    HOT_ONCE_CASE(13, BODY) HOT_ONCE_CASE(14, BODY) HOT_ONCE_CASE(15, BODY)                      \
+    default: HOT_ONCE_CASE(16, BODY)                                                            \
+  }
 
 // The per-launch form.  The tables are constant during hot_gsw: the first sub-tile's are
 // staged before waiting for the previous launch.

@@ -1,8 +1,9 @@
 """GPU: the one-exponential GSW step (hot_set_once) -- each pixel-trap exponential evaluated once
 per iteration and kept in registers between the back-projection and the forward field.  Checked
 against the FP64 oracle (Eq. 1, Sec. 3; tolerances as in test_gpu_parity) and against the direct
-kernels, on shapes that cover every trap-count shape of the kernel, ragged strips, both column
-staging paths and runs of a block that cross from one 32-pixel strip into the next."""
+kernels, on shapes that cover the kernel's forms (8, 4, 3 and 2 rows per sub-tile, with and without
+the fused forward field, padding), ragged strips, both column staging paths and runs of a block
+that cross from one 32-pixel strip into the next."""
 import numpy as np
 import pytest
 
@@ -33,12 +34,16 @@ def rel_err(a, b):
 
 @pytest.mark.parametrize("precision", ["accurate", "fast"])
 @pytest.mark.parametrize("W,H,M", [
-    (96, 64, 32),     # 8 rows per sub-tile, 4 traps per warp
-    (70, 45, 64),     # W not a multiple of 4: column parts copied one by one
-    (1024, 40, 100),  # runs of 4-5 row segments that cross strip boundaries; 13 traps per warp
-    (300, 60, 104),   # a ragged last strip (12 columns), runs cut into 3-row sub-tiles and a remainder
-    (128, 30, 128),   # 2 rows per sub-tile, 16 traps per warp
-    (37, 29, 9),      # one ragged strip, fewer traps than warps
+    (96, 64, 32),     # 4 traps per warp, 8 rows per sub-tile
+    (70, 45, 64),     # W not a multiple of 4: column parts copied one by one; 8 traps x 4 rows
+    (1024, 40, 100),  # runs that cross strip boundaries; 13 traps x 2 rows, padding on four warps
+    (300, 60, 104),   # a ragged last strip (12 columns); 13 traps x 2 rows, a remainder sub-tile of one row
+    (128, 30, 128),   # 16 traps x 2 rows
+    (37, 29, 9),      # one ragged strip, fewer traps than warps (2 x 8 with padding)
+    (160, 33, 89),    # 12 traps x 2 rows, padding on seven warps; an odd row count
+    (64, 47, 122),    # 16 traps x 2 rows, padding on six warps
+    (200, 21, 88),    # 11 traps x 3 rows
+    (96, 50, 77),     # 10 traps x 3 rows, padding on three warps
 ])
 def test_once_matches_oracle_and_direct_kernels(hot, W, H, M, precision):
     w = wl.random_case(W, H, M, seed=W * 7 + H + M, precision=precision)
