@@ -942,6 +942,11 @@ static __global__ void __launch_bounds__(kLossThreads) intensity_loss_kernel(Los
 // resumed from stored phases gives the same bits.
 constexpr int kOnceMaxM = 128;
 constexpr int kOnceTMax = 16;  // traps per warp at most (8 warps x 16 = kOnceMaxM)
+// Rows per sub-tile of the forward field of given phases (no exponentials kept between sub-tiles,
+// so taller sub-tiles: fewer barriers).  Its block runs are the step's, cut into sub-tiles of
+// these rows: per trap the same rows are added in the same order, so the sums are the bits of
+// the step's forward field.
+constexpr int kOnceFwdRows = 8;
 
 // Floats per trap in a staged block of row parts (R rows, in 16-byte pieces).
 __host__ __device__ constexpr int once_yw(int R) { return (R + 3) & ~3; }

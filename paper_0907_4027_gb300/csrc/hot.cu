@@ -81,6 +81,9 @@ struct hot_ctx {
   hot::SubTile *osub = nullptr;  // [on_sub]
   int *ofirst = nullptr;         // [ogrid + 1]
   int ogrid = 0, on_sub = 0;
+  // the same block runs cut into sub-tiles of hot::kOnceFwdRows rows: the forward field of given phases
+  hot::SubTile *ofsub = nullptr;
+  int *offirst = nullptr;
   int shard_k = -1;                      // last launch of a sharded sequence (hot_sharded_*)
   // state
   float *phi = nullptr;  // [N]
@@ -314,8 +317,8 @@ int launch_sep(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const fl
 template <bool BACK>
 int launch_once(hot_ctx *c, bool pdl, int k, const float *phi) {
   hot::StepArgs a = make_step_args(c, k, phi, nullptr, nullptr);
-  a.sub = c->osub;
-  a.first = c->ofirst;
+  a.sub = BACK ? c->osub : c->ofsub;
+  a.first = BACK ? c->ofirst : c->offirst;
   a.chunk = c->M;
   Probe p(c, BACK ? HOT_KERNEL_STEP : HOT_KERNEL_FORWARD);
   cudaLaunchConfig_t cfg = {};
@@ -405,6 +408,8 @@ int build_once_schedule(hot_ctx *c, int sms) {
   c->on_sub = 0;
   dfree(c->osub);
   dfree(c->ofirst);
+  dfree(c->ofsub);
+  dfree(c->offirst);
   const int shape = hot::once_shape(c->M);
   if (!c->once_req || !shape || (c->precision != HOT_PREC_FAST && c->precision != HOT_PREC_ACCURATE)) return HOT_OK;
   int per_sm = 0, rc = HOT_OK;
@@ -414,12 +419,19 @@ int build_once_schedule(hot_ctx *c, int sms) {
   const int G = (int)std::min<long long>((long long)sms * per_sm, U);
   std::vector<hot::SubTile> sub;
   std::vector<int> first;
+  std::vector<hot::SubTile> fsub;
+  std::vector<int> ffirst;
   cut_schedule(c->W, c->H, G, hot::once_rows(shape), sub, first, true);
+  cut_schedule(c->W, c->H, G, hot::kOnceFwdRows, fsub, ffirst, true);
   rc = dalloc(&c->osub, sub.size());
   if (rc == HOT_OK) rc = dalloc(&c->ofirst, first.size());
+  if (rc == HOT_OK) rc = dalloc(&c->ofsub, fsub.size());
+  if (rc == HOT_OK) rc = dalloc(&c->offirst, ffirst.size());
   if (rc != HOT_OK) return rc;
   HOT_CUDA(cudaMemcpy(c->osub, sub.data(), sizeof(hot::SubTile) * sub.size(), cudaMemcpyHostToDevice));
   HOT_CUDA(cudaMemcpy(c->ofirst, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice));
+  HOT_CUDA(cudaMemcpy(c->ofsub, fsub.data(), sizeof(hot::SubTile) * fsub.size(), cudaMemcpyHostToDevice));
+  HOT_CUDA(cudaMemcpy(c->offirst, ffirst.data(), sizeof(int) * ffirst.size(), cudaMemcpyHostToDevice));
   c->ogrid = G;
   c->on_sub = (int)sub.size();
   c->once = shape;
@@ -761,6 +773,8 @@ void hot_destroy(hot_ctx *c) {
   dfree(c->first);
   dfree(c->osub);
   dfree(c->ofirst);
+  dfree(c->ofsub);
+  dfree(c->offirst);
   dfree(c->metrics);
   dfree(c->u8);
   dfree(c->sync);

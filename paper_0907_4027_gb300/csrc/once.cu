@@ -7,14 +7,17 @@ namespace hot_once {
 namespace {
 
 // Raises the dynamic shared-memory limit of a shape's kernels to what they use.
+// The forward field of given phases runs on sub-tiles of hot::kOnceFwdRows rows (its own schedule).
+constexpr int kFwdRows = hot::kOnceFwdRows;
+
 template <int TMAX, int R>
 cudaError_t set_smem() {
-  const int smem = hot::once_smem_bytes(R);
+  const int smem = hot::once_smem_bytes(R), fsmem = hot::once_smem_bytes(kFwdRows);
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e = cudaFuncSetAttribute(hot::gsw_once_kernel<true, true, TMAX, R>, at, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(hot::gsw_once_kernel<true, false, TMAX, R>, at, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(hot::gsw_once_kernel<true, false, TMAX, kFwdRows>, at, fsmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(hot::gsw_once_kernel<false, true, TMAX, R>, at, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(hot::gsw_once_kernel<false, false, TMAX, R>, at, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(hot::gsw_once_kernel<false, false, TMAX, kFwdRows>, at, fsmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(hot::gsw_once_persistent_kernel<true, TMAX, R>, at, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(hot::gsw_once_persistent_kernel<false, TMAX, R>, at, smem);
   return e;
@@ -22,8 +25,8 @@ cudaError_t set_smem() {
 
 template <int TMAX, int R>
 cudaError_t occupancy_shape(int *per_sm) {
-  int a = 0, b = 0, p = 0, q = 0;
-  const int smem = hot::once_smem_bytes(R);
+  int a = 0, b = 0, p = 0, q = 0, f = 0, g = 0;
+  const int smem = hot::once_smem_bytes(R), fsmem = hot::once_smem_bytes(kFwdRows);
   *per_sm = 0;
   cudaError_t e = set_smem<TMAX, R>();
   if (e == cudaSuccess)
@@ -34,18 +37,22 @@ cudaError_t occupancy_shape(int *per_sm) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, hot::gsw_once_persistent_kernel<true, TMAX, R>, hot::kThreads, smem);
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, hot::gsw_once_persistent_kernel<false, TMAX, R>, hot::kThreads, smem);
-  *per_sm = std::min(std::min(a, b), std::min(p, q));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, hot::gsw_once_kernel<true, false, TMAX, kFwdRows>, hot::kThreads, fsmem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, hot::gsw_once_kernel<false, false, TMAX, kFwdRows>, hot::kThreads, fsmem);
+  *per_sm = std::min(std::min(std::min(a, b), std::min(p, q)), std::min(f, g));
   return e;
 }
 
 template <int TMAX, int R>
 cudaError_t step_shape(bool fast, bool back, cudaLaunchConfig_t cfg, const hot::StepArgs &a) {
-  cfg.dynamicSmemBytes = hot::once_smem_bytes(R);
+  cfg.dynamicSmemBytes = hot::once_smem_bytes(back ? R : kFwdRows);
   if (fast)
     return back ? cudaLaunchKernelEx(&cfg, hot::gsw_once_kernel<true, true, TMAX, R>, a)
-                : cudaLaunchKernelEx(&cfg, hot::gsw_once_kernel<true, false, TMAX, R>, a);
+                : cudaLaunchKernelEx(&cfg, hot::gsw_once_kernel<true, false, TMAX, kFwdRows>, a);
   return back ? cudaLaunchKernelEx(&cfg, hot::gsw_once_kernel<false, true, TMAX, R>, a)
-              : cudaLaunchKernelEx(&cfg, hot::gsw_once_kernel<false, false, TMAX, R>, a);
+              : cudaLaunchKernelEx(&cfg, hot::gsw_once_kernel<false, false, TMAX, kFwdRows>, a);
 }
 
 template <int TMAX, int R>
