@@ -139,11 +139,25 @@ int hot_set_precision(hot_ctx *c, int precision);
 int hot_gsw(hot_ctx *c, int iters, double *eff_out, double *unif_out);
 
 /* Checkpoint / resume: the GSW state is the phases and the weights (float32, exactly as held),
- * so hot_set_state on a context with the same optics and traps continues bit for bit where
- * hot_get_state left off.  phi: HOST float32 [H*W]; w: HOST float32 [M] (finite, > 0).
- * Both synchronise; HOT_ESTATE before hot_set_traps. */
+ * so hot_set_state on a context with the same optics and traps continues where hot_get_state
+ * left off, bit for bit in the direct, separable and tensor modes.  phi: HOST float32 [H*W];
+ * w: HOST float32 [M] (finite, > 0).  Both synchronise; HOT_ESTATE before hot_set_traps.
+ * hot_set_state drops the unit phasors below. */
 int hot_get_state(hot_ctx *c, float *phi, float *w);
 int hot_set_state(hot_ctx *c, const float *phi, const float *w);
+
+/* The one-exponential step (hot_set_once) takes u_j = S_j/|S_j| for the forward field of each
+ * iteration and evaluates phi_j = arg S_j only in the last launch of a hot_gsw, where it also
+ * keeps u_j; the next hot_gsw of the context starts from those u_j, so that hot_gsw(a) followed by
+ * hot_gsw(b) equals hot_gsw(a + b) bit for bit.  They belong to the state of that form:
+ * hot_get_phasors copies them out (HOT_ESTATE when the current phases have none: set by the
+ * caller, or written by another mode); hot_set_phasors, after hot_set_state with the phases
+ * they belong to, restores them, and the resumed run continues bit for bit (without them it
+ * starts from e^{i phi_j}, equal to within the phasors' rounding, ~1e-7).  u: HOST float32
+ * [H*W][2] (re, im); every value finite with magnitude <= 2, else HOT_EINVAL; HOT_ESTATE when the
+ * one-exponential step is not in effect.  Both synchronise.  (No counterpart in the paper.) */
+int hot_get_phasors(hot_ctx *c, float *u);
+int hot_set_phasors(hot_ctx *c, const float *u);
 
 /* Convergence trace (no counterpart in the paper): with enable != 0, every following hot_gsw
  * records e and u (Eq. 4) of the field each iteration starts from; block 0 of each step

@@ -77,8 +77,16 @@ struct StepArgs {
   // Explicit coefficients G_m (Re, Im) instead of the GSW update (superposition, adjoint),
   // and the gradient output of the adjoint (ADJ)
   const float2 *G;                   // [M] or NULL: coefficients of the back-projection
-  float *grad;                       // [H*W] out: dL/dphi_j
+  union {
+    float *grad;  // [H*W] out: dL/dphi_j (ADJ)
+    float2 *u;    // NULL, or [H*W]: unit phasors u_j of phi (gsw_once_kernel, see once_flags)
+  };
   float inv_n;                       // 1 / N
+  // gsw_once_kernel: its step takes u_j = S_j/|S_j| for the forward field and writes phi_j = arg S_j
+  // only in the last launch of a call (kOnceLast), with u_j into u when set; its forward field of
+  // the phases in phi reads u_j from u under kOnceReadU (the phasors the last step wrote for them)
+  // instead of evaluating e^{i phi_j}.
+  int once_flags;
   float *trace;                      // NULL, or out: e, u (Eq. 4) of the field this launch reads
   float fx_scale;           // 2^fx_shift: fixed-point scale of the sums
   float inv_fx_n;           // 1 / (N 2^fx_shift)
@@ -1060,6 +1068,21 @@ __device__ __forceinline__ float2 unit_phasor(float ph) {
   return make_float2(c, s);
 }
 
+constexpr int kOnceLast = 1, kOnceReadU = 2;  // StepArgs::once_flags
+
+// u = S/|S|, the unit phasor e^{i arg S} without the angle; 1 for S = 0 (atan2(0, 0) = 0).
+__device__ __forceinline__ float2 unit_of(float2 s) {
+  float q = abs2(s);
+  if (q < 0x1p-100f) {  // |S| below 2^-50: scaled by 2^64 (exactly) so that |S|^2 stays a normal number
+    s.x *= 0x1p64f;
+    s.y *= 0x1p64f;
+    q = abs2(s);
+  }
+  if (q == 0.f) return make_float2(1.f, 0.f);
+  const float r = rsqrtf(q);
+  return make_float2(s.x * r, s.y * r);
+}
+
 // Back-projection of a warp's TV traps (tables and coefficients from Xs, Yb, Cw, trap by trap)
 // onto the lane's R rows: E[k][r] = e^{i (X + Y)} (kept), S[r] = sum_k c_k E[k][r], accumulated
 // as U[r] = sum_k Re(c_k) E[k][r] and W[r] = sum_k Im(c_k) E[k][r] (S = U + i W) with packed FP32
@@ -1162,9 +1185,11 @@ __device__ __forceinline__ void once_forward_only(const float *Xs, const float *
 // forward sums, totalled over its lanes in a fixed order and added in fixed point.
 // PIPE: the forward field of each sub-tile runs inside the next sub-tile's back-projection
 // (once_back), the last one's after the loop.
+// BACK: the forward field takes u_j = S_j/|S_j|; last: phi_j = atan2(S_j) is written (and u_j to
+// a.u when set).  Otherwise u_j is read from a.u under kOnceReadU, else e^{i phi_j} from a.phi.
 template <bool FAST, bool BACK, int TV, int R, bool PIPE>
 __device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm, int t_begin, int t_end, int lo,
-                                          int T) {
+                                          int T, bool last) {
   const int lane = threadIdx.x & 31, warp = gthread() >> 5, t = gthread();
   constexpr int YW = once_yw(R);
   float2 acc[TV];
@@ -1211,17 +1236,24 @@ __device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm,
           s.x += q.x;
           s.y += q.y;
         }
-        const float ph = atan2f(s.y, s.x);
-        if (ix < a.W) a.phi[(size_t)(st.y0 + r) * a.W + ix] = ph;
-        sm.Ps[r * kTileW + l] = ix < a.W ? unit_phasor<FAST>(FAST ? ph : phase_turns(ph)) : make_float2(0.f, 0.f);
+        const float2 u = unit_of(s);
+        if (last && ix < a.W) {
+          const size_t j = (size_t)(st.y0 + r) * a.W + ix;
+          a.phi[j] = atan2f(s.y, s.x);
+          if (a.u) a.u[j] = u;
+        }
+        sm.Ps[r * kTileW + l] = ix < a.W ? u : make_float2(0.f, 0.f);
       }
       asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // the next sub-tile's tables
     } else {
       if (t < st.rows * kTileW) {
         const int r = t >> 5, l = t & 31, ix = st.x0 + l;
-        const float ph = ix < a.W ? a.phi[(size_t)(st.y0 + r) * a.W + ix] : 0.f;
-        sm.Ps[r * kTileW + l] =
-            ix < a.W ? unit_phasor<FAST>(FAST ? reduced_radians(ph) : reduced_phase_turns(ph)) : make_float2(0.f, 0.f);
+        const size_t j = (size_t)(st.y0 + r) * a.W + ix;
+        float2 u = make_float2(0.f, 0.f);
+        if (ix < a.W)
+          u = (a.once_flags & kOnceReadU) ? a.u[j]
+                                          : unit_phasor<FAST>(FAST ? reduced_radians(a.phi[j]) : reduced_phase_turns(a.phi[j]));
+        sm.Ps[r * kTileW + l] = u;
       }
       asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this sub-tile's tables
     }
@@ -1265,7 +1297,7 @@ __device__ __forceinline__ void once_loop(const StepArgs &a, const OnceSmem &sm,
 // registers spill; with 2 traps per warp it does not pay).
 template <bool FAST, bool BACK, int TMAX, int R>
 __device__ __forceinline__ void once_block(const StepArgs &a, const OnceSmem &sm, int t_begin, int t_end,
-                                           float *trace) {
+                                           float *trace, bool last) {
   static_assert(TMAX >= 1 && TMAX <= kOnceTMax, "traps per warp");
   const int lane = threadIdx.x & 31, warp = gthread() >> 5;
   int lo, hi;
@@ -1292,7 +1324,7 @@ __device__ __forceinline__ void once_block(const StepArgs &a, const OnceSmem &sm
     __syncwarp();
   }
   constexpr bool PIPE = TMAX >= 4 && TMAX * R <= 32;
-  once_loop<FAST, BACK, TMAX, R, PIPE>(a, sm, t_begin, t_end, lo, T);
+  once_loop<FAST, BACK, TMAX, R, PIPE>(a, sm, t_begin, t_end, lo, T, last);
 }
 
 // Stages the first sub-tile's tables of a block (one committed group; empty without work).
@@ -1338,7 +1370,7 @@ __global__ void __launch_bounds__(kThreads, 2) gsw_once_kernel(StepArgs a) {
   once_stage_first<R>(a, sm, t_begin, t_end);
   grid_dependency_wait();
   for (int i = vb * kThreads + gthread(); i < 2 * a.M * a.copies; i += vg * kThreads) a.acc_clear[i] = 0ull;
-  once_block<FAST, BACK, TMAX, R>(a, sm, t_begin, t_end, a.trace);
+  once_block<FAST, BACK, TMAX, R>(a, sm, t_begin, t_end, a.trace, (a.once_flags & kOnceLast) != 0);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1781,9 +1813,9 @@ __global__ void __launch_bounds__(kThreads, 2) gsw_once_persistent_kernel(const 
     once_stage_first<R>(a, sm, t_begin, t_end);
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M * a.copies; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
     if (k == 0)
-      once_block<FAST, false, TMAX, R>(a, sm, t_begin, t_end, nullptr);
+      once_block<FAST, false, TMAX, R>(a, sm, t_begin, t_end, nullptr, false);
     else
-      once_block<FAST, true, TMAX, R>(a, sm, t_begin, t_end, p.trace ? p.trace + 2 * (k - 1) : nullptr);
+      once_block<FAST, true, TMAX, R>(a, sm, t_begin, t_end, p.trace ? p.trace + 2 * (k - 1) : nullptr, k == p.iters);
   }
 }
 

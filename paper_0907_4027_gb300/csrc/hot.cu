@@ -84,6 +84,11 @@ struct hot_ctx {
   // the same block runs cut into sub-tiles of hot::kOnceFwdRows rows: the forward field of given phases
   hot::SubTile *ofsub = nullptr;
   int *offirst = nullptr;
+  // the unit phasors u_j = S_j/|S_j| of phi, written by the last step of a one-exponential hot_gsw
+  // (hot::StepArgs::u_out); valid while phi is the phases that step wrote.  The next hot_gsw's first
+  // forward field then reads them (gsw_from_u) and so adds the terms an uninterrupted run adds.
+  float2 *ubuf = nullptr;  // [N]
+  bool u_valid = false, gsw_from_u = false;
   int shard_k = -1;                      // last launch of a sharded sequence (hot_sharded_*)
   // state
   float *phi = nullptr;  // [N]
@@ -113,6 +118,7 @@ struct hot_ctx {
   // CUDA graphs of whole hot_gsw(iters) launch sequences, keyed by (iters, precision)
   struct Graph {
     int iters, precision;
+    bool from_u;  // the first forward field reads ubuf
     long long kernels;
     cudaGraphExec_t exec;
   };
@@ -184,6 +190,7 @@ void free_traps(hot_ctx *c) {
   dfree(c->G);
   c->M = 0;
   c->have_fields = false;
+  c->u_valid = false;
 }
 
 int check_launch(hot_ctx *c, const char *what) {
@@ -251,7 +258,7 @@ void launch(hot_ctx *c, void (*kernel)(KArgs...), int grid, int block, int smem,
 // iteration k).  Accumulators rotate over three buffers, weights over two.
 hot::StepArgs make_step_args(const hot_ctx *c, int k, const float *phi, const float2 *G, float *grad) {
   const bool fast = c->precision == HOT_PREC_FAST;
-  hot::StepArgs a;
+  hot::StepArgs a = {};
   a.W = c->W;
   a.H = c->H;
   a.M = c->M;
@@ -281,6 +288,7 @@ hot::StepArgs make_step_args(const hot_ctx *c, int k, const float *phi, const fl
   a.grad = grad;
   a.inv_n = (float)(1.0 / (n_total(c)));
   a.trace = (c->tracing && c->trace && k >= 1 && k <= c->trace_cap) ? c->trace + 2 * (k - 1) : nullptr;
+  a.once_flags = 0;
   return a;
 }
 
@@ -315,8 +323,10 @@ int launch_sep(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const fl
 // The one-exponential step (BACK: weight update, back-projection and forward field) or its
 // forward field of given phases, on the context's one-exponential schedule.
 template <bool BACK>
-int launch_once(hot_ctx *c, bool pdl, int k, const float *phi) {
+int launch_once(hot_ctx *c, bool pdl, int k, const float *phi, bool last) {
   hot::StepArgs a = make_step_args(c, k, phi, nullptr, nullptr);
+  a.u = c->ubuf;
+  a.once_flags = (last ? hot::kOnceLast : 0) | (!BACK && !phi && c->gsw_from_u ? hot::kOnceReadU : 0);
   a.sub = BACK ? c->osub : c->ofsub;
   a.first = BACK ? c->ofirst : c->offirst;
   a.chunk = c->M;
@@ -337,9 +347,9 @@ int launch_once(hot_ctx *c, bool pdl, int k, const float *phi) {
 // The step kernel of the context's mode (accurate / fast direct evaluation, or separable).
 template <bool BACK, bool FWD, bool ADJ = false>
 int launch_mode(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const float2 *G = nullptr,
-                float *grad = nullptr) {
+                float *grad = nullptr, bool last = true) {
   if (separable_kernels(c)) return launch_sep<BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
-  if (c->once && FWD && !ADJ && !G) return launch_once<BACK>(c, pdl, k, phi);
+  if (c->once && FWD && !ADJ && !G) return launch_once<BACK>(c, pdl, k, phi, last);
   if (c->precision == HOT_PREC_FAST) return launch_tile<true, BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
   return launch_tile<false, BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
 }
@@ -432,6 +442,10 @@ int build_once_schedule(hot_ctx *c, int sms) {
   HOT_CUDA(cudaMemcpy(c->ofirst, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice));
   HOT_CUDA(cudaMemcpy(c->ofsub, fsub.data(), sizeof(hot::SubTile) * fsub.size(), cudaMemcpyHostToDevice));
   HOT_CUDA(cudaMemcpy(c->offirst, ffirst.data(), sizeof(int) * ffirst.size(), cudaMemcpyHostToDevice));
+  if (!c->ubuf) {
+    rc = dalloc(&c->ubuf, (size_t)c->W * c->H);
+    if (rc != HOT_OK) return rc;
+  }
   c->ogrid = G;
   c->on_sub = (int)sub.size();
   c->once = shape;
@@ -510,9 +524,10 @@ int build_schedule(hot_ctx *c) {
 }
 
 // One step-kernel launch (launch k of the sequence): weight update + back-projection and/or
-// forward field.
-int launch_step(hot_ctx *c, bool back, bool fwd, bool pdl, int k) {
-  if (back && fwd) return launch_mode<true, true>(c, pdl, k);
+// forward field.  last: the last launch of a call (the one-exponential step writes the phases only
+// then; every other kernel writes them at each launch).
+int launch_step(hot_ctx *c, bool back, bool fwd, bool pdl, int k, bool last = true) {
+  if (back && fwd) return launch_mode<true, true>(c, pdl, k, nullptr, nullptr, nullptr, last);
   if (back) return launch_mode<true, false>(c, pdl, k);
   return launch_mode<false, true>(c, pdl, k);
 }
@@ -604,6 +619,9 @@ int launch_persistent(hot_ctx *c, int iters) {
     p.step[j] = make_step_args(c, j, nullptr, nullptr, nullptr);
     if (c->precision == HOT_PREC_SEPARABLE) p.step[j].chunk = sep_chunk(c);
   }
+  if (c->once)
+    for (int j = 0; j < 6; j++) p.step[j].u = c->ubuf;
+  p.step[0].once_flags = c->gsw_from_u ? hot::kOnceReadU : 0;  // launch 0: the forward field of phi
   p.iters = iters;
   p.trace = c->tracing ? c->trace : nullptr;
   p.sync.count = c->sync;
@@ -652,6 +670,7 @@ int check_wait_error(hot_ctx *c, const char *who) {
   if (c->M) HOT_CUDA(cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * acc_elems(c->M), c->st));
   HOT_CUDA(cudaStreamSynchronize(c->st));
   c->have_fields = false;
+  c->u_valid = false;
   return fail(HOT_ETIMEOUT, "%s: a bounded device-side wait ran out (limit %.3g s)", who, c->wait_limit_s);
 }
 
@@ -669,8 +688,8 @@ int enqueue_gsw(hot_ctx *c, int iters) {
     return rc;
   }
   int rc = launch_step(c, false, true, false, 0);       // V^1 = F(phi^0)
-  for (int k = 1; k <= iters && rc == HOT_OK; k++)
-    rc = launch_step(c, true, true, pdl, k);            // w^k, c^k from V^k; phi^k; V^{k+1} = F(phi^k)
+  for (int k = 1; k <= iters && rc == HOT_OK; k++)      // w^k, c^k from V^k; phi^k; V^{k+1} = F(phi^k)
+    rc = launch_step(c, true, true, pdl, k, k == iters);
   if (rc == HOT_OK) rc = launch_finalize(c, pdl, iters);  // e, u of V^{iters+1}
   return rc;
 }
@@ -678,7 +697,7 @@ int enqueue_gsw(hot_ctx *c, int iters) {
 // Replays (capturing on first use) the graph of enqueue_gsw(iters).
 int launch_gsw_graph(hot_ctx *c, int iters) {
   for (auto &g : c->graphs)
-    if (g.iters == iters && g.precision == c->precision) {
+    if (g.iters == iters && g.precision == c->precision && g.from_u == c->gsw_from_u) {
       HOT_CUDA(cudaGraphLaunch(g.exec, c->st));
       c->launches += g.kernels;
       return HOT_OK;
@@ -707,7 +726,7 @@ int launch_gsw_graph(hot_ctx *c, int iters) {
   e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(HOT_ECUDA, "hot_gsw: graph instantiation: %s", cudaGetErrorString(e));
-  c->graphs.push_back({iters, c->precision, kernels, exec});
+  c->graphs.push_back({iters, c->precision, c->gsw_from_u, kernels, exec});
   HOT_CUDA(cudaGraphLaunch(exec, c->st));
   c->launches += kernels;
   return HOT_OK;
@@ -775,6 +794,7 @@ void hot_destroy(hot_ctx *c) {
   dfree(c->ofirst);
   dfree(c->ofsub);
   dfree(c->offirst);
+  dfree(c->ubuf);
   dfree(c->metrics);
   dfree(c->u8);
   dfree(c->sync);
@@ -856,6 +876,7 @@ int hot_set_traps(hot_ctx *c, int M, const double *xyz_m, const double *w0) {
   free(wh);
   if (e != cudaSuccess) return fail(HOT_ECUDA, "hot_set_traps: %s", cudaGetErrorString(e));
   c->have_fields = false;
+  c->u_valid = false;
   return launch_build_tables(c);
 }
 
@@ -882,6 +903,7 @@ int hot_set_phase(hot_ctx *c, const float *phi, int on_device) {
     HOT_CUDA(cudaStreamSynchronize(c->st));
   }
   c->have_fields = false;
+  c->u_valid = false;
   return HOT_OK;
 }
 
@@ -896,6 +918,7 @@ int hot_set_precision(hot_ctx *c, int precision) {
     HOT_CUDA(cudaStreamSynchronize(c->st));
   const bool resched = was_sep != (precision == HOT_PREC_SEPARABLE || precision == HOT_PREC_TENSOR);
   c->precision = precision;
+  c->u_valid = false;
   if (resched && c->M) return build_schedule(c);  // the two kernels' occupancies differ
   return HOT_OK;
 }
@@ -922,8 +945,14 @@ int hot_gsw(hot_ctx *c, int iters, double *eff_out, double *unif_out) {
     }
     c->trace_iters = iters;
   }
+  const bool had_u = c->u_valid;
+  c->gsw_from_u = c->u_valid && c->once && c->ubuf;
+  c->u_valid = false;
   const int rc = (c->use_graphs && !c->profiling && !c->persistent) ? launch_gsw_graph(c, iters) : enqueue_gsw(c, iters);
+  c->gsw_from_u = false;
   if (rc != HOT_OK) return rc;
+  // the last step of the one-exponential form left u_j of the phases it wrote in ubuf
+  c->u_valid = iters > 0 ? c->once && c->ubuf : had_u;
   c->have_fields = true;
   if (eff_out || unif_out) {
     if (c->persistent || c->precision == HOT_PREC_TENSOR) {
@@ -1023,6 +1052,7 @@ int hot_superposition(hot_ctx *c, const double *coef) {
   }
   dfree(d);
   c->have_fields = false;
+  c->u_valid = false;
   return rc;
 }
 
@@ -1076,6 +1106,7 @@ int hot_set_band(hot_ctx *c, int total_height, int y0) {
   c->y_off = y0;
   c->fx_shift = fixed_point_shift((long long)c->W * total_height);
   c->have_fields = false;
+  c->u_valid = false;
   c->shard_k = -1;
   return c->M ? launch_build_tables(c) : HOT_OK;
 }
@@ -1085,6 +1116,7 @@ int hot_sharded_begin(hot_ctx *c) {
   if (!c->M) return fail(HOT_ESTATE, "hot_sharded_begin: no traps set");
   c->shard_k = -1;
   c->have_fields = false;
+  c->u_valid = false;
   int rc = HOT_OK;
   if (c->precision == HOT_PREC_TENSOR) {
     rc = ensure_tc_plan(c);
@@ -1202,6 +1234,33 @@ int hot_set_state(hot_ctx *c, const float *phi, const float *w) {
   HOT_CUDA(cudaMemcpyAsync(c->w, w, sizeof(float) * c->M, cudaMemcpyHostToDevice, c->st));
   HOT_CUDA(cudaStreamSynchronize(c->st));
   c->have_fields = false;
+  c->u_valid = false;
+  return HOT_OK;
+}
+
+int hot_get_phasors(hot_ctx *c, float *u) {
+  if (!c || !u) return fail(HOT_EINVAL, "hot_get_phasors: NULL argument");
+  if (!c->M) return fail(HOT_ESTATE, "hot_get_phasors: no traps set");
+  if (!c->u_valid)
+    return fail(HOT_ESTATE, "hot_get_phasors: no unit phasors of the current phases (a one-exponential hot_gsw leaves them)");
+  const int rc = check_wait_error(c, "hot_get_phasors");
+  if (rc != HOT_OK) return rc;
+  HOT_CUDA(cudaMemcpyAsync(u, c->ubuf, sizeof(float2) * (size_t)c->W * c->H, cudaMemcpyDeviceToHost, c->st));
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  return HOT_OK;
+}
+
+int hot_set_phasors(hot_ctx *c, const float *u) {
+  if (!c || !u) return fail(HOT_EINVAL, "hot_set_phasors: NULL argument");
+  if (!c->M) return fail(HOT_ESTATE, "hot_set_phasors: no traps set");
+  if (!c->once || !c->ubuf) return fail(HOT_ESTATE, "hot_set_phasors: the one-exponential step is not in effect");
+  const size_t n = 2 * (size_t)c->W * c->H;
+  for (size_t i = 0; i < n; i++)
+    if (!std::isfinite(u[i]) || std::fabs(u[i]) > 2.f)
+      return fail(HOT_EINVAL, "hot_set_phasors: value %zu is not a unit phasor component", i);
+  HOT_CUDA(cudaMemcpyAsync(c->ubuf, u, sizeof(float) * n, cudaMemcpyHostToDevice, c->st));
+  HOT_CUDA(cudaStreamSynchronize(c->st));
+  c->u_valid = true;
   return HOT_OK;
 }
 
@@ -1714,6 +1773,7 @@ int save_state(hot_ctx *c, Saved &s, cudaStream_t st) {
 }
 
 int restore_state(hot_ctx *c, const Saved &s, cudaStream_t st) {
+  c->u_valid = false;
   HOT_CUDA(cudaMemcpyAsync(c->phi, s.phi, (size_t)c->W * c->H * sizeof(float), cudaMemcpyDeviceToDevice, st));
   HOT_CUDA(cudaMemcpyAsync(c->w, s.w, c->M * sizeof(float), cudaMemcpyDeviceToDevice, st));
   return HOT_OK;
@@ -1795,6 +1855,7 @@ int hot_set_once(hot_ctx *c, int on) {
   if (on != 0 && on != 1) return fail(HOT_EINVAL, "hot_set_once: on = %d is not 0 or 1", on);
   HOT_CUDA(cudaStreamSynchronize(c->st));
   c->once_req = on != 0;
+  c->u_valid = false;
   drop_graphs(c);
   return c->M ? build_schedule(c) : HOT_OK;
 }
@@ -1850,6 +1911,7 @@ int hot_autotune(hot_ctx *c, int iters, int *rows, int *blocks_per_sm, int *chun
   const int rc2 = restore_state(c, saved, c->st);
   cudaStreamSynchronize(c->st);
   c->have_fields = false;
+  c->u_valid = false;
   if (rc != HOT_OK) return rc;
   if (rc2 != HOT_OK) return rc2;
   if (rows) *rows = best.rows;
@@ -1930,7 +1992,10 @@ int hot_batch_gsw(hot_batch *b, int iters) {
   for (auto &g : b->graphs)
     if (g.iters == iters) {
       HOT_CUDA(cudaGraphLaunch(g.exec, b->st));
-      for (auto *c : b->ctx) c->have_fields = true;
+      for (auto *c : b->ctx) {
+        c->have_fields = true;
+        c->u_valid = false;  // the batch kernels wrote the phases
+      }
       b->ran = true;
       return HOT_OK;
     }
@@ -1957,7 +2022,10 @@ int hot_batch_gsw(hot_batch *b, int iters) {
   if (e != cudaSuccess) return fail(HOT_ECUDA, "hot_batch_gsw: graph instantiation: %s", cudaGetErrorString(e));
   b->graphs.push_back({iters, exec});
   HOT_CUDA(cudaGraphLaunch(exec, b->st));
-  for (auto *c : b->ctx) c->have_fields = true;
+  for (auto *c : b->ctx) {
+    c->have_fields = true;
+    c->u_valid = false;  // the batch kernels wrote the phases
+  }
   b->ran = true;
   return HOT_OK;
 }
@@ -1985,7 +2053,10 @@ int hot_batch_autotune(hot_batch *b, int iters, int *rows, int *blocks_per_sm, i
       [&](double *us) { return time_runs(b->st, iters, us, restore, [&]() { return hot_batch_gsw(b, iters); }); });
   const int rc2 = restore();
   cudaStreamSynchronize(b->st);
-  for (auto *c : b->ctx) c->have_fields = false;
+  for (auto *c : b->ctx) {
+    c->have_fields = false;
+    c->u_valid = false;
+  }
   b->ran = false;
   if (rc != HOT_OK) return rc;
   if (rc2 != HOT_OK) return rc2;

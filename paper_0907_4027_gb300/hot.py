@@ -76,6 +76,8 @@ SIGNATURES = {
     "hot_get_trace": (_c_int, [_vp, _vp, _vp, _c_int]),
     "hot_get_state": (_c_int, [_vp, _vp, _vp]),
     "hot_set_state": (_c_int, [_vp, _vp, _vp]),
+    "hot_get_phasors": (_c_int, [_vp, _vp]),
+    "hot_set_phasors": (_c_int, [_vp, _vp]),
     "hot_set_wait_limit": (_c_int, [_vp, _c_double]),
     "hot_profile": (_c_int, [_vp, _c_int]),
     "hot_profile_read": (_c_int, [_vp, _vp, _vp]),
@@ -405,6 +407,22 @@ def hot_set_state(ctx: int, phi, w) -> None:
     _ok(lib.hot_set_state(_vp(ctx), pp, wp), "hot_set_state")
 
 
+def hot_get_phasors(ctx: int, N: int):
+    """The unit phasors the last one-exponential step left for the current phases (float32 [N][2]),
+    or None when there are none (HOT_ESTATE)."""
+    u = np.empty(2 * N, dtype=np.float32)
+    rc = lib.hot_get_phasors(_vp(ctx), u.ctypes.data_as(_vp))
+    if rc == HOT_ESTATE:
+        return None
+    _ok(rc, "hot_get_phasors")
+    return u
+
+
+def hot_set_phasors(ctx: int, u) -> None:
+    u, up = _host_ptr(np.asarray(u).reshape(-1), np.float32)
+    _ok(lib.hot_set_phasors(_vp(ctx), up), "hot_set_phasors")
+
+
 def hot_use_persistent(ctx: int, enable: bool) -> None:
     _ok(lib.hot_use_persistent(_vp(ctx), int(bool(enable))), "hot_use_persistent")
 
@@ -561,11 +579,15 @@ class Hologram:
         return hot_get_trace(self.ctx, iters + 1)
 
     def get_state(self):
-        """(phi, w) float32 host copies: resume elsewhere with set_state, bit for bit."""
-        return hot_get_state(self.ctx, self.N, self.M)
+        """(phi, w, u) host copies -- phases, weights and the unit phasors the last one-exponential
+        step left for them (None otherwise): resume elsewhere with set_state, bit for bit."""
+        phi, w = hot_get_state(self.ctx, self.N, self.M)
+        return phi, w, hot_get_phasors(self.ctx, self.N)
 
-    def set_state(self, phi, w):
+    def set_state(self, phi, w, u=None):
         hot_set_state(self.ctx, phi, w)
+        if u is not None:
+            hot_set_phasors(self.ctx, u)
 
     def set_wait_limit(self, seconds: float):
         hot_set_wait_limit(self.ctx, seconds)

@@ -134,3 +134,25 @@ def test_once_full_hd_slm_against_oracle(hot, precision):
     np.testing.assert_allclose(w1, r1["w"], rtol=REL_V)
     r2 = oracle.gsw(w.geom, w.xyz, 2, w.phi0)
     assert abs(e2 - r2["e"]) < ABS_EU and abs(u2 - r2["u"]) < ABS_EU
+
+
+def test_once_stored_phasors_follow_the_phases(hot):
+    """The unit phasors that the last step of a call leaves for the next call serve only the phases
+    that step wrote: after hot_set_phase the next call starts from e^{i phi} of the new phases
+    (against the oracle), and hot_get_phasors reports none; a resumed call uses them."""
+    w = wl.random_case(160, 64, 40, seed=5, precision="fast")
+    other = np.random.default_rng(9).uniform(-np.pi, np.pi, w.W * w.H).astype(np.float32)
+    with hot.Hologram.from_workload(w) as h:
+        assert hot.hot_get_phasors(h.ctx, h.N) is None  # phases set by the caller
+        h.gsw(2)
+        u = hot.hot_get_phasors(h.ctx, h.N)
+        assert u is not None
+        phi = h.phase("f32")
+        np.testing.assert_allclose(u[0::2] + 1j * u[1::2], np.exp(1j * phi.astype(np.float64)), atol=2e-6)
+        h.set_phase(other)
+        assert hot.hot_get_phasors(h.ctx, h.N) is None
+        h.gsw(0)
+        V, _ = h.fields()
+        h.gsw(0)  # still no phasors: the same bits again
+        assert np.array_equal(h.fields()[0], V)
+    assert rel_err(V, oracle.forward(w.geom, w.xyz, other.astype(np.float64))) < REL_V

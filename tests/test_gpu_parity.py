@@ -342,23 +342,34 @@ def test_convergence_trace_matches_oracle(hot, persistent):
 
 
 def test_checkpoint_resume_across_contexts(hot):
-    """hot_get_state / hot_set_state: 3 iterations, state moved to a fresh context, 2 more
-    iterations equal 5 iterations in one context, bit for bit."""
+    """hot_get_state / hot_set_state (with the one-exponential step's unit phasors): 3 iterations,
+    state moved to a fresh context, 2 more iterations equal 5 iterations in one context, bit for
+    bit; without the phasors, to within their rounding."""
     w = wl.random_case(70, 45, 20, seed=22, precision="fast")
     with make(hot, w) as a:
         a.gsw(5)
         ref = (a.phase("f32"), a.fields())
     with make(hot, w) as b:
         b.gsw(3)
-        phi, wt = b.get_state()
+        phi, wt, u = b.get_state()
+    assert u is not None  # the one-exponential step's unit phasors belong to the state
     with hot.Hologram(w.W, w.H, w.pitch, w.wavelength, w.focal, precision=w.precision) as c:
         c.set_traps(w.xyz)
-        c.set_state(phi, wt)
+        c.set_state(phi, wt, u)
         c.gsw(2)
         got = (c.phase("f32"), c.fields())
         with pytest.raises(hot.HotError, match="HOT_EINVAL"):
             c.set_state(phi, -wt)
+        with pytest.raises(hot.HotError, match="HOT_EINVAL"):
+            c.set_state(phi, wt, np.full_like(u, np.nan))
+        # without the phasors the run starts from e^{i phi}: equal to within their rounding
+        c.set_state(phi, wt)
+        assert hot.hot_get_phasors(c.ctx, c.N) is None
+        c.gsw(2)
+        near = (c.phase("f32"), c.fields())
     assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1][0], got[1][0]) and np.array_equal(ref[1][1], got[1][1])
+    np.testing.assert_allclose(np.abs(near[1][0]), np.abs(ref[1][0]), rtol=1e-5)
+    np.testing.assert_allclose(near[1][1], ref[1][1], rtol=1e-5)
 
 
 @pytest.mark.parametrize("precision", ["accurate", "fast", "separable", "tensor"])
