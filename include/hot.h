@@ -302,13 +302,15 @@ int hot_get_block_merge(const hot_ctx *c, int *requested, int *in_effect);
 /* One-exponential step of the accurate and fast modes (no counterpart in the paper's kernel;
  * the same sums, Eq. 1 and Sec. 3): with M <= 128 traps the GSW step evaluates each pixel-trap
  * exponential E = e^{i Delta_j^m} (Eq. 2) once per iteration and keeps it in registers between
- * the back-projection S_j = sum_m c_m E and the forward field N V_m = sum_j e^{i phi_j} conj(E),
- * which halves the cos/sin work of an iteration.  Its blocks split the M traps among their warps
- * (at most 16 traps per warp, so at most 128 traps) and walk sub-tiles of 2 to 8 rows (fixed by
- * M); its schedule is its own, so the tiling above does not apply to it (it still applies to the
- * adjoint and the superposition, which keep the direct kernels).  The forward field of given
- * phases (the first launch of hot_gsw, hot_field) uses the same arithmetic, so resumed
- * sequences, CUDA graphs and the persistent form give the same bits.  Its results differ from
+ * the back-projection S_j = sum_m c_m E and the forward field N V_m = sum_j u_j conj(E), with
+ * u_j = S_j/|S_j| = e^{i phi_j} (phi_j = atan2 S_j is evaluated only in the last launch of a
+ * call), which halves the cos/sin work of an iteration.  Its blocks split the M traps among their
+ * warps (at most 16 traps per warp, so at most 128 traps) and walk sub-tiles of 2 to 8 rows (fixed
+ * by M); its schedule is its own, so the tiling above does not apply to it (it still applies to
+ * the adjoint and the superposition, which keep the direct kernels).  The forward field of the
+ * phases a call starts from (its first launch) uses the same arithmetic, with the unit phasors
+ * the previous call's last step kept (hot_get_phasors), so resumed sequences, CUDA graphs and the
+ * persistent form give the same bits.  Its results differ from
  * the direct kernels' by FP32 rounding.  on: 1 (default) or 0, else HOT_EINVAL; it is in effect
  * where M <= 128 and the mode is HOT_PREC_ACCURATE or HOT_PREC_FAST.  Rebuilds the schedule;
  * synchronises the context's stream.  hot_get_once reports the setting and whether it is in
