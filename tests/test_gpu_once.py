@@ -156,3 +156,28 @@ def test_once_stored_phasors_follow_the_phases(hot):
         h.gsw(0)  # still no phasors: the same bits again
         assert np.array_equal(h.fields()[0], V)
     assert rel_err(V, oracle.forward(w.geom, w.xyz, other.astype(np.float64))) < REL_V
+
+
+def test_once_phasors_dropped_by_other_phase_writers(hot):
+    """hot_superposition and a batch write the phases of a context with kept unit phasors: the
+    phasors are dropped, and the next call's forward field is that of the new phases."""
+    w = wl.random_case(96, 40, 30, seed=8, precision="fast")
+    coef = np.exp(1j * np.random.default_rng(4).uniform(-np.pi, np.pi, w.xyz.shape[0]))
+    with hot.Hologram.from_workload(w) as h:
+        h.gsw(2)
+        assert hot.hot_get_phasors(h.ctx, h.N) is not None
+        h.superposition(coef)
+        assert hot.hot_get_phasors(h.ctx, h.N) is None
+        phi_sr = h.phase("f32")
+        h.gsw(0)
+        V_sr, _ = h.fields()
+        h.gsw(2)
+        assert hot.hot_get_phasors(h.ctx, h.N) is not None
+        with hot.Batch([h]) as b:
+            b.gsw(1)
+        assert hot.hot_get_phasors(h.ctx, h.N) is None
+        phi_b = h.phase("f32")
+        h.gsw(0)
+        V_b, _ = h.fields()
+    assert rel_err(V_sr, oracle.forward(w.geom, w.xyz, phi_sr.astype(np.float64))) < REL_V
+    assert rel_err(V_b, oracle.forward(w.geom, w.xyz, phi_b.astype(np.float64))) < REL_V
