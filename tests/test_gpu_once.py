@@ -181,3 +181,25 @@ def test_once_phasors_dropped_by_other_phase_writers(hot):
         V_b, _ = h.fields()
     assert rel_err(V_sr, oracle.forward(w.geom, w.xyz, phi_sr.astype(np.float64))) < REL_V
     assert rel_err(V_b, oracle.forward(w.geom, w.xyz, phi_b.astype(np.float64))) < REL_V
+
+
+def test_once_phasor_calls_where_they_do_not_apply(hot):
+    """hot_set_phasors needs the one-exponential step in effect; get_state carries no phasors in
+    the other modes, and set_state without them starts from e^{i phi}."""
+    w = wl.random_case(64, 24, 20, seed=2, precision="separable")
+    with hot.Hologram.from_workload(w) as h:
+        h.gsw(1)
+        phi, wt, u = h.get_state()
+        assert u is None
+        with pytest.raises(hot.HotError, match="HOT_ESTATE"):
+            hot.hot_set_phasors(h.ctx, np.zeros(2 * h.N, dtype=np.float32))
+        h.set_state(phi, wt)
+        h.gsw(0)
+    w = wl.random_case(64, 24, 20, seed=2, precision="fast")
+    with hot.Hologram.from_workload(w) as h:
+        h.gsw(1)
+        _, _, u = h.get_state()
+        assert u is not None and u.shape == (2 * h.N,)
+        with pytest.raises(hot.HotError, match="HOT_EINVAL"):
+            hot.hot_set_phasors(h.ctx, np.full(2 * h.N, 3.0, dtype=np.float32))
+        assert hot.hot_get_phasors(h.ctx, h.N) is not None  # a rejected call leaves them
