@@ -1753,6 +1753,7 @@ __device__ __forceinline__ bool grid_sync(const GridSync &g, unsigned int &epoch
 struct PersistArgs {
   StepArgs step[6];
   int iters;
+  int k0;  // one-exponential form: the first launch it runs (1: launch 0 was its own launch before it)
   GridSync sync;
   float *trace;  // NULL, or [iters][2]: e, u of the field read by iteration k (convergence trace)
 };
@@ -1807,9 +1808,9 @@ __global__ void __launch_bounds__(kThreads, 2) gsw_once_persistent_kernel(const 
   const StepArgs &a0 = p.step[0];
   const int t_begin = a0.first[blockIdx.x], t_end = a0.first[blockIdx.x + 1];
   unsigned int epoch = 0u;
-  for (int k = 0; k <= p.iters; k++) {
+  for (int k = p.k0; k <= p.iters; k++) {
     const StepArgs &a = p.step[k % 6];
-    if (k > 0 && !grid_sync(p.sync, epoch)) return;
+    if (k > p.k0 && !grid_sync(p.sync, epoch)) return;
     once_stage_first<R>(a, sm, t_begin, t_end);
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < 2 * a.M * a.copies; i += gridDim.x * kThreads) a.acc_clear[i] = 0ull;
     if (k == 0)

@@ -349,7 +349,12 @@ template <bool BACK, bool FWD, bool ADJ = false>
 int launch_mode(hot_ctx *c, bool pdl, int k, const float *phi = nullptr, const float2 *G = nullptr,
                 float *grad = nullptr, bool last = true) {
   if (separable_kernels(c)) return launch_sep<BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
-  if (c->once && FWD && !ADJ && !G) return launch_once<BACK>(c, pdl, k, phi, last);
+  if (c->once && FWD && !ADJ && !G) {
+    // the forward field a call opens with, of phases the caller set: the separable kernel
+    // (complex tables, FMA only) at about half the cost of evaluating every exponential
+    if (!BACK && !phi && !c->gsw_from_u) return launch_sep<false, true>(c, pdl, k);
+    return launch_once<BACK>(c, pdl, k, phi, last);
+  }
   if (c->precision == HOT_PREC_FAST) return launch_tile<true, BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
   return launch_tile<false, BACK, FWD, ADJ>(c, pdl, k, phi, G, grad);
 }
@@ -622,6 +627,7 @@ int launch_persistent(hot_ctx *c, int iters) {
   if (c->once)
     for (int j = 0; j < 6; j++) p.step[j].u = c->ubuf;
   p.step[0].once_flags = c->gsw_from_u ? hot::kOnceReadU : 0;  // launch 0: the forward field of phi
+  p.k0 = 0;
   p.iters = iters;
   p.trace = c->tracing ? c->trace : nullptr;
   p.sync.count = c->sync;
@@ -639,6 +645,11 @@ int launch_persistent(hot_ctx *c, int iters) {
   HOT_CUDA(cudaMemsetAsync(c->sync, 0, sizeof(unsigned int), c->st));  // arrival count
   Probe probe(c, HOT_KERNEL_STEP);
   if (c->once) {
+    if (!c->gsw_from_u) {  // launch 0 as in enqueue_gsw: the separable forward field of phi
+      const int rc = launch_sep<false, true>(c, false, 0);
+      if (rc != HOT_OK) return rc;
+      p.k0 = 1;
+    }
     for (int j = 0; j < 6; j++) {
       p.step[j].sub = c->osub;
       p.step[j].first = c->ofirst;
