@@ -307,10 +307,11 @@ int hot_get_block_merge(const hot_ctx *c, int *requested, int *in_effect);
  * call), which halves the cos/sin work of an iteration.  Its blocks split the M traps among their
  * warps (at most 16 traps per warp, so at most 128 traps) and walk sub-tiles of 2 to 8 rows (fixed
  * by M); its schedule is its own, so the tiling above does not apply to it (it still applies to
- * the adjoint and the superposition, which keep the direct kernels).  The forward field of the
- * phases a call starts from (its first launch) uses the same arithmetic, with the unit phasors
- * the previous call's last step kept (hot_get_phasors), so resumed sequences, CUDA graphs and the
- * persistent form give the same bits.  Its results differ from
+ * the adjoint and the superposition, which keep the direct kernels).  A call that continues from
+ * the phases of the previous one starts with the forward field of the unit phasors that call's
+ * last step kept (hot_get_phasors), in the step's arithmetic, so resumed sequences, CUDA graphs
+ * and the persistent form give the same bits; a call that starts from phases the caller set
+ * takes their forward field from the separable kernel (complex tables).  Its results differ from
  * the direct kernels' by FP32 rounding.  on: 1 (default) or 0, else HOT_EINVAL; it is in effect
  * where M <= 128 and the mode is HOT_PREC_ACCURATE or HOT_PREC_FAST.  Rebuilds the schedule;
  * synchronises the context's stream.  hot_get_once reports the setting and whether it is in
