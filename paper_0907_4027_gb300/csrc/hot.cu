@@ -539,7 +539,7 @@ int launch_step(hot_ctx *c, bool back, bool fwd, bool pdl, int k, bool last = tr
 
 // After the last launch (k = iters): Eq. 4 metrics, field sums, weights home, accumulators cleared.
 int launch_finalize(hot_ctx *c, bool pdl, int iters) {
-  hot::FinalizeArgs f;
+  hot::FinalizeArgs f = {};  // done = NULL: no completion stamp
   const size_t M2 = 2 * (size_t)c->M * acc_copies(c);
   f.M = c->M;
   f.copies = acc_copies(c);
@@ -619,7 +619,7 @@ int launch_tc(hot_ctx *c, bool pdl, int k) {
 // The whole sequence of enqueue_gsw's step launches as one cooperative launch (all blocks
 // resident; the grid is one wave by construction of the schedule).
 int launch_persistent(hot_ctx *c, int iters) {
-  hot::PersistArgs p;
+  hot::PersistArgs p = {};
   for (int j = 0; j < 6; j++) {
     p.step[j] = make_step_args(c, j, nullptr, nullptr, nullptr);
     if (c->precision == HOT_PREC_SEPARABLE) p.step[j].chunk = sep_chunk(c);

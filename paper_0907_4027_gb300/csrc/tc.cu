@@ -151,7 +151,7 @@ void plan_destroy(Plan *p) {
 }
 
 cudaError_t plan_refresh(Plan *p, cudaStream_t st) {
-  tc::TableArgs t;
+  tc::TableArgs t = {};
   t.W = p->W;
   t.H = p->H;
   t.M = p->M;
@@ -275,7 +275,7 @@ cudaError_t launch_forward(Plan *p, const Step &s, cudaStream_t st, bool pdl, bo
 
 cudaError_t launch_iteration(Plan *p, const Step &s, cudaStream_t st, bool pdl, bool chain, int *kernels) {
   *kernels = 0;
-  tc::PrepArgs pa;
+  tc::PrepArgs pa = {};
   pa.H = p->H;
   pa.M = p->M;
   pa.Kb = p->Kb;
