@@ -54,6 +54,11 @@ def test_invalid_arguments_fail_before_device_work(hot):
     assert lib.hot_get_fields(None, None, None) == hot.HOT_EINVAL
     assert lib.hot_set_precision(None, 0) == hot.HOT_EINVAL
     assert lib.hot_sync(None) == hot.HOT_EINVAL
+    assert lib.hot_get_state(None, None, None) == hot.HOT_EINVAL
+    assert lib.hot_set_state(None, None, None) == hot.HOT_EINVAL
+    assert lib.hot_get_phasors(None, None) == hot.HOT_EINVAL
+    assert lib.hot_set_phasors(None, None) == hot.HOT_EINVAL
+    assert lib.hot_set_once(None, 1) == hot.HOT_EINVAL
     assert lib.hot_kernel_launches(None) == 0
     lib.hot_destroy(None)
 
